@@ -1,0 +1,367 @@
+"""Benchmark of the CrowdSplat crowd-synthesis hot path on GB300.
+
+One step = one animated frame of the paper-scale crowd: new joint poses for
+every instance (cs_set_instances) followed by cs_render (forward kinematics,
+distance LoD + cull, LBS + EWA projection + SH colour, tile binning, depth
+and tile radix sorts, compositing) at 1920x1080.  Workload: 14 procedural
+templates x 65,536 Gaussians (SH degree 3), 3,500 instances on a jittered
+grid, 3 distance LoD levels (100/25/6 %, 10 m / 30 m), camera 3 m from the
+first row (synthetic stand-ins for the paper's avatars and motions).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead (a bounded pixel sample of the same frame).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "crowd FPS @3,500 inst 1080p; learned vs plain LoD FPS at equal PSNR"
+UNIT = "frames/s"
+WORKLOAD = "crowd_14x65536g_sh3_3500inst_1920x1080_lod3_animated"
+PAPER_FPS = 31.0  # RTX4090, resolution not stated: context only, not this workload
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=float(d["hbm_gbs"]), src="measured", sm_max_mhz=float(d.get("sm_max_mhz", 2070)))
+    return dict(hbm_gbs=6800.0, src="fallback", sm_max_mhz=2070.0)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per stage (per frame), see the design doc
+# ---------------------------------------------------------------------------
+
+def stage_bytes(st, n_inst, tpl_bytes, pixels):
+    S, P = st["splats"], st["pairs"]
+    V = st["instances_visible"]
+    sort_passes_depth = 4
+    sort_passes_tile = math.ceil(max(1, math.ceil(math.log2(max(2, st["tiles_x"] * st["tiles_y"])))) / 8)
+    return {
+        "fk": n_inst * (4 + 72 * 4 + 24 * 48),
+        "cull_lod": n_inst * (4 + 48 + 48 + 16 + 4),
+        # template attributes once (shared, L2-resident across a group) +
+        # per-instance transforms + per-splat outputs (record 48 B, key 4,
+        # id 4, rect 8, tile count 4)
+        "skin_project": tpl_bytes + V * (24 * 48 + 64) + S * 68,
+        # per pass: keys read by the histogram, key+value read and written
+        "depth_sort": S * sort_passes_depth * (4 + 8 + 8),
+        # order + gathered tile count (scan: read twice), rect, pair writes
+        "pair_emit": S * (4 + 4 + 4 + 4 + 8 + 8) + P * 6,
+        "tile_sort": P * sort_passes_tile * (2 + 6 + 6),
+        "tile_ranges": P * 2 * 2,
+        # each pair: splat id + 48 B record; each pixel: 16 B written
+        "blend": P * (4 + 48) + pixels * 16,
+    }
+
+
+def template_bytes(sc):
+    tot = 0
+    for t in sc.templates:
+        k = (t.sh_degree + 1) ** 2
+        tot += t.means.shape[0] * (16 + 16 + 8 + 16 + 4 + ((k * 3 + 3) // 4) * 16)
+    return tot
+
+
+# ---------------------------------------------------------------------------
+# oracle on the host cores (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_frame_time(sc, stride=16):
+    """Seconds for one full frame of the oracle, from two bounded runs: a
+    single-pixel lattice (all projection work, no compositing) and a lattice
+    of every `stride`-th pixel in both directions (adds 1/stride^2 of the
+    compositing).  Full frame = project + stride^2 x (lattice - project)."""
+    import oracle
+    os_ = oracle.OracleScene(sc)
+    W, H = sc.camera.width, sc.camera.height
+    t0 = time.perf_counter()
+    oracle.render(os_, lattice=(W // 2, H // 2, 1, 1, 1, 1))
+    t_proj = time.perf_counter() - t0
+    nx, ny = (W + stride - 1) // stride, (H + stride - 1) // stride
+    t0 = time.perf_counter()
+    oracle.render(os_, lattice=(0, 0, stride, stride, nx, ny))
+    t_lat = time.perf_counter() - t0
+    t_pix = max(t_lat - t_proj, 0.0)
+    full = t_proj + t_pix * (W * H) / (nx * ny)
+    return full, dict(project_s=round(t_proj, 3), lattice_s=round(t_lat, 3), stride=stride,
+                      lattice_px=nx * ny, cores=oracle.num_threads())
+
+
+def run_reference(args, sc, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    times = []
+    info = {}
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps are not run
+    for step in range(args.steps):
+        full, info = oracle_frame_time(sc, stride=args.oracle_stride)
+        times.append(full)
+    med = statistics.median(times)
+    fps = 1.0 / med
+    sample = (f"every {info['stride']}th pixel in x and y ({info['lattice_px']} px) composited after "
+              f"projecting all {sc.instances.n} instances in FP64; full-frame time extrapolated as "
+              f"project + {info['stride']}^2 x composite")
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": med * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                             "sample": sample, **{k: info[k] for k in ("project_s", "lattice_s")}},
+            "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, sc, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2501_17792_gb300 import binding, build
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    r = binding.Renderer(device=local_rank, stream=stream, stage_timing=True)
+    r.upload_templates(sc.templates)
+    r.set_lod(sc.lod)
+    n = sc.instances.n
+    from paper_2501_17792_gb300 import scene as S
+    frames = args.warmup + args.steps
+    # per-frame poses resident in HBM before the timed region (animated crowd)
+    poses = torch.stack([torch.from_numpy(S.random_poses(100 + 1000 * rank + f, n)) for f in range(frames)]).to(dev)
+    tid = torch.from_numpy(sc.instances.template_id).to(dev)
+    root = torch.from_numpy(sc.instances.root.reshape(n, 12)).to(dev)
+    out = torch.empty((sc.camera.height, sc.camera.width, 4), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step(f, stats=False):
+        with torch.cuda.stream(stream):
+            r.set_instances(tid, root, poses[f])
+            return r.render(sc.camera, out=out, stats=stats)
+
+    _, st0 = step(0, stats=True)
+    for f in range(args.warmup):
+        step(f)
+    torch.cuda.synchronize()
+    r.stage_times(average=True)  # restart the stage means at the timed region
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local_rank) if rank == 0 else None
+    if clk:
+        clk.start()
+        time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for f in range(args.warmup, frames):
+        step(f)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    stage_ms, stage_frames = r.stage_times(average=True)
+    clocks = clk.stop() if clk else None
+    t_local = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t_local.item())
+    ms_per_step = ms_max / args.steps
+    value = world * args.steps / (ms_max / 1e3)
+
+    # end to end through the C ABI with host buffers: pinned poses in, image out
+    h_pose = torch.empty((n, 24, 3), dtype=torch.float32).pin_memory()
+    h_img = torch.empty((sc.camera.height, sc.camera.width, 4), dtype=torch.float32).pin_memory()
+    h_tid = sc.instances.template_id.copy()
+    h_root = sc.instances.root.reshape(n, 12).copy()
+    host_poses = [S.random_poses(100 + 1000 * rank + f, n) for f in range(args.e2e_steps + 2)]
+    import ctypes as C
+    cam = binding.camera_struct(sc.camera)
+    L = binding.load()
+
+    def e2e_step(f):
+        h_pose.numpy()[...] = host_poses[f]
+        rc = L.cs_set_instances(r.h, n, h_tid.ctypes.data, h_root.ctypes.data, h_pose.data_ptr(), 0)
+        assert rc == 0, L.cs_last_error(r.h)
+        rc = L.cs_render_to_host(r.h, C.byref(cam), h_img.data_ptr(), None)
+        assert rc == 0, L.cs_last_error(r.h)
+
+    for f in range(2):
+        e2e_step(f)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for f in range(args.e2e_steps):
+        e2e_step(f + 2)
+    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.e2e_steps / float(t_e2e.item())
+    h2d = n * (4 + 48 + 24 * 3 * 4)
+    d2h = sc.camera.width * sc.camera.height * 16
+
+    if rank != 0:
+        return
+    pk = peaks()
+    pixels = sc.camera.width * sc.camera.height
+    sb = stage_bytes(st0, n, template_bytes(sc), pixels)
+    stages = {}
+    for name, ms in stage_ms.items():
+        gbs = sb[name] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        stages[name] = {"ms": round(ms, 4), "algo_bytes": int(sb[name]), "GB/s": round(gbs, 1),
+                        "frac": round(gbs / pk["hbm_gbs"], 4)}
+    top = max(stage_ms, key=lambda k: stage_ms[k])
+    prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))) if os.path.exists(
+        os.path.join(ROOT, "profiles", "traffic.json")) else {}
+    traffic = prof.get(top)
+    achieved = stages[top]["GB/s"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "templates": len(sc.templates), "gaussians_per_template": int(sc.templates[0].n),
+                   "sh_degree": int(sc.templates[0].sh_degree), "instances": n, "width": sc.camera.width,
+                   "height": sc.camera.height, "lod": {"thresholds_m": [10, 30], "fractions": [1, 0.25, 0.06]},
+                   "l2": "inputs larger than L2 (templates 231 MB, splat records > 1 GB per frame)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "frame": {"visible_instances": st0["instances_visible"], "per_level": st0["instances_per_level"][:3],
+                  "splats": st0["splats"], "pairs": st0["pairs"],
+                  "gaussians_per_s": st0["splats"] * value},
+        "stages": stages,
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
+                     "peak_source": f"{pk['src']} (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured" else "fallback"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(st0["kernel_launches"]) * args.steps,
+        "clocks": clocks,
+        "paper_context": {"fps": PAPER_FPS, "hardware": "RTX4090 + i9-13900", "note": "different workload, context only"},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        full, info = oracle_frame_time(sc, stride=args.oracle_stride)
+        line["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                                "sample": (f"every {info['stride']}th pixel in x and y ({info['lattice_px']} px) "
+                                           f"after FP64 projection of all {n} instances; full frame extrapolated "
+                                           f"(project {info['project_s']} s, lattice {info['lattice_s']} s)")}
+    print(json.dumps(line), flush=True)
+    r.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--oracle-stride", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="small crowd (debugging)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    from paper_2501_17792_gb300 import scene as S
+    if args.small:
+        sc = S.crowd(n_templates=2, n_gauss=4096, cols=10, rows=10, width=640, height=360)
+    else:
+        sc = S.crowd()
+    if args.impl == "reference":
+        run_reference(args, sc, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, sc, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

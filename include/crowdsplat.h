@@ -1,0 +1,222 @@
+/*
+ * crowdsplat.h -- C ABI of the GB300 (sm_103a) CrowdSplat crowd-synthesis
+ * library (libcrowdsplat.so).
+ *
+ * The library renders crowds of animated 3D-Gaussian avatars as CrowdSplat
+ * (arXiv 2501.17792) describes them: a few avatar templates whose Gaussian
+ * attributes are shared by every duplicated character (Sec. 1, third
+ * contribution; Sec. 2: only the posed means differ between characters of
+ * one template), each character animated by linear blend skinning (Fig. 2,
+ * Sec. 2), a distance-based level of detail (Sec. 2: fewer Gaussians farther
+ * from the camera), and the 3D Gaussian Splatting rasteriser the paper
+ * renders with (Sec. 1 and Sec. 2 cite Kerbl et al. 2023): EWA projection
+ * with spherical-harmonic colour, 16x16 tile binning, a (tile, depth) sort,
+ * front-to-back alpha compositing.
+ *
+ * Conventions
+ *   - Metres, right-handed.  Camera space is OpenCV-style: x right, y down,
+ *     z forward.  Pixel (i, j) has its centre at (i + 0.5, j + 0.5).
+ *   - Matrices are row-major float32.
+ *   - Every function returns CS_OK (0) or a CS_ERR_* code; the text of the
+ *     last error of a context is cs_last_error().  No C++ exception crosses
+ *     this boundary.  A context is not thread-safe: calls on one context
+ *     must not overlap.
+ *   - All GPU work is ordered on the context's stream (cs_create_params.stream).
+ *     cs_render returns when its work is enqueued, except for the two short
+ *     host reads of the frame's splat and pair counts that size its launches.
+ *   - Ownership: the library deep-copies every input before returning, so
+ *     the caller may free or reuse its buffers; outputs are caller-owned.
+ */
+#ifndef CROWDSPLAT_H
+#define CROWDSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define CS_OK 0
+#define CS_ERR_ARG 1      /* invalid argument (the message names it)           */
+#define CS_ERR_CUDA 2     /* a CUDA runtime call failed                        */
+#define CS_ERR_OOM 3      /* device or host allocation failed                  */
+#define CS_ERR_CAPACITY 4 /* a size exceeds a documented maximum               */
+#define CS_ERR_TIMEOUT 5  /* a bounded device wait gave up                     */
+#define CS_ERR_STATE 6    /* call out of order (e.g. render before upload)     */
+
+/* limits */
+#define CS_MAX_TEMPLATES 63
+#define CS_MAX_LEVELS 4
+#define CS_MAX_INSTANCES 131072
+#define CS_MAX_IMAGE_SIDE 4096
+#define CS_NUM_JOINTS 24
+#define CS_TILE 16
+
+/* skinning modes */
+#define CS_SKIN_FULL 0       /* LBS moves means and rotates covariances      */
+#define CS_SKIN_MEANS_ONLY 1 /* LBS moves means; covariances follow the root */
+
+/* frame of the SH viewing direction */
+#define CS_SH_ROOT_FRAME 0  /* direction expressed in the instance's root frame */
+#define CS_SH_WORLD_FRAME 1 /* direction in world coordinates                   */
+
+typedef struct cs_ctx cs_ctx; /* opaque, library-owned */
+
+typedef struct {
+    int32_t device;        /* CUDA device ordinal                                      */
+    void *stream;          /* cudaStream_t all work is ordered on; NULL = legacy default */
+    int32_t skin_mode;     /* CS_SKIN_FULL or CS_SKIN_MEANS_ONLY                       */
+    int32_t sh_frame;      /* CS_SH_ROOT_FRAME or CS_SH_WORLD_FRAME                    */
+    int32_t instance_cull; /* 1: drop instances whose every splat misses the image
+                              (conservative bound; never changes the image); 0: off */
+    int32_t stage_timing;  /* 1: record CUDA events per stage (cs_get_stage_times)     */
+} cs_create_params;
+
+/* One avatar template, all pointers HOST memory, read during the call.
+ * means[n*3] metres (template local frame); scales[n*3] metres (> 0);
+ * quats[n*4] (w,x,y,z), normalised by the library; opacity[n] in [0,1];
+ * sh[n*K*3] with K = (sh_degree+1)^2, coefficient-major per Gaussian
+ * (sh[(g*K + k)*3 + channel]); skin_idx[n*4] joint ids < 24; skin_w[n*4]
+ * non-negative, summing to 1 (+-1e-3); rest_joints[24*3] T-pose joint
+ * positions; parents[24] with parents[0] = -1 and parents[j] < j.
+ * The stored order defines the levels of detail: level l keeps the first
+ * N_l = round(fraction_l * n) Gaussians. */
+typedef struct {
+    int32_t n_gauss;
+    int32_t sh_degree; /* 0..3 */
+    const float *means;
+    const float *scales;
+    const float *quats;
+    const float *opacity;
+    const float *sh;
+    const uint8_t *skin_idx;
+    const float *skin_w;
+    const float *rest_joints;
+    const int32_t *parents;
+} cs_template_desc;
+
+/* Pinhole camera: x_cam = R x_world + t; u = fx x/z + cx, v = fy y/z + cy.
+ * Splats with view depth z <= near_z are culled. */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_z;
+} cs_camera;
+
+typedef struct {
+    int32_t instances;              /* instances set                                  */
+    int32_t instances_visible;      /* after the instance cull                        */
+    int32_t instances_per_level[CS_MAX_LEVELS];
+    int64_t splats;                 /* Gaussian-instances projected                   */
+    int64_t splats_live;            /* survived the per-splat culls (0 unless stats
+                                       were requested: costs one extra reduction)    */
+    int64_t pairs;                  /* (tile, splat) pairs sorted and blended         */
+    int32_t tiles_x, tiles_y;
+    int32_t kernel_launches;        /* CUDA kernels this frame launched               */
+} cs_frame_stats;
+
+typedef struct {
+    int64_t template_bytes;   /* shared template attributes (persistent)        */
+    int64_t instance_bytes;   /* per-instance state and FK output (persistent)  */
+    int64_t frame_bytes;      /* per-frame splat, sort and pair buffers         */
+    int64_t total_bytes;
+} cs_memory_stats_t;
+
+/* Create a context on p->device.  *out receives the handle (NULL on failure).
+ * Errors: CS_ERR_ARG (bad mode or device), CS_ERR_CUDA. */
+int cs_create(cs_ctx **out, const cs_create_params *p);
+
+/* Destroy a context and free its device memory (synchronises its stream).
+ * NULL is accepted. */
+void cs_destroy(cs_ctx *ctx);
+
+/* Upload the shared avatar templates (CrowdSplat Sec. 2: attributes other
+ * than the posed means are reused by every character of a template).
+ * Replaces any previous templates; resets the LoD to one full-detail level.
+ * Errors: CS_ERR_ARG (a field out of range: n_gauss < 1, sh_degree > 3,
+ * joint id > 23, negative weight, bad parents), CS_ERR_CAPACITY (more than
+ * CS_MAX_TEMPLATES), CS_ERR_OOM, CS_ERR_CUDA. */
+int cs_upload_templates(cs_ctx *ctx, int32_t n_templates, const cs_template_desc *templates);
+
+/* Distance level of detail (CrowdSplat Sec. 2).  Host arrays:
+ * dist_thresh[n_levels-1] ascending metres (an instance whose root is at
+ * distance d from the camera centre takes level = number of thresholds <= d);
+ * fraction[n_levels] in (0,1] (level l renders the first round(f_l * n)
+ * Gaussians of its template); scale_mult[n_levels] > 0 (level l multiplies
+ * every Gaussian scale by it).  Errors: CS_ERR_ARG, CS_ERR_STATE (no
+ * templates). */
+int cs_set_lod(cs_ctx *ctx, int32_t n_levels, const float *dist_thresh, const float *fraction,
+               const float *scale_mult);
+
+/* Per-frame instance state (CrowdSplat Sec. 2, stage 2: duplicated
+ * characters, each with its template and pose).  template_id[n];
+ * root[n*12] row-major 3x4 rigid [R|t] from template-local to world
+ * coordinates; joint_pose[n*24*3] axis-angle radians per joint.
+ * on_device = 0: host pointers (copied host->device on the stream, the call
+ * returns once the copy is staged); 1: device pointers (device->device copy).
+ * Roots must be rigid (the instance cull assumes unit scale).
+ * Errors: CS_ERR_ARG (n < 0, template id out of range when host pointers),
+ * CS_ERR_CAPACITY (n > CS_MAX_INSTANCES), CS_ERR_STATE, CS_ERR_OOM, CS_ERR_CUDA. */
+int cs_set_instances(cs_ctx *ctx, int32_t n, const int32_t *template_id, const float *root,
+                     const float *joint_pose, int32_t on_device);
+
+/* Render one frame of the current instances (the whole hot path: forward
+ * kinematics, LoD + cull, LBS + EWA projection + SH colour, tile binning,
+ * (tile, depth) sort, compositing).  rgba_out: caller-owned DEVICE buffer of
+ * height*width*4 float32, row-major, premultiplied RGB on a black background
+ * and alpha = 1 - final transmittance.  stats may be NULL.
+ * Errors: CS_ERR_ARG (image side < 1 or > CS_MAX_IMAGE_SIDE, non-positive
+ * focal length or near plane, NULL or not 16-byte aligned output), CS_ERR_STATE (no templates or
+ * instances), CS_ERR_OOM, CS_ERR_CUDA. */
+int cs_render(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats);
+
+/* cs_render into an internal device buffer followed by a device->host copy
+ * of the image into rgba_host (HOST memory, pinned for full speed); returns
+ * after the copy completes.  Same errors as cs_render. */
+int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_frame_stats *stats);
+
+/* Per-stage milliseconds (needs stage_timing = 1), measured with CUDA events
+ * on the context's stream: ms[0..n) = fk, cull+lod, skin+project, depth
+ * sort, pair emit, tile sort, tile ranges, blend.  average = 0: the last
+ * frame (waits for it); average = 1: the mean over every frame rendered
+ * since the previous average call (waits for the last one), then restarts
+ * the mean.  *frames_out (may be NULL) receives the number of frames
+ * covered.  Returns the number of stages written, or -CS_ERR_* on error
+ * (-CS_ERR_STATE when no timed frame exists). */
+int cs_get_stage_times(cs_ctx *ctx, float *ms, int32_t n, int32_t average, int64_t *frames_out);
+
+/* Device memory held by the context (CrowdSplat Table 1 accounting). */
+int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out);
+
+/* Text of the last error on this context ("" if none); valid until the
+ * next call on the context. */
+const char *cs_last_error(const cs_ctx *ctx);
+
+/* Copy an internal buffer of the last frame to HOST memory (testing and
+ * diagnosis).  which = CS_DBG_*; copies min(bytes, size) bytes and stores
+ * the buffer's full size in *size_out (may be NULL).  Synchronises. */
+#define CS_DBG_SKIN_B 1      /* float [I][24][12]: skinning transforms, instance-local */
+#define CS_DBG_VISIBLE 2     /* int32 [V]: visible instance ids in group order         */
+#define CS_DBG_GROUPS 3      /* int32 [G][6]: template, level, first slot, slots,
+                                gaussians per slot, first splat                        */
+#define CS_DBG_RECORDS 4     /* float [S][12]: u, v, conic A, B, C, opacity, radius,
+                                depth, r, g, b, 0                                      */
+#define CS_DBG_DEPTH_KEYS 5  /* uint32 [S]: depth bits in depth order, 0xFFFFFFFF = culled */
+#define CS_DBG_RECTS 6       /* uint16 [S][4]: tile rect x0, y0, x1, y1 (inclusive)    */
+#define CS_DBG_DEPTH_ORDER 7 /* uint32 [S]: splat ids sorted by depth                  */
+#define CS_DBG_PAIR_TILES 8  /* uint16 [P]: tile of each pair, (tile, depth) order     */
+#define CS_DBG_PAIR_SPLATS 9 /* uint32 [P]: splat of each pair, (tile, depth) order    */
+#define CS_DBG_TILE_RANGES 10 /* uint32 [T][2]: [start, end) of each tile's pairs      */
+int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size_t *size_out);
+
+/* Library version string. */
+const char *cs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CROWDSPLAT_H */

@@ -1,0 +1,278 @@
+"""Thin Python binding of libcrowdsplat.so (argument marshalling only).
+
+Every function of ``include/crowdsplat.h`` is reachable under the same name
+through :func:`lib`; :class:`Renderer` wraps a context with PyTorch device
+memory and streams.  All computation runs in the library's CUDA kernels:
+there is no CPU path, and :func:`load` raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+CS_OK, CS_ERR_ARG, CS_ERR_CUDA, CS_ERR_OOM, CS_ERR_CAPACITY, CS_ERR_TIMEOUT, CS_ERR_STATE = range(7)
+CS_SKIN_FULL, CS_SKIN_MEANS_ONLY = 0, 1
+CS_SH_ROOT_FRAME, CS_SH_WORLD_FRAME = 0, 1
+DBG = dict(skin_b=1, visible=2, groups=3, records=4, depth_keys=5, rects=6, depth_order=7,
+           pair_tiles=8, pair_splats=9, tile_ranges=10)
+STAGES = ("fk", "cull_lod", "skin_project", "depth_sort", "pair_emit", "tile_sort", "tile_ranges",
+          "blend")
+
+
+class CreateParams(C.Structure):
+    _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("skin_mode", C.c_int32),
+                ("sh_frame", C.c_int32), ("instance_cull", C.c_int32), ("stage_timing", C.c_int32)]
+
+
+class TemplateDesc(C.Structure):
+    _fields_ = [("n_gauss", C.c_int32), ("sh_degree", C.c_int32), ("means", C.c_void_p),
+                ("scales", C.c_void_p), ("quats", C.c_void_p), ("opacity", C.c_void_p),
+                ("sh", C.c_void_p), ("skin_idx", C.c_void_p), ("skin_w", C.c_void_p),
+                ("rest_joints", C.c_void_p), ("parents", C.c_void_p)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("near_z", C.c_float)]
+
+
+class FrameStats(C.Structure):
+    _fields_ = [("instances", C.c_int32), ("instances_visible", C.c_int32),
+                ("instances_per_level", C.c_int32 * 4), ("splats", C.c_int64),
+                ("splats_live", C.c_int64), ("pairs", C.c_int64), ("tiles_x", C.c_int32),
+                ("tiles_y", C.c_int32), ("kernel_launches", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return dict(instances=self.instances, instances_visible=self.instances_visible,
+                    instances_per_level=list(self.instances_per_level), splats=self.splats,
+                    splats_live=self.splats_live, pairs=self.pairs, tiles_x=self.tiles_x,
+                    tiles_y=self.tiles_y, kernel_launches=self.kernel_launches)
+
+
+class MemoryStats(C.Structure):
+    _fields_ = [("template_bytes", C.c_int64), ("instance_bytes", C.c_int64),
+                ("frame_bytes", C.c_int64), ("total_bytes", C.c_int64)]
+
+
+_lib = None
+
+# name -> (restype, argtypes) for every function of include/crowdsplat.h
+_P = C.c_void_p
+SIGNATURES = {
+    "cs_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(CreateParams)]),
+    "cs_destroy": (None, [_P]),
+    "cs_upload_templates": (C.c_int, [_P, C.c_int32, C.POINTER(TemplateDesc)]),
+    "cs_set_lod": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "cs_set_instances": (C.c_int, [_P, C.c_int32, _P, _P, _P, C.c_int32]),
+    "cs_render": (C.c_int, [_P, C.POINTER(Camera), _P, C.POINTER(FrameStats)]),
+    "cs_render_to_host": (C.c_int, [_P, C.POINTER(Camera), _P, C.POINTER(FrameStats)]),
+    "cs_get_stage_times": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]),
+    "cs_memory_stats": (C.c_int, [_P, C.POINTER(MemoryStats)]),
+    "cs_last_error": (C.c_char_p, [_P]),
+    "cs_debug_read": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "cs_version": (C.c_char_p, []),
+}
+
+
+def load(path: str | None = None):
+    """Load libcrowdsplat.so; raises RuntimeError if it has not been built."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it first (python -m paper_2501_17792_gb300.build "
+                               "or __graft_entry__.build()); there is no CPU fallback")
+        L = C.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+lib = load
+
+
+class CrowdSplatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"crowdsplat error {code}: {msg}")
+        self.code = code
+
+
+def camera_struct(cam) -> Camera:
+    """Camera from an object with R, t, fx, fy, cx, cy, width, height, near."""
+    c = Camera()
+    R = np.asarray(cam.R, np.float32).reshape(9)
+    t = np.asarray(cam.t, np.float32).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.near_z = float(getattr(cam, "near", 0.2))
+    return c
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Renderer:
+    """One library context on one CUDA device.
+
+    Device memory and streams come from PyTorch: ``render`` writes into a
+    torch CUDA tensor on the context's stream (the current torch stream at
+    creation unless ``stream`` is given).
+    """
+
+    def __init__(self, device: int = 0, stream=None, skin_mode: int = CS_SKIN_FULL,
+                 sh_frame: int = CS_SH_ROOT_FRAME, instance_cull: bool = True,
+                 stage_timing: bool = False):
+        import torch
+        self.torch = torch
+        self.L = load()
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        p = CreateParams(device=self.device, stream=C.c_void_p(int(stream.cuda_stream)),
+                         skin_mode=int(skin_mode), sh_frame=int(sh_frame),
+                         instance_cull=1 if instance_cull else 0,
+                         stage_timing=1 if stage_timing else 0)
+        h = C.c_void_p()
+        rc = self.L.cs_create(C.byref(h), C.byref(p))
+        if rc != CS_OK:
+            raise CrowdSplatError(rc, "cs_create failed")
+        self.h = h
+        self._keep = []
+
+    # -- helpers ----------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != CS_OK:
+            raise CrowdSplatError(rc, self.L.cs_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.cs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API ---------------------------------------------------------------
+    def upload_templates(self, templates):
+        descs = (TemplateDesc * len(templates))()
+        keep = []
+        for k, t in enumerate(templates):
+            arrs = [_host(t.means, np.float32), _host(t.scales, np.float32), _host(t.quats, np.float32),
+                    _host(t.opacity, np.float32), _host(t.sh, np.float32), _host(t.skin_idx, np.uint8),
+                    _host(t.skin_w, np.float32), _host(t.rest_joints, np.float32),
+                    _host(t.parents, np.int32)]
+            keep.append(arrs)
+            d = descs[k]
+            d.n_gauss = int(arrs[0].shape[0])
+            d.sh_degree = int(t.sh_degree)
+            (d.means, d.scales, d.quats, d.opacity, d.sh, d.skin_idx, d.skin_w, d.rest_joints,
+             d.parents) = (a.ctypes.data for a in arrs)
+        self._check(self.L.cs_upload_templates(self.h, len(templates), descs))
+
+    def set_lod(self, lod):
+        thr = _host(lod.thresholds, np.float32)
+        frac = _host(lod.fractions, np.float32)
+        mult = _host(lod.scale_mult, np.float32)
+        n = int(frac.shape[0])
+        self._check(self.L.cs_set_lod(self.h, n, thr.ctypes.data if thr.size else None,
+                                      frac.ctypes.data, mult.ctypes.data))
+
+    def set_instances(self, template_id, root, pose):
+        """Host arrays (numpy, or CPU tensors) or CUDA tensors on this device."""
+        torch = self.torch
+        if isinstance(root, torch.Tensor) and root.is_cuda:
+            tid = template_id.to(torch.int32).contiguous()
+            r = root.to(torch.float32).contiguous()
+            p = pose.to(torch.float32).contiguous()
+            self._check(self.L.cs_set_instances(self.h, int(tid.shape[0]), tid.data_ptr(), r.data_ptr(),
+                                                p.data_ptr(), 1))
+            self._keep = [tid, r, p]  # keep alive until the stream has copied them
+            return
+        tid = _host(np.asarray(template_id), np.int32)
+        r = _host(np.asarray(root), np.float32)
+        p = _host(np.asarray(pose), np.float32)
+        self._check(self.L.cs_set_instances(self.h, int(tid.shape[0]), tid.ctypes.data, r.ctypes.data,
+                                            p.ctypes.data, 0))
+        self._keep = [tid, r, p]
+
+    def render(self, camera, out=None, stats: bool = False):
+        """Render into a CUDA tensor [H, W, 4] float32 (allocated if None)."""
+        torch = self.torch
+        cam = camera_struct(camera)
+        if out is None:
+            with torch.cuda.stream(self.stream):
+                out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32,
+                                  device=f"cuda:{self.device}")
+        st = FrameStats()
+        self._check(self.L.cs_render(self.h, C.byref(cam), out.data_ptr(), C.byref(st) if stats else None))
+        return (out, st.as_dict()) if stats else out
+
+    def render_to_host(self, camera, out: np.ndarray | None = None, stats: bool = False):
+        cam = camera_struct(camera)
+        if out is None:
+            out = np.empty((cam.height, cam.width, 4), np.float32)
+        st = FrameStats()
+        self._check(self.L.cs_render_to_host(self.h, C.byref(cam), out.ctypes.data,
+                                             C.byref(st) if stats else None))
+        return (out, st.as_dict()) if stats else out
+
+    def stage_times(self, average: bool = False):
+        """Per-stage ms of the last frame, or (average=True) the mean over the
+        frames since the previous average call; returns (dict, frames)."""
+        ms = (C.c_float * len(STAGES))()
+        frames = C.c_int64()
+        n = self.L.cs_get_stage_times(self.h, ms, len(STAGES), 1 if average else 0, C.byref(frames))
+        if n < 0:
+            self._check(-n)
+        return {STAGES[i]: float(ms[i]) for i in range(n)}, int(frames.value)
+
+    def memory_stats(self) -> dict:
+        m = MemoryStats()
+        self._check(self.L.cs_memory_stats(self.h, C.byref(m)))
+        return dict(template_bytes=m.template_bytes, instance_bytes=m.instance_bytes,
+                    frame_bytes=m.frame_bytes, total_bytes=m.total_bytes)
+
+    def debug(self, which: str) -> np.ndarray:
+        code = DBG[which]
+        size = C.c_size_t()
+        self._check(self.L.cs_debug_read(self.h, code, None, 0, C.byref(size)))
+        buf = np.empty(size.value, np.uint8)
+        if size.value:
+            self._check(self.L.cs_debug_read(self.h, code, buf.ctypes.data, size.value, None))
+        dt = {"skin_b": np.float32, "visible": np.int32, "groups": np.int32, "records": np.float32,
+              "depth_keys": np.uint32, "rects": np.uint16, "depth_order": np.uint32,
+              "pair_tiles": np.uint16, "pair_splats": np.uint32, "tile_ranges": np.uint32}[which]
+        a = buf.view(dt)
+        shape = {"skin_b": (-1, 24, 3, 4), "groups": (-1, 6), "records": (-1, 12), "rects": (-1, 4),
+                 "tile_ranges": (-1, 2)}.get(which)
+        return a.reshape(shape) if shape else a
+
+
+def render_scene(scene, *, device: int = 0, **kw):
+    """Convenience: upload a scene object (templates, instances, camera, lod)
+    and render one frame; returns (renderer, image tensor)."""
+    r = Renderer(device=device, **kw)
+    r.upload_templates(scene.templates)
+    r.set_lod(scene.lod)
+    r.set_instances(scene.instances.template_id, scene.instances.root, scene.instances.pose)
+    img = r.render(scene.camera)
+    return r, img

@@ -1,0 +1,780 @@
+// cs_api.cu -- the C ABI of libcrowdsplat.so (declared in include/crowdsplat.h):
+// context and device-memory management, template upload, LoD and
+// per-frame instance state, and the ordering of one frame's kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/crowdsplat.h"
+#include "cs_internal.cuh"
+
+using namespace cs;
+
+namespace {
+
+constexpr int kStages = 8;
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;  // elements
+};
+
+}  // namespace
+
+struct cs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int skin_mode = 0, sh_frame = 0, instance_cull = 1, stage_timing = 0;
+    std::string err;
+
+    // templates
+    int n_tpl = 0;
+    std::vector<TemplateInfo> tpl_host;
+    std::vector<std::vector<float>> reach_g, smax_g;  // per Gaussian, for LoD bounds
+    TemplateInfo *d_tpl = nullptr;
+    float4 *d_mean_op = nullptr, *d_cov_a = nullptr, *d_skin_w = nullptr, *d_sh = nullptr;
+    float2 *d_cov_b = nullptr;
+    uint32_t *d_skin_i = nullptr;
+    size_t n_gauss_total = 0, sh_planes_total = 0;
+    int max_depth = 0;
+
+    // LoD
+    LodParams lod{};
+    float lod_frac[kMaxLevels] = {1, 1, 1, 1};
+
+    // instances
+    int n_inst = 0;
+    DevBuf<int32_t> tid, vis;
+    DevBuf<float> root, pose, B, V, Cloc;
+    std::vector<int32_t> tid_host_check;
+    DevBuf<Group> groups;
+    int32_t *d_meta = nullptr, *h_meta = nullptr;  // pinned mirror
+    uint32_t *h_pairs = nullptr;                   // pinned
+
+    // per-frame buffers
+    DevBuf<float4> rec;
+    DevBuf<uint32_t> key, ids, key2, ids2, ntiles, pair_off, pval, pval2, scratch;
+    DevBuf<uint2> rect, ranges;
+    DevBuf<uint16_t> ptile, ptile2;
+    DevBuf<float4> img;  // for cs_render_to_host
+
+    // last frame
+    int64_t S = 0, P = 0;
+    int n_groups = 0, visible = 0, tiles_x = 0, tiles_y = 0;
+    int order_buf = 0, pair_buf = 0;  // which ping-pong half holds the result
+    int per_level[kMaxLevels] = {0, 0, 0, 0};
+    int launches = 0;  // kernels launched by the last cs_render
+    // stage timing: two event sets used by alternate frames, so a frame's
+    // events are read (without waiting) two frames later
+    cudaEvent_t ev[2][kStages + 1] = {};
+    int ev_cur = 0;           // set used by the last timed frame
+    bool ev_pending[2] = {false, false};
+    double stage_sum[kStages] = {};
+    int64_t stage_frames = 0;
+    bool timed = false;
+};
+
+namespace {
+
+int fail(cs_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define CS_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? CS_ERR_OOM : CS_ERR_CUDA,    \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
+                        __LINE__);                                                          \
+        }                                                                                   \
+    } while (0)
+
+#define CS_TRY(expr)              \
+    do {                          \
+        int r_ = (expr);          \
+        if (r_ != CS_OK) return r_; \
+    } while (0)
+
+template <typename T>
+int ensure(cs_ctx *ctx, DevBuf<T> &b, size_t n, const char *what) {
+    if (n <= b.cap && b.p) return CS_OK;
+    size_t cap = std::max<size_t>(n + n / 4, 1024);
+    if (b.p) {
+        CS_CUDA(cudaStreamSynchronize(ctx->stream));
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, cap * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(ctx, CS_ERR_OOM, "allocating %s (%zu bytes): %s", what, cap * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    b.cap = cap;
+    return CS_OK;
+}
+
+template <typename T>
+void release(DevBuf<T> &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+template <typename T>
+size_t bytes_of(const DevBuf<T> &b) {
+    return b.cap * sizeof(T);
+}
+
+void free_templates(cs_ctx *c) {
+    cudaFree(c->d_tpl);
+    cudaFree(c->d_mean_op);
+    cudaFree(c->d_cov_a);
+    cudaFree(c->d_cov_b);
+    cudaFree(c->d_skin_w);
+    cudaFree(c->d_skin_i);
+    cudaFree(c->d_sh);
+    c->d_tpl = nullptr;
+    c->d_mean_op = c->d_cov_a = c->d_skin_w = c->d_sh = nullptr;
+    c->d_cov_b = nullptr;
+    c->d_skin_i = nullptr;
+    c->n_tpl = 0;
+    c->n_gauss_total = c->sh_planes_total = 0;
+}
+
+// Level sizes and instance-cull bounds of every template for the current LoD.
+void refresh_lod_bounds(cs_ctx *c) {
+    for (int t = 0; t < c->n_tpl; ++t) {
+        TemplateInfo &T = c->tpl_host[t];
+        for (int l = 0; l < kMaxLevels; ++l) {
+            int lvl = l < c->lod.n_levels ? l : c->lod.n_levels - 1;
+            double cnt = std::floor((double)c->lod_frac[lvl] * (double)T.n + 0.5);
+            int n = (int)std::min<double>(std::max<double>(cnt, 0.0), (double)T.n);
+            T.n_level[l] = n;
+            float reach = 0.f, smax = 0.f;
+            for (int g = 0; g < n; ++g) {
+                reach = std::max(reach, c->reach_g[t][g]);
+                smax = std::max(smax, c->smax_g[t][g]);
+            }
+            T.reach[l] = reach;
+            T.sigma_max[l] = smax * c->lod.mult[lvl];
+        }
+    }
+}
+
+int push_templates(cs_ctx *ctx) {
+    CS_CUDA(cudaMemcpyAsync(ctx->d_tpl, ctx->tpl_host.data(), sizeof(TemplateInfo) * ctx->n_tpl,
+                            cudaMemcpyHostToDevice, ctx->stream));
+    CS_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CS_OK;
+}
+
+void cam_params(const cs_ctx *c, const cs_camera *cam, CamParams &p) {
+    for (int i = 0; i < 9; ++i) p.R[i] = cam->R[i];
+    for (int i = 0; i < 3; ++i) p.t[i] = cam->t[i];
+    p.fx = cam->fx;
+    p.fy = cam->fy;
+    p.cx = cam->cx;
+    p.cy = cam->cy;
+    p.W = cam->width;
+    p.H = cam->height;
+    p.near_z = cam->near_z;
+    for (int i = 0; i < 3; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k) s -= (double)cam->R[k * 3 + i] * (double)cam->t[k];
+        p.center[i] = (float)s;
+    }
+    p.limx = (float)(1.3 * (0.5 * cam->width) / (double)cam->fx);
+    p.limy = (float)(1.3 * (0.5 * cam->height) / (double)cam->fy);
+    p.tiles_x = (cam->width + kTile - 1) / kTile;
+    p.tiles_y = (cam->height + kTile - 1) / kTile;
+    // Conservative instance cull.  A splat's support half-width is at most
+    // 3 |J| sigma + 3 sqrt(0.3 + sqrt(0.1)) + 1 px with
+    // |J| <= (f_max / z) sqrt(2 + limx^2 + limy^2); the pixel term becomes a
+    // margin on the side planes, the sigma term a growth of the bounding
+    // sphere (in metres, scaled by f_max / f_min for the plane's own focal).
+    const double margin = 3.0 * std::sqrt(0.3 + std::sqrt(0.1)) + 1.0 + 2.0;
+    const double fmax = std::max(cam->fx, cam->fy), fmin = std::min(cam->fx, cam->fy);
+    p.cull_sigma_k = (float)(3.0 * std::sqrt(2.0 + (double)p.limx * p.limx + (double)p.limy * p.limy) *
+                             (fmax / fmin) * 1.01);
+    const double tr = (cam->width - cam->cx + margin) / cam->fx;
+    const double tl = (cam->cx + margin) / cam->fx;
+    const double tb = (cam->height - cam->cy + margin) / cam->fy;
+    const double tt = (cam->cy + margin) / cam->fy;
+    const double planes[4][3] = {{1, 0, -tr}, {-1, 0, -tl}, {0, 1, -tb}, {0, -1, -tt}};
+    for (int k = 0; k < 4; ++k) {
+        double n = std::sqrt(planes[k][0] * planes[k][0] + planes[k][1] * planes[k][1] +
+                             planes[k][2] * planes[k][2]);
+        for (int e = 0; e < 3; ++e) p.plane[k][e] = (float)(planes[k][e] / n);
+        p.plane[k][3] = 0.f;
+    }
+}
+
+// Add the stage times of event set k (a completed frame) to the running sums.
+int accumulate_stage_times(cs_ctx *ctx, int k) {
+    if (!ctx->ev_pending[k]) return CS_OK;
+    CS_CUDA(cudaEventSynchronize(ctx->ev[k][kStages]));
+    for (int i = 0; i < kStages; ++i) {
+        float t = 0.f;
+        CS_CUDA(cudaEventElapsedTime(&t, ctx->ev[k][i], ctx->ev[k][i + 1]));
+        ctx->stage_sum[i] += t;
+    }
+    ctx->stage_frames += 1;
+    ctx->ev_pending[k] = false;
+    return CS_OK;
+}
+
+int bits_for(uint32_t n_values) {
+    int b = 0;
+    while (b < 32 && (1ull << b) < n_values) ++b;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cs_version(void) { return "crowdsplat-gb300 0.1 (sm_103a)"; }
+
+const char *cs_last_error(const cs_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int cs_create(cs_ctx **out, const cs_create_params *p) {
+    if (!out || !p) return CS_ERR_ARG;
+    *out = nullptr;
+    if (p->skin_mode != CS_SKIN_FULL && p->skin_mode != CS_SKIN_MEANS_ONLY) return CS_ERR_ARG;
+    if (p->sh_frame != CS_SH_ROOT_FRAME && p->sh_frame != CS_SH_WORLD_FRAME) return CS_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return CS_ERR_CUDA;
+    }
+    if (p->device < 0 || p->device >= ndev) return CS_ERR_ARG;
+    cs_ctx *ctx = new (std::nothrow) cs_ctx();
+    if (!ctx) return CS_ERR_OOM;
+    ctx->device = p->device;
+    ctx->stream = (cudaStream_t)p->stream;
+    ctx->skin_mode = p->skin_mode;
+    ctx->sh_frame = p->sh_frame;
+    ctx->instance_cull = p->instance_cull ? 1 : 0;
+    ctx->stage_timing = p->stage_timing ? 1 : 0;
+    ctx->lod.n_levels = 1;
+    for (int l = 0; l < kMaxLevels; ++l) ctx->lod.mult[l] = 1.0f;
+    int rc = CS_OK;
+    do {
+        if (cudaSetDevice(ctx->device) != cudaSuccess) { rc = CS_ERR_CUDA; break; }
+        if (cudaMalloc(&ctx->d_meta, kMetaWords * sizeof(int32_t)) != cudaSuccess) { rc = CS_ERR_OOM; break; }
+        if (cudaHostAlloc(&ctx->h_meta, kMetaWords * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) { rc = CS_ERR_OOM; break; }
+        if (cudaHostAlloc(&ctx->h_pairs, 4 * sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) { rc = CS_ERR_OOM; break; }
+        for (int k = 0; k < 2 && rc == CS_OK; ++k)
+            for (int i = 0; i <= kStages; ++i)
+                if (cudaEventCreate(&ctx->ev[k][i]) != cudaSuccess) { rc = CS_ERR_CUDA; break; }
+    } while (0);
+    if (rc != CS_OK) {
+        cudaGetLastError();
+        cs_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return CS_OK;
+}
+
+void cs_destroy(cs_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_templates(ctx);
+    release(ctx->tid); release(ctx->vis); release(ctx->root); release(ctx->pose);
+    release(ctx->B); release(ctx->V); release(ctx->Cloc); release(ctx->groups);
+    release(ctx->rec); release(ctx->key); release(ctx->ids); release(ctx->key2); release(ctx->ids2);
+    release(ctx->ntiles); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
+    release(ctx->scratch); release(ctx->rect); release(ctx->ranges); release(ctx->ptile);
+    release(ctx->ptile2); release(ctx->img);
+    if (ctx->d_meta) cudaFree(ctx->d_meta);
+    if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
+    if (ctx->h_pairs) cudaFreeHost(ctx->h_pairs);
+    for (int k = 0; k < 2; ++k)
+        for (int i = 0; i <= kStages; ++i)
+            if (ctx->ev[k][i]) cudaEventDestroy(ctx->ev[k][i]);
+    cudaGetLastError();
+    delete ctx;
+}
+
+int cs_upload_templates(cs_ctx *ctx, int32_t n_templates, const cs_template_desc *tp) {
+    if (!ctx) return CS_ERR_ARG;
+    if (n_templates < 1 || !tp) return fail(ctx, CS_ERR_ARG, "n_templates must be >= 1");
+    if (n_templates > CS_MAX_TEMPLATES)
+        return fail(ctx, CS_ERR_CAPACITY, "n_templates %d exceeds %d", n_templates, CS_MAX_TEMPLATES);
+    CS_CUDA(cudaSetDevice(ctx->device));
+    // validate and lay out
+    std::vector<TemplateInfo> info(n_templates);
+    size_t g_total = 0, planes_total = 0;
+    int max_depth = 0;
+    for (int t = 0; t < n_templates; ++t) {
+        const cs_template_desc &d = tp[t];
+        if (d.n_gauss < 1) return fail(ctx, CS_ERR_ARG, "template %d: n_gauss must be >= 1", t);
+        if (d.sh_degree < 0 || d.sh_degree > 3)
+            return fail(ctx, CS_ERR_ARG, "template %d: sh_degree must be 0..3", t);
+        if (!d.means || !d.scales || !d.quats || !d.opacity || !d.sh || !d.skin_idx || !d.skin_w ||
+            !d.rest_joints || !d.parents)
+            return fail(ctx, CS_ERR_ARG, "template %d: NULL array", t);
+        TemplateInfo &T = info[t];
+        memset(&T, 0, sizeof T);
+        T.g_off = (int32_t)g_total;
+        T.n = d.n_gauss;
+        T.sh_deg = d.sh_degree;
+        int K = (d.sh_degree + 1) * (d.sh_degree + 1);
+        T.sh_planes = (K * 3 + 3) / 4;
+        T.sh_off = (int64_t)planes_total;
+        for (int j = 0; j < kJoints; ++j) {
+            int par = d.parents[j];
+            if ((j == 0 && par != -1) || (j > 0 && (par < 0 || par >= j)))
+                return fail(ctx, CS_ERR_ARG, "template %d: parents[%d] = %d (need -1 for the root, "
+                            "0 <= parent < j otherwise)", t, j, par);
+            T.parent[j] = (int8_t)par;
+            T.depth[j] = (int8_t)(par < 0 ? 0 : T.depth[par] + 1);
+            max_depth = std::max(max_depth, (int)T.depth[j]);
+            for (int e = 0; e < 3; ++e) T.rest[j * 3 + e] = d.rest_joints[j * 3 + e];
+        }
+        g_total += (size_t)d.n_gauss;
+        planes_total += (size_t)T.sh_planes * (size_t)d.n_gauss;
+        if (g_total >= (size_t)INT32_MAX)
+            return fail(ctx, CS_ERR_CAPACITY, "total Gaussians exceed 2^31 - 1");
+    }
+    // host staging in the device layout, plus per-Gaussian cull bounds
+    std::vector<float4> mean_op(g_total), cov_a(g_total), skin_w(g_total), sh(planes_total);
+    std::vector<float2> cov_b(g_total);
+    std::vector<uint32_t> skin_i(g_total);
+    std::vector<std::vector<float>> reach(n_templates), smax(n_templates);
+    for (int t = 0; t < n_templates; ++t) {
+        const cs_template_desc &d = tp[t];
+        TemplateInfo &T = info[t];
+        // chain length of each joint: sum of bone lengths up to the root
+        double chain[kJoints];
+        for (int j = 0; j < kJoints; ++j) {
+            if (T.parent[j] < 0) {
+                chain[j] = 0.0;
+                continue;
+            }
+            int p = T.parent[j];
+            double dx = T.rest[j * 3] - T.rest[p * 3], dy = T.rest[j * 3 + 1] - T.rest[p * 3 + 1],
+                   dz = T.rest[j * 3 + 2] - T.rest[p * 3 + 2];
+            chain[j] = chain[p] + std::sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        int K = (d.sh_degree + 1) * (d.sh_degree + 1);
+        reach[t].resize(d.n_gauss);
+        smax[t].resize(d.n_gauss);
+        for (int g = 0; g < d.n_gauss; ++g) {
+            size_t gi = (size_t)T.g_off + g;
+            double m[3] = {d.means[g * 3], d.means[g * 3 + 1], d.means[g * 3 + 2]};
+            double o = d.opacity[g];
+            if (!(o >= 0.0 && o <= 1.0)) return fail(ctx, CS_ERR_ARG, "template %d: opacity[%d] not in [0,1]", t, g);
+            mean_op[gi] = make_float4(d.means[g * 3], d.means[g * 3 + 1], d.means[g * 3 + 2], d.opacity[g]);
+            // canonical covariance R S S^T R^T in double, stored in float
+            double q[4] = {d.quats[g * 4], d.quats[g * 4 + 1], d.quats[g * 4 + 2], d.quats[g * 4 + 3]};
+            double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+            if (!(qn > 0.0) || !std::isfinite(qn)) return fail(ctx, CS_ERR_ARG, "template %d: quats[%d] has zero norm", t, g);
+            double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+            double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                           2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                           2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+            double s[3] = {d.scales[g * 3], d.scales[g * 3 + 1], d.scales[g * 3 + 2]};
+            if (!(s[0] > 0 && s[1] > 0 && s[2] > 0)) return fail(ctx, CS_ERR_ARG, "template %d: scales[%d] must be > 0", t, g);
+            double C[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double a = 0.0;
+                    for (int k = 0; k < 3; ++k) a += R[i * 3 + k] * s[k] * s[k] * R[j * 3 + k];
+                    C[i * 3 + j] = a;
+                }
+            cov_a[gi] = make_float4((float)C[0], (float)C[1], (float)C[2], (float)C[4]);
+            cov_b[gi] = make_float2((float)C[5], (float)C[8]);
+            double wsum = 0.0, r = 0.0;
+            uint32_t packed = 0;
+            for (int k = 0; k < 4; ++k) {
+                int j = d.skin_idx[g * 4 + k];
+                float wk = d.skin_w[g * 4 + k];
+                if (j >= kJoints) return fail(ctx, CS_ERR_ARG, "template %d: skin_idx[%d] >= 24", t, g);
+                if (!(wk >= 0.0f)) return fail(ctx, CS_ERR_ARG, "template %d: negative skin weight at %d", t, g);
+                wsum += wk;
+                packed |= (uint32_t)j << (8 * k);
+                double dx = m[0] - T.rest[j * 3], dy = m[1] - T.rest[j * 3 + 1], dz = m[2] - T.rest[j * 3 + 2];
+                if (wk > 0.0f) r = std::max(r, std::sqrt(dx * dx + dy * dy + dz * dz) + chain[j]);
+            }
+            if (std::fabs(wsum - 1.0) > 1e-3)
+                return fail(ctx, CS_ERR_ARG, "template %d: skin weights of %d sum to %g (need 1 +- 1e-3)", t, g, wsum);
+            skin_w[gi] = make_float4(d.skin_w[g * 4], d.skin_w[g * 4 + 1], d.skin_w[g * 4 + 2], d.skin_w[g * 4 + 3]);
+            skin_i[gi] = packed;
+            // weights summing to 1 + e can push the blend out by e |pelvis|
+            double pel = std::sqrt((double)T.rest[0] * T.rest[0] + (double)T.rest[1] * T.rest[1] + (double)T.rest[2] * T.rest[2]);
+            reach[t][g] = (float)((r + std::fabs(wsum - 1.0) * (pel + r)) * wsum + 1e-6);
+            smax[t][g] = (float)(std::max(s[0], std::max(s[1], s[2])) * std::max(1.0, wsum));
+            const float *shg = d.sh + (size_t)g * K * 3;
+            for (int pl = 0; pl < T.sh_planes; ++pl) {
+                float v[4];
+                for (int e = 0; e < 4; ++e) {
+                    int f = pl * 4 + e;
+                    v[e] = f < K * 3 ? shg[f] : 0.0f;
+                }
+                sh[(size_t)T.sh_off + (size_t)pl * T.n + g] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    }
+    // device copies
+    CS_CUDA(cudaStreamSynchronize(ctx->stream));
+    free_templates(ctx);
+    CS_CUDA(cudaMalloc(&ctx->d_tpl, sizeof(TemplateInfo) * n_templates));
+    CS_CUDA(cudaMalloc(&ctx->d_mean_op, sizeof(float4) * g_total));
+    CS_CUDA(cudaMalloc(&ctx->d_cov_a, sizeof(float4) * g_total));
+    CS_CUDA(cudaMalloc(&ctx->d_cov_b, sizeof(float2) * g_total));
+    CS_CUDA(cudaMalloc(&ctx->d_skin_w, sizeof(float4) * g_total));
+    CS_CUDA(cudaMalloc(&ctx->d_skin_i, sizeof(uint32_t) * g_total));
+    CS_CUDA(cudaMalloc(&ctx->d_sh, sizeof(float4) * planes_total));
+    CS_CUDA(cudaMemcpy(ctx->d_mean_op, mean_op.data(), sizeof(float4) * g_total, cudaMemcpyHostToDevice));
+    CS_CUDA(cudaMemcpy(ctx->d_cov_a, cov_a.data(), sizeof(float4) * g_total, cudaMemcpyHostToDevice));
+    CS_CUDA(cudaMemcpy(ctx->d_cov_b, cov_b.data(), sizeof(float2) * g_total, cudaMemcpyHostToDevice));
+    CS_CUDA(cudaMemcpy(ctx->d_skin_w, skin_w.data(), sizeof(float4) * g_total, cudaMemcpyHostToDevice));
+    CS_CUDA(cudaMemcpy(ctx->d_skin_i, skin_i.data(), sizeof(uint32_t) * g_total, cudaMemcpyHostToDevice));
+    CS_CUDA(cudaMemcpy(ctx->d_sh, sh.data(), sizeof(float4) * planes_total, cudaMemcpyHostToDevice));
+    ctx->n_tpl = n_templates;
+    ctx->tpl_host = info;
+    ctx->reach_g = std::move(reach);
+    ctx->smax_g = std::move(smax);
+    ctx->n_gauss_total = g_total;
+    ctx->sh_planes_total = planes_total;
+    ctx->max_depth = max_depth;
+    // default LoD: one full-detail level
+    ctx->lod.n_levels = 1;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        ctx->lod.mult[l] = 1.0f;
+        ctx->lod_frac[l] = 1.0f;
+    }
+    refresh_lod_bounds(ctx);
+    return push_templates(ctx);
+}
+
+int cs_set_lod(cs_ctx *ctx, int32_t n_levels, const float *dist_thresh, const float *fraction,
+               const float *scale_mult) {
+    if (!ctx) return CS_ERR_ARG;
+    if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "cs_set_lod before cs_upload_templates");
+    if (n_levels < 1 || n_levels > CS_MAX_LEVELS)
+        return fail(ctx, CS_ERR_ARG, "n_levels must be 1..%d", CS_MAX_LEVELS);
+    if (!fraction || !scale_mult || (n_levels > 1 && !dist_thresh))
+        return fail(ctx, CS_ERR_ARG, "NULL LoD array");
+    for (int l = 0; l < n_levels; ++l) {
+        if (!(fraction[l] > 0.0f && fraction[l] <= 1.0f))
+            return fail(ctx, CS_ERR_ARG, "fraction[%d] must be in (0, 1]", l);
+        if (!(scale_mult[l] > 0.0f && std::isfinite(scale_mult[l])))
+            return fail(ctx, CS_ERR_ARG, "scale_mult[%d] must be > 0", l);
+    }
+    for (int l = 0; l + 1 < n_levels; ++l) {
+        if (!std::isfinite(dist_thresh[l]) || (l > 0 && dist_thresh[l] < dist_thresh[l - 1]))
+            return fail(ctx, CS_ERR_ARG, "dist_thresh must be finite and ascending");
+    }
+    ctx->lod.n_levels = n_levels;
+    for (int l = 0; l < kMaxLevels; ++l) {
+        int s = l < n_levels ? l : n_levels - 1;
+        ctx->lod.mult[l] = scale_mult[s];
+        ctx->lod_frac[l] = fraction[s];
+        if (l < kMaxLevels - 1) ctx->lod.thresh[l] = l < n_levels - 1 ? dist_thresh[l] : INFINITY;
+    }
+    CS_CUDA(cudaSetDevice(ctx->device));
+    refresh_lod_bounds(ctx);
+    return push_templates(ctx);
+}
+
+int cs_set_instances(cs_ctx *ctx, int32_t n, const int32_t *template_id, const float *root,
+                     const float *joint_pose, int32_t on_device) {
+    if (!ctx) return CS_ERR_ARG;
+    if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "cs_set_instances before cs_upload_templates");
+    if (n < 0) return fail(ctx, CS_ERR_ARG, "n must be >= 0");
+    if (n > CS_MAX_INSTANCES) return fail(ctx, CS_ERR_CAPACITY, "n = %d exceeds %d", n, CS_MAX_INSTANCES);
+    if (n > 0 && (!template_id || !root || !joint_pose)) return fail(ctx, CS_ERR_ARG, "NULL instance array");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    size_t want = (size_t)std::max(n, 1);
+    CS_TRY(ensure(ctx, ctx->tid, want, "template ids"));
+    CS_TRY(ensure(ctx, ctx->vis, want, "visible list"));
+    CS_TRY(ensure(ctx, ctx->root, want * 12, "roots"));
+    CS_TRY(ensure(ctx, ctx->pose, want * kJoints * 3, "poses"));
+    CS_TRY(ensure(ctx, ctx->B, want * kJoints * 12, "skinning transforms"));
+    CS_TRY(ensure(ctx, ctx->V, want * 12, "view transforms"));
+    CS_TRY(ensure(ctx, ctx->Cloc, want * 4, "local camera centres"));
+    CS_TRY(ensure(ctx, ctx->groups, (size_t)kMaxTemplates * kMaxLevels, "groups"));
+    if (n > 0) {
+        cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (!on_device) {
+            for (int i = 0; i < n; ++i)
+                if (template_id[i] < 0 || template_id[i] >= ctx->n_tpl)
+                    return fail(ctx, CS_ERR_ARG, "template_id[%d] = %d out of range", i, template_id[i]);
+        }
+        CS_CUDA(cudaMemcpyAsync(ctx->tid.p, template_id, sizeof(int32_t) * n, kind, ctx->stream));
+        CS_CUDA(cudaMemcpyAsync(ctx->root.p, root, sizeof(float) * 12 * n, kind, ctx->stream));
+        CS_CUDA(cudaMemcpyAsync(ctx->pose.p, joint_pose, sizeof(float) * kJoints * 3 * n, kind, ctx->stream));
+    }
+    ctx->n_inst = n;
+    return CS_OK;
+}
+
+static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_stats *stats) {
+    if (!cam || !out) return fail(ctx, CS_ERR_ARG, "NULL camera or output");
+    if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(ctx, CS_ERR_ARG, "rgba_out must be 16-byte aligned");
+    if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "no templates uploaded");
+    if (cam->width < 1 || cam->height < 1 || cam->width > CS_MAX_IMAGE_SIDE || cam->height > CS_MAX_IMAGE_SIDE)
+        return fail(ctx, CS_ERR_ARG, "image size %dx%d outside 1..%d", cam->width, cam->height, CS_MAX_IMAGE_SIDE);
+    if (!(cam->fx > 0.f && cam->fy > 0.f && cam->near_z > 0.f) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
+        return fail(ctx, CS_ERR_ARG, "focal lengths and near plane must be positive and finite");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(cam->R[i])) return fail(ctx, CS_ERR_ARG, "camera rotation not finite");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(cam->t[i])) return fail(ctx, CS_ERR_ARG, "camera translation not finite");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    CamParams cp;
+    cam_params(ctx, cam, cp);
+    const int T = cp.tiles_x * cp.tiles_y;
+    const int I = ctx->n_inst;
+    const bool timing = ctx->stage_timing != 0;
+    ctx->tiles_x = cp.tiles_x;
+    ctx->tiles_y = cp.tiles_y;
+    ctx->timed = false;
+    int launched = 0;
+    cudaEvent_t *ev = nullptr;
+    if (timing) {
+        // this frame uses the other set; that set's frame (two frames ago)
+        // finished before the last frame's first host read, so this does not wait
+        const int k = ctx->ev_cur ^ 1;
+        CS_TRY(accumulate_stage_times(ctx, k));
+        ctx->ev_cur = k;
+        ev = ctx->ev[k];
+    }
+    CS_TRY(ensure(ctx, ctx->ranges, (size_t)T, "tile ranges"));
+    CS_TRY(ensure(ctx, ctx->groups, (size_t)kMaxTemplates * kMaxLevels, "groups"));
+    CS_TRY(ensure(ctx, ctx->vis, (size_t)std::max(I, 1), "visible list"));
+    if (timing) CS_CUDA(cudaEventRecord(ev[0], st));
+
+    // 1. forward kinematics
+    if (I > 0)
+        launched += launch_fk(I, ctx->n_tpl, ctx->tid.p, ctx->pose.p, ctx->d_tpl, ctx->max_depth, ctx->B.p, st);
+    if (timing) CS_CUDA(cudaEventRecord(ev[1], st));
+    // 2. LoD band, instance cull, grouping by (template, level)
+    int64_t S = 0;
+    if (I > 0) {
+        launched += launch_cull_group(I, ctx->n_tpl, ctx->tid.p, ctx->root.p, ctx->d_tpl, cp, ctx->lod,
+                          ctx->instance_cull, ctx->V.p, ctx->Cloc.p, ctx->vis.p, ctx->groups.p,
+                          ctx->d_meta, st);
+        CS_CUDA(cudaGetLastError());
+        CS_CUDA(cudaMemcpyAsync(ctx->h_meta, ctx->d_meta, kMetaWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CS_CUDA(cudaStreamSynchronize(st));
+        ctx->visible = ctx->h_meta[kMetaVisible];
+        ctx->n_groups = ctx->h_meta[kMetaGroups];
+        S = ctx->h_meta[kMetaSplats];
+        for (int l = 0; l < kMaxLevels; ++l) ctx->per_level[l] = ctx->h_meta[kMetaLevel0 + l];
+        if (S >= 0x7fffffffLL) return fail(ctx, CS_ERR_CAPACITY, "more than 2^31 - 1 splats in a frame");
+    } else {
+        ctx->visible = ctx->n_groups = 0;
+        for (int l = 0; l < kMaxLevels; ++l) ctx->per_level[l] = 0;
+    }
+    if (timing) CS_CUDA(cudaEventRecord(ev[2], st));
+    ctx->S = S;
+    // 3. LBS + EWA projection + SH colour
+    const size_t Sa = (size_t)std::max<int64_t>(S, 1);
+    CS_TRY(ensure(ctx, ctx->rec, Sa * 3, "splat records"));
+    CS_TRY(ensure(ctx, ctx->key, Sa, "depth keys"));
+    CS_TRY(ensure(ctx, ctx->ids, Sa, "splat ids"));
+    CS_TRY(ensure(ctx, ctx->key2, Sa, "depth keys (ping-pong)"));
+    CS_TRY(ensure(ctx, ctx->ids2, Sa, "splat ids (ping-pong)"));
+    CS_TRY(ensure(ctx, ctx->rect, Sa, "tile rects"));
+    CS_TRY(ensure(ctx, ctx->ntiles, Sa, "tile counts"));
+    CS_TRY(ensure(ctx, ctx->pair_off, Sa + 1, "pair offsets"));
+    CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Sa), scan_scratch_words(Sa + 1)), "scratch"));
+    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh};
+    if (S > 0)
+        launched += launch_project((int)S, ctx->groups.p, ctx->n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
+                       ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
+                       ctx->rec.p, ctx->key.p, ctx->ids.p, ctx->rect.p, ctx->ntiles.p, st);
+    if (timing) CS_CUDA(cudaEventRecord(ev[3], st));
+    // 4. depth sort of the splats (stable, ties by splat id)
+    int ob = 0;
+    if (S > 0) launched += radix_sort_u32(ctx->key.p, ctx->ids.p, ctx->key2.p, ctx->ids2.p, (uint32_t)S, 32,
+                                          ctx->scratch.p, st, &ob);
+    ctx->order_buf = ob;
+    uint32_t *order = ob ? ctx->ids2.p : ctx->ids.p;
+    uint32_t *sorted_keys = ob ? ctx->key2.p : ctx->key.p;
+    if (timing) CS_CUDA(cudaEventRecord(ev[4], st));
+    // 5. pair offsets in depth order and pair emission
+    launched += exclusive_scan(ctx->ntiles.p, order, ctx->pair_off.p, (uint32_t)S, ctx->scratch.p, st);
+    CS_CUDA(cudaGetLastError());
+    if (stats && S > 0) launched += launch_count_live((uint32_t)S, sorted_keys, ctx->d_meta + kMetaWords - 1, st);
+    CS_CUDA(cudaMemcpyAsync(ctx->h_pairs, ctx->pair_off.p + S, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (stats) CS_CUDA(cudaMemcpyAsync(ctx->h_pairs + 1, ctx->d_meta + kMetaWords - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CS_CUDA(cudaStreamSynchronize(st));
+    const int64_t P = ctx->h_pairs[0];
+    ctx->P = P;
+    const size_t Pa = (size_t)std::max<int64_t>(P, 1);
+    CS_TRY(ensure(ctx, ctx->ptile, Pa, "pair tiles"));
+    CS_TRY(ensure(ctx, ctx->ptile2, Pa, "pair tiles (ping-pong)"));
+    CS_TRY(ensure(ctx, ctx->pval, Pa, "pair splats"));
+    CS_TRY(ensure(ctx, ctx->pval2, Pa, "pair splats (ping-pong)"));
+    CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Pa), radix_scratch_words(Sa)), "scratch"));
+    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, ctx->pair_off.p, ctx->rect.p, cp.tiles_x,
+                                 ctx->ptile.p, ctx->pval.p, st);
+    if (timing) CS_CUDA(cudaEventRecord(ev[5], st));
+    // 6. stable sort of the pairs by tile
+    int pb = 0;
+    if (P > 0) launched += radix_sort_u16(ctx->ptile.p, ctx->pval.p, ctx->ptile2.p, ctx->pval2.p, (uint32_t)P,
+                                          bits_for((uint32_t)T), ctx->scratch.p, st, &pb);
+    ctx->pair_buf = pb;
+    uint16_t *ptile = pb ? ctx->ptile2.p : ctx->ptile.p;
+    uint32_t *pval = pb ? ctx->pval2.p : ctx->pval.p;
+    if (timing) CS_CUDA(cudaEventRecord(ev[6], st));
+    // 7. per-tile ranges
+    CS_CUDA(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * T, st));
+    launched += launch_tile_ranges((uint32_t)P, ptile, ctx->ranges.p, st);
+    if (timing) CS_CUDA(cudaEventRecord(ev[7], st));
+    // 8. compositing
+    launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ctx->ranges.p, pval, ctx->rec.p, out, st);
+    if (timing) CS_CUDA(cudaEventRecord(ev[8], st));
+    CS_CUDA(cudaGetLastError());
+    ctx->timed = timing;
+    ctx->ev_pending[ctx->ev_cur] = timing;
+    ctx->launches = launched;
+    if (stats) {
+        stats->instances = I;
+        stats->instances_visible = ctx->visible;
+        for (int l = 0; l < CS_MAX_LEVELS; ++l) stats->instances_per_level[l] = ctx->per_level[l];
+        stats->splats = S;
+        stats->splats_live = S > 0 ? (int64_t)ctx->h_pairs[1] : 0;
+        stats->pairs = P;
+        stats->tiles_x = cp.tiles_x;
+        stats->tiles_y = cp.tiles_y;
+        stats->kernel_launches = launched;
+    }
+    return CS_OK;
+}
+
+int cs_render(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats) {
+    if (!ctx) return CS_ERR_ARG;
+    return render_impl(ctx, cam, reinterpret_cast<float4 *>(rgba_out), stats);
+}
+
+int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_frame_stats *stats) {
+    if (!ctx) return CS_ERR_ARG;
+    if (!cam || !rgba_host) return fail(ctx, CS_ERR_ARG, "NULL camera or output");
+    if (cam->width < 1 || cam->height < 1 || cam->width > CS_MAX_IMAGE_SIDE || cam->height > CS_MAX_IMAGE_SIDE)
+        return fail(ctx, CS_ERR_ARG, "image size %dx%d outside 1..%d", cam->width, cam->height, CS_MAX_IMAGE_SIDE);
+    CS_CUDA(cudaSetDevice(ctx->device));
+    const size_t npix = (size_t)cam->width * cam->height;
+    CS_TRY(ensure(ctx, ctx->img, npix, "image"));
+    CS_TRY(render_impl(ctx, cam, ctx->img.p, stats));
+    CS_CUDA(cudaMemcpyAsync(rgba_host, ctx->img.p, npix * sizeof(float4), cudaMemcpyDeviceToHost, ctx->stream));
+    CS_CUDA(cudaStreamSynchronize(ctx->stream));
+    return CS_OK;
+}
+
+int cs_get_stage_times(cs_ctx *ctx, float *ms, int32_t n, int32_t average, int64_t *frames_out) {
+    if (!ctx || !ms || n < 0) return -CS_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+        fail(ctx, CS_ERR_CUDA, "cudaSetDevice failed");
+        return -CS_ERR_CUDA;
+    }
+    const int k = std::min<int>(n, kStages);
+    if (average) {
+        for (int s = 0; s < 2; ++s) {
+            int rc = accumulate_stage_times(ctx, s);
+            if (rc != CS_OK) return -rc;
+        }
+        if (ctx->stage_frames == 0) {
+            fail(ctx, CS_ERR_STATE, "no timed frame since the last average");
+            return -CS_ERR_STATE;
+        }
+        for (int i = 0; i < k; ++i) ms[i] = (float)(ctx->stage_sum[i] / (double)ctx->stage_frames);
+        if (frames_out) *frames_out = ctx->stage_frames;
+        for (int i = 0; i < kStages; ++i) ctx->stage_sum[i] = 0.0;
+        ctx->stage_frames = 0;
+        return k;
+    }
+    if (!ctx->timed) {
+        fail(ctx, CS_ERR_STATE, "no timed frame (stage_timing off or no render yet)");
+        return -CS_ERR_STATE;
+    }
+    cudaEvent_t *ev = ctx->ev[ctx->ev_cur];
+    if (cudaEventSynchronize(ev[kStages]) != cudaSuccess) {
+        fail(ctx, CS_ERR_CUDA, "event synchronise failed");
+        return -CS_ERR_CUDA;
+    }
+    for (int i = 0; i < k; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) != cudaSuccess) {
+            fail(ctx, CS_ERR_CUDA, "event timing failed");
+            return -CS_ERR_CUDA;
+        }
+        ms[i] = t;
+    }
+    if (frames_out) *frames_out = 1;
+    return k;
+}
+
+int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
+    if (!ctx || !out) return CS_ERR_ARG;
+    int64_t tb = (int64_t)ctx->n_gauss_total * (sizeof(float4) * 3 + sizeof(float2) + sizeof(uint32_t)) +
+                 (int64_t)ctx->sh_planes_total * sizeof(float4) + (int64_t)ctx->n_tpl * sizeof(TemplateInfo);
+    int64_t ib = bytes_of(ctx->tid) + bytes_of(ctx->vis) + bytes_of(ctx->root) + bytes_of(ctx->pose) +
+                 bytes_of(ctx->B) + bytes_of(ctx->V) + bytes_of(ctx->Cloc) + bytes_of(ctx->groups);
+    int64_t fb = bytes_of(ctx->rec) + bytes_of(ctx->key) + bytes_of(ctx->ids) + bytes_of(ctx->key2) +
+                 bytes_of(ctx->ids2) + bytes_of(ctx->ntiles) + bytes_of(ctx->pair_off) + bytes_of(ctx->pval) +
+                 bytes_of(ctx->pval2) + bytes_of(ctx->scratch) + bytes_of(ctx->rect) + bytes_of(ctx->ranges) +
+                 bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img);
+    out->template_bytes = tb;
+    out->instance_bytes = ib;
+    out->frame_bytes = fb;
+    out->total_bytes = tb + ib + fb;
+    return CS_OK;
+}
+
+int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size_t *size_out) {
+    if (!ctx) return CS_ERR_ARG;
+    CS_CUDA(cudaSetDevice(ctx->device));
+    const void *src = nullptr;
+    size_t size = 0;
+    const int T = ctx->tiles_x * ctx->tiles_y;
+    switch (which) {
+        case CS_DBG_SKIN_B: src = ctx->B.p; size = (size_t)ctx->n_inst * kJoints * 12 * sizeof(float); break;
+        case CS_DBG_VISIBLE: src = ctx->vis.p; size = (size_t)ctx->visible * sizeof(int32_t); break;
+        case CS_DBG_GROUPS: src = ctx->groups.p; size = (size_t)ctx->n_groups * sizeof(Group); break;
+        case CS_DBG_RECORDS: src = ctx->rec.p; size = (size_t)ctx->S * 12 * sizeof(float); break;
+        case CS_DBG_DEPTH_KEYS: src = ctx->order_buf ? ctx->key2.p : ctx->key.p; size = (size_t)ctx->S * 4; break;
+        case CS_DBG_RECTS: src = ctx->rect.p; size = (size_t)ctx->S * 8; break;
+        case CS_DBG_DEPTH_ORDER: src = ctx->order_buf ? ctx->ids2.p : ctx->ids.p; size = (size_t)ctx->S * 4; break;
+        case CS_DBG_PAIR_TILES: src = ctx->pair_buf ? ctx->ptile2.p : ctx->ptile.p; size = (size_t)ctx->P * 2; break;
+        case CS_DBG_PAIR_SPLATS: src = ctx->pair_buf ? ctx->pval2.p : ctx->pval.p; size = (size_t)ctx->P * 4; break;
+        case CS_DBG_TILE_RANGES: src = ctx->ranges.p; size = (size_t)T * 8; break;
+        default: return fail(ctx, CS_ERR_ARG, "unknown debug buffer %d", which);
+    }
+    if (size_out) *size_out = size;
+    CS_CUDA(cudaStreamSynchronize(ctx->stream));
+    size_t n = std::min(bytes, size);
+    if (n > 0) {
+        if (!host_dst || !src) return fail(ctx, CS_ERR_ARG, "NULL destination or empty buffer");
+        CS_CUDA(cudaMemcpy(host_dst, src, n, cudaMemcpyDeviceToHost));
+    }
+    return CS_OK;
+}
+
+}  // extern "C"

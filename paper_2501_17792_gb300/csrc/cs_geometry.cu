@@ -1,0 +1,482 @@
+// cs_geometry.cu -- per-instance and per-Gaussian geometry of a CrowdSplat
+// frame: forward kinematics, distance LoD with instance culling and
+// grouping, and the fused skinning + EWA projection + SH colour kernel.
+//
+// CrowdSplat Sec. 2 (stage 2): each duplicated character is animated by
+// linear blend skinning of its template, whose attributes other than the
+// posed means are shared; a distance band picks the template's level of
+// detail.  The projection follows the 3DGS rasteriser the paper renders
+// with (cited in Sec. 1 and Sec. 2).
+#include "cs_internal.cuh"
+
+namespace cs {
+
+// ---------------------------------------------------------------------------
+// forward kinematics: one warp per instance, lane j = joint j
+// ---------------------------------------------------------------------------
+
+// Rodrigues' formula in FP32: R = cos(th) I + sinc(th) K + b v v^T with
+// K = skew(v), b = (1 - cos th) / th^2 written as 2 sin^2(th/2) / th^2 to
+// avoid cancellation; second-order series below th = 1e-8.
+__device__ __forceinline__ void rodrigues(float x, float y, float z, float R[9]) {
+    float th2 = x * x + y * y + z * z;
+    float c, a, b;
+    if (th2 < 1e-16f) {
+        c = 1.0f - 0.5f * th2;
+        a = 1.0f;
+        b = 0.5f;
+    } else {
+        float th = sqrtf(th2);
+        float s, hs, hc;
+        sincosf(th, &s, &c);
+        sincosf(0.5f * th, &hs, &hc);
+        a = s / th;
+        float h = hs / th;
+        b = 2.0f * h * h;
+    }
+    R[0] = c + b * x * x;     R[1] = -a * z + b * x * y; R[2] = a * y + b * x * z;
+    R[3] = a * z + b * x * y; R[4] = c + b * y * y;      R[5] = -a * x + b * y * z;
+    R[6] = -a * y + b * x * z; R[7] = a * x + b * y * z; R[8] = c + b * z * z;
+}
+
+__global__ void __launch_bounds__(256) k_fk(int n_inst, int n_tpl, const int32_t *__restrict__ tid,
+                                            const float *__restrict__ pose,
+                                            const TemplateInfo *__restrict__ tpls, int max_depth,
+                                            float *__restrict__ B) {
+    const int inst = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (inst >= n_inst) return;  // uniform per warp
+    const int t = tid[inst];
+    if (t < 0 || t >= n_tpl) return;  // such instances are hidden by the cull kernel
+    const TemplateInfo &T = tpls[t];
+    const int j = lane < kJoints ? lane : kJoints - 1;
+    const int par = T.parent[j];
+    const int dep = lane < kJoints ? T.depth[j] : 1 << 20;
+    float R[9];
+    const float *pv = pose + (size_t)inst * kJoints * 3 + j * 3;
+    rodrigues(pv[0], pv[1], pv[2], R);
+    float jx = T.rest[j * 3 + 0], jy = T.rest[j * 3 + 1], jz = T.rest[j * 3 + 2];
+    float lx = jx, ly = jy, lz = jz;
+    if (par >= 0) {
+        lx -= T.rest[par * 3 + 0];
+        ly -= T.rest[par * 3 + 1];
+        lz -= T.rest[par * 3 + 2];
+    }
+    // local transform L = [R | l]; global G = G_parent o L, level by level
+    float G[12] = {R[0], R[1], R[2], lx, R[3], R[4], R[5], ly, R[6], R[7], R[8], lz};
+    const int src = par >= 0 ? par : j;
+    for (int level = 1; level <= max_depth; ++level) {
+        float P[12];
+#pragma unroll
+        for (int e = 0; e < 12; ++e) P[e] = __shfl_sync(0xffffffffu, G[e], src);
+        if (dep == level) {
+            float N[12];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    N[r * 4 + c] = P[r * 4 + 0] * R[0 * 3 + c] + P[r * 4 + 1] * R[1 * 3 + c] +
+                                   P[r * 4 + 2] * R[2 * 3 + c];
+                N[r * 4 + 3] = P[r * 4 + 0] * lx + P[r * 4 + 1] * ly + P[r * 4 + 2] * lz + P[r * 4 + 3];
+            }
+#pragma unroll
+            for (int e = 0; e < 12; ++e) G[e] = N[e];
+        }
+    }
+    if (lane < kJoints) {
+        // B = G o [I | -J]
+        float *o = B + ((size_t)inst * kJoints + j) * 12;
+        float4 r0, r1, r2;
+        r0 = make_float4(G[0], G[1], G[2], G[3] - (G[0] * jx + G[1] * jy + G[2] * jz));
+        r1 = make_float4(G[4], G[5], G[6], G[7] - (G[4] * jx + G[5] * jy + G[6] * jz));
+        r2 = make_float4(G[8], G[9], G[10], G[11] - (G[8] * jx + G[9] * jy + G[10] * jz));
+        reinterpret_cast<float4 *>(o)[0] = r0;
+        reinterpret_cast<float4 *>(o)[1] = r1;
+        reinterpret_cast<float4 *>(o)[2] = r2;
+    }
+}
+
+int launch_fk(int n_inst, int n_tpl, const int32_t *tid, const float *pose, const TemplateInfo *tpls,
+              int max_depth, float *B, cudaStream_t st) {
+    if (n_inst <= 0) return 0;
+    int blocks = (n_inst + 7) / 8;
+    k_fk<<<blocks, 256, 0, st>>>(n_inst, n_tpl, tid, pose, tpls, max_depth, B);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// LoD + instance cull + grouping: one block of 1024 threads
+// ---------------------------------------------------------------------------
+
+constexpr int kCullThreads = 1024;
+constexpr int CS_MAX_INSTANCES_BYTES = 131072;  // one group byte per instance
+constexpr uint8_t kHidden = 255;
+
+__global__ void __launch_bounds__(kCullThreads) k_cull_group(
+    int n_inst, int n_tpl, const int32_t *__restrict__ tid, const float *__restrict__ root,
+    const TemplateInfo *__restrict__ tpls, CamParams cam, LodParams lod, int do_cull,
+    float *__restrict__ V, float *__restrict__ Cloc, int32_t *__restrict__ vis,
+    Group *__restrict__ groups, int32_t *__restrict__ meta) {
+    extern __shared__ uint8_t grp[];  // [n_inst] group of each instance
+    __shared__ int32_t gcount[kMaxTemplates * kMaxLevels];
+    __shared__ int32_t gslot[kMaxTemplates * kMaxLevels];
+    const int L = lod.n_levels;
+    const int n_grp = n_tpl * L;
+    for (int g = threadIdx.x; g < n_grp; g += blockDim.x) gcount[g] = 0;
+    __syncthreads();
+
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        const float *rt = root + (size_t)i * 12;
+        float Rr[9] = {rt[0], rt[1], rt[2], rt[4], rt[5], rt[6], rt[8], rt[9], rt[10]};
+        float tr[3] = {rt[3], rt[7], rt[11]};
+        // distance band: number of thresholds <= distance (CrowdSplat Sec. 2)
+        float dx = tr[0] - cam.center[0], dy = tr[1] - cam.center[1], dz = tr[2] - cam.center[2];
+        float d = sqrtf(dx * dx + dy * dy + dz * dz);
+        int lvl = 0;
+        for (int k = 0; k < L - 1; ++k) lvl += (d >= lod.thresh[k]) ? 1 : 0;
+        // V = camera o root
+        float Vm[12];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Vm[r * 4 + c] = cam.R[r * 3 + 0] * Rr[0 * 3 + c] + cam.R[r * 3 + 1] * Rr[1 * 3 + c] +
+                                cam.R[r * 3 + 2] * Rr[2 * 3 + c];
+            Vm[r * 4 + 3] = cam.R[r * 3 + 0] * tr[0] + cam.R[r * 3 + 1] * tr[1] +
+                            cam.R[r * 3 + 2] * tr[2] + cam.t[r];
+        }
+        float4 *vo = reinterpret_cast<float4 *>(V + (size_t)i * 12);
+        vo[0] = make_float4(Vm[0], Vm[1], Vm[2], Vm[3]);
+        vo[1] = make_float4(Vm[4], Vm[5], Vm[6], Vm[7]);
+        vo[2] = make_float4(Vm[8], Vm[9], Vm[10], Vm[11]);
+        // camera centre in the root frame: Rr^T (c - t)
+        float e0 = -dx, e1 = -dy, e2 = -dz;
+        reinterpret_cast<float4 *>(Cloc)[i] =
+            make_float4(Rr[0] * e0 + Rr[3] * e1 + Rr[6] * e2, Rr[1] * e0 + Rr[4] * e1 + Rr[7] * e2,
+                        Rr[2] * e0 + Rr[5] * e1 + Rr[8] * e2, 0.0f);
+        int t = tid[i];
+        bool visible = t >= 0 && t < n_tpl;  // out-of-range ids (device input) are hidden
+        if (do_cull && visible) {
+            const TemplateInfo &T = tpls[t];
+            // bounding sphere: centre = pelvis rest position (posed local
+            // means stay within reach of it), grown by the splat support
+            float px = T.rest[0], py = T.rest[1], pz = T.rest[2];
+            float cxs = Vm[0] * px + Vm[1] * py + Vm[2] * pz + Vm[3];
+            float cys = Vm[4] * px + Vm[5] * py + Vm[6] * pz + Vm[7];
+            float czs = Vm[8] * px + Vm[9] * py + Vm[10] * pz + Vm[11];
+            float reach = T.reach[lvl] * 1.0001f + 1e-4f;
+            float grow = reach + cam.cull_sigma_k * T.sigma_max[lvl] + 1e-3f;
+            if (czs + reach <= cam.near_z) visible = false;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                float s = cam.plane[p][0] * cxs + cam.plane[p][1] * cys + cam.plane[p][2] * czs;
+                if (s > grow) visible = false;
+            }
+        }
+        uint8_t g = visible ? (uint8_t)(t * L + lvl) : kHidden;
+        grp[i] = g;
+        if (visible) atomicAdd(&gcount[g], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int slot = 0, ng = 0;
+        long long splat = 0;
+        int per_level[kMaxLevels] = {0, 0, 0, 0};
+        for (int g = 0; g < n_grp; ++g) {
+            gslot[g] = slot;
+            int c = gcount[g];
+            if (c == 0) continue;
+            int t = g / L, l = g % L;
+            Group G;
+            G.tpl = t;
+            G.lvl = l;
+            G.slot0 = slot;
+            G.nslots = c;
+            G.ng = tpls[t].n_level[l];
+            G.splat0 = (int32_t)(splat < 0x7fffffffLL ? splat : 0x7fffffffLL);
+            groups[ng++] = G;
+            slot += c;
+            splat += (long long)c * G.ng;
+            per_level[l] += c;
+        }
+        meta[kMetaVisible] = slot;
+        meta[kMetaGroups] = ng;
+        // splat count, saturated: the host rejects counts >= 2^31
+        meta[kMetaSplats] = (int32_t)(splat < 0x7fffffffLL ? splat : 0x7fffffffLL);
+        for (int l = 0; l < kMaxLevels; ++l) meta[kMetaLevel0 + l] = per_level[l];
+    }
+    __syncthreads();
+    // stable placement: one warp per group sweeps the instances in order
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int g = warp; g < n_grp; g += kCullThreads / 32) {
+        if (gcount[g] == 0) continue;
+        int pos = gslot[g];
+        for (int base = 0; base < n_inst; base += 32) {
+            int i = base + lane;
+            bool hit = i < n_inst && grp[i] == g;
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) vis[pos + __popc(m & ((1u << lane) - 1u))] = i;
+            pos += __popc(m);
+        }
+    }
+}
+
+int launch_cull_group(int n_inst, int n_tpl, const int32_t *tid, const float *root,
+                       const TemplateInfo *tpls, const CamParams &cam, const LodParams &lod,
+                       int do_cull, float *V, float *Cloc, int32_t *vis, Group *groups,
+                       int32_t *meta, cudaStream_t st) {
+    size_t smem = (size_t)(n_inst > 0 ? n_inst : 1);
+    if (smem > 48 * 1024) {
+        static int configured_device = -1;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (configured_device != dev) {
+            cudaFuncSetAttribute(k_cull_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 CS_MAX_INSTANCES_BYTES);
+            configured_device = dev;
+        }
+    }
+    k_cull_group<<<1, kCullThreads, smem, st>>>(n_inst, n_tpl, tid, root, tpls, cam, lod, do_cull,
+                                                V, Cloc, vis, groups, meta);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// fused LBS + EWA projection + SH colour: one thread per splat
+// ---------------------------------------------------------------------------
+
+// Real SH basis to degree 3 (3DGS sign convention, degree 1 = C1 (-y, z, -x)),
+// constants from their closed forms.
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float Y[16]) {
+    const float C0 = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
+    const float C1 = 0.4886025119029199f;   // sqrt(3 / (4 pi))
+    Y[0] = C0;
+    if (deg < 1) return;
+    Y[1] = -C1 * y;
+    Y[2] = C1 * z;
+    Y[3] = -C1 * x;
+    if (deg < 2) return;
+    const float A2 = 1.0925484305920792f;   // sqrt(15 / pi) / 2
+    const float B2 = 0.31539156525252005f;  // sqrt(5 / pi) / 4
+    const float E2 = 0.5462742152960396f;   // sqrt(15 / pi) / 4
+    float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = A2 * x * y;
+    Y[5] = -A2 * y * z;
+    Y[6] = B2 * (2.0f * zz - xx - yy);
+    Y[7] = -A2 * x * z;
+    Y[8] = E2 * (xx - yy);
+    if (deg < 3) return;
+    const float K0 = 0.5900435899266435f;  // sqrt(35 / (2 pi)) / 4
+    const float K1 = 2.890611442640554f;   // sqrt(105 / pi) / 2
+    const float K2 = 0.4570457994644658f;  // sqrt(21 / (2 pi)) / 4
+    const float K3 = 0.3731763325901154f;  // sqrt(7 / pi) / 4
+    const float K5 = 1.445305721320277f;   // sqrt(105 / pi) / 4
+    Y[9] = -K0 * y * (3.0f * xx - yy);
+    Y[10] = K1 * x * y * z;
+    Y[11] = -K2 * y * (4.0f * zz - xx - yy);
+    Y[12] = K3 * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -K2 * x * (4.0f * zz - xx - yy);
+    Y[14] = K5 * z * (xx - yy);
+    Y[15] = -K0 * x * (xx - 3.0f * yy);
+}
+
+template <int DEG>
+__device__ __forceinline__ void sh_colour(const float4 *__restrict__ sh, int64_t base, int n,
+                                          float dx, float dy, float dz, float rgb[3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int P = (K * 3 + 3) / 4;
+    float Y[16];
+    sh_basis(DEG, dx, dy, dz, Y);
+    float c[P * 4];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        float4 v = __ldg(sh + base + (int64_t)p * n);
+        c[p * 4 + 0] = v.x;
+        c[p * 4 + 1] = v.y;
+        c[p * 4 + 2] = v.z;
+        c[p * 4 + 3] = v.w;
+    }
+    float r = 0.f, g = 0.f, b = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        r += Y[k] * c[k * 3 + 0];
+        g += Y[k] * c[k * 3 + 1];
+        b += Y[k] * c[k * 3 + 2];
+    }
+    rgb[0] = fmaxf(r + 0.5f, 0.0f);
+    rgb[1] = fmaxf(g + 0.5f, 0.0f);
+    rgb[2] = fmaxf(b + 0.5f, 0.0f);
+}
+
+constexpr int kProjThreads = 256;
+
+__global__ void __launch_bounds__(kProjThreads) k_project(
+    int n_splats, const Group *__restrict__ groups, int n_groups, const int32_t *__restrict__ vis,
+    const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ Cloc,
+    const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,
+    CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
+    uint32_t *__restrict__ key, uint32_t *__restrict__ ids, uint2 *__restrict__ rect,
+    uint32_t *__restrict__ ntiles) {
+    __shared__ Group sg[kMaxTemplates * kMaxLevels];
+    for (int g = threadIdx.x; g < n_groups; g += blockDim.x) sg[g] = groups[g];
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_splats) return;
+    // group of this splat: last group with splat0 <= s
+    int lo = 0, hi = n_groups - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sg[mid].splat0 <= s) lo = mid; else hi = mid - 1;
+    }
+    const Group G = sg[lo];
+    const int rel = s - G.splat0;
+    const int slot = G.slot0 + rel / G.ng;
+    const int gg = rel - (rel / G.ng) * G.ng;
+    const int inst = vis[slot];
+    const TemplateInfo &T = tpls[G.tpl];
+    const int gi = T.g_off + gg;
+    ids[s] = (uint32_t)s;
+
+    // LBS (CrowdSplat Sec. 2): M = sum_k w_k B_{idx_k} (instance local)
+    const float4 w = __ldg(ta.skin_w + gi);
+    const uint32_t packed = __ldg(ta.skin_i + gi);
+    const float4 *Bi = reinterpret_cast<const float4 *>(Bm + (size_t)inst * kJoints * 12);
+    float M[12];
+    {
+        const float wk[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int e = 0; e < 12; ++e) M[e] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = (packed >> (8 * k)) & 0xFF;
+            const float4 b0 = __ldg(Bi + j * 3 + 0), b1 = __ldg(Bi + j * 3 + 1), b2 = __ldg(Bi + j * 3 + 2);
+            M[0] += wk[k] * b0.x; M[1] += wk[k] * b0.y; M[2] += wk[k] * b0.z; M[3] += wk[k] * b0.w;
+            M[4] += wk[k] * b1.x; M[5] += wk[k] * b1.y; M[6] += wk[k] * b1.z; M[7] += wk[k] * b1.w;
+            M[8] += wk[k] * b2.x; M[9] += wk[k] * b2.y; M[10] += wk[k] * b2.z; M[11] += wk[k] * b2.w;
+        }
+    }
+    const float4 mo = __ldg(ta.mean_op + gi);
+    const float lx = M[0] * mo.x + M[1] * mo.y + M[2] * mo.z + M[3];
+    const float ly = M[4] * mo.x + M[5] * mo.y + M[6] * mo.z + M[7];
+    const float lz = M[8] * mo.x + M[9] * mo.y + M[10] * mo.z + M[11];
+    // view transform (camera o root)
+    const float4 *Vi = reinterpret_cast<const float4 *>(Vm + (size_t)inst * 12);
+    const float4 v0 = __ldg(Vi), v1 = __ldg(Vi + 1), v2 = __ldg(Vi + 2);
+    const float tx = v0.x * lx + v0.y * ly + v0.z * lz + v0.w;
+    const float ty = v1.x * lx + v1.y * ly + v1.z * lz + v1.w;
+    const float tz = v2.x * lx + v2.y * ly + v2.z * lz + v2.w;
+
+    bool live = tz > cam.near_z;  // also false for NaN
+    uint2 rc = make_uint2(0u, 0u);
+    uint32_t nt = 0;
+    if (live) {
+        // covariance in camera space: Wc = (V_R A) (m^2 Sigma) (V_R A)^T,
+        // A = the 3x3 part of M (full LBS) or identity (means only)
+        float W[9];
+        if (skin_mode == 0) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float4 vr = r == 0 ? v0 : (r == 1 ? v1 : v2);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) W[r * 3 + c] = vr.x * M[c] + vr.y * M[4 + c] + vr.z * M[8 + c];
+            }
+        } else {
+            W[0] = v0.x; W[1] = v0.y; W[2] = v0.z;
+            W[3] = v1.x; W[4] = v1.y; W[5] = v1.z;
+            W[6] = v2.x; W[7] = v2.y; W[8] = v2.z;
+        }
+        const float4 ca = __ldg(ta.cov_a + gi);
+        const float2 cb = __ldg(ta.cov_b + gi);
+        const float m = lod.mult[G.lvl];
+        const float m2 = m * m;
+        const float S0 = ca.x * m2, S1 = ca.y * m2, S2 = ca.z * m2, S3 = ca.w * m2, S4 = cb.x * m2,
+                    S5 = cb.y * m2;
+        // EWA Jacobian at the mean, x/z and y/z clamped (3DGS)
+        const float iz = 1.0f / tz;
+        const float txz = fminf(fmaxf(tx * iz, -cam.limx), cam.limx);
+        const float tyz = fminf(fmaxf(ty * iz, -cam.limy), cam.limy);
+        const float j00 = cam.fx * iz, j02 = -cam.fx * txz * iz;
+        const float j11 = cam.fy * iz, j12 = -cam.fy * tyz * iz;
+        // T = J W (2x3)
+        const float t00 = j00 * W[0] + j02 * W[6], t01 = j00 * W[1] + j02 * W[7], t02 = j00 * W[2] + j02 * W[8];
+        const float t10 = j11 * W[3] + j12 * W[6], t11 = j11 * W[4] + j12 * W[7], t12 = j11 * W[5] + j12 * W[8];
+        // T Sigma (2x3), Sigma symmetric (S0 S1 S2; S1 S3 S4; S2 S4 S5)
+        const float u00 = t00 * S0 + t01 * S1 + t02 * S2;
+        const float u01 = t00 * S1 + t01 * S3 + t02 * S4;
+        const float u02 = t00 * S2 + t01 * S4 + t02 * S5;
+        const float u10 = t10 * S0 + t11 * S1 + t12 * S2;
+        const float u11 = t10 * S1 + t11 * S3 + t12 * S4;
+        const float u12 = t10 * S2 + t11 * S4 + t12 * S5;
+        const float a = u00 * t00 + u01 * t01 + u02 * t02 + 0.3f;
+        const float b = u00 * t10 + u01 * t11 + u02 * t12;
+        const float c = u10 * t10 + u11 * t11 + u12 * t12 + 0.3f;
+        const float det = a * c - b * b;
+        live = det > 0.0f;
+        if (live) {
+            const float idet = 1.0f / det;
+            const float cA = c * idet, cB = -b * idet, cC = a * idet;
+            const float mid = 0.5f * (a + c);
+            const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+            const float r = ceilf(3.0f * sqrtf(lam));
+            const float u = cam.fx * tx * iz + cam.cx;
+            const float v = cam.fy * ty * iz + cam.cy;
+            // pixels with centre inside the support box, clipped to the image
+            float fx0 = fmaxf(ceilf(u - r - 0.5f), 0.0f);
+            float fx1 = fminf(floorf(u + r - 0.5f), (float)(cam.W - 1));
+            float fy0 = fmaxf(ceilf(v - r - 0.5f), 0.0f);
+            float fy1 = fminf(floorf(v + r - 0.5f), (float)(cam.H - 1));
+            live = r > 0.0f && fx0 <= fx1 && fy0 <= fy1 && isfinite(u) && isfinite(v) &&
+                   isfinite(r) && isfinite(cA) && isfinite(cB) && isfinite(cC);
+            if (live) {
+                const uint32_t x0 = (uint32_t)fx0 >> 4, x1 = (uint32_t)fx1 >> 4;
+                const uint32_t y0 = (uint32_t)fy0 >> 4, y1 = (uint32_t)fy1 >> 4;
+                rc = make_uint2(x0 | (y0 << 16), x1 | (y1 << 16));
+                nt = (x1 - x0 + 1) * (y1 - y0 + 1);
+                // colour: SH at the viewing direction (camera centre -> mean)
+                float ddx, ddy, ddz;
+                const float4 cl = __ldg(reinterpret_cast<const float4 *>(Cloc) + inst);
+                ddx = lx - cl.x;
+                ddy = ly - cl.y;
+                ddz = lz - cl.z;
+                if (sh_frame == 1) {
+                    const float *rt = root + (size_t)inst * 12;
+                    const float wx = rt[0] * ddx + rt[1] * ddy + rt[2] * ddz;
+                    const float wy = rt[4] * ddx + rt[5] * ddy + rt[6] * ddz;
+                    const float wz = rt[8] * ddx + rt[9] * ddy + rt[10] * ddz;
+                    ddx = wx; ddy = wy; ddz = wz;
+                }
+                const float inv = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+                ddx *= inv; ddy *= inv; ddz *= inv;
+                float rgb[3];
+                const int64_t base = T.sh_off + gg;
+                switch (T.sh_deg) {
+                    case 0: sh_colour<0>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                    case 1: sh_colour<1>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                    case 2: sh_colour<2>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                    default: sh_colour<3>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                }
+                rec[(size_t)s * 3 + 0] = make_float4(u, v, cA, cB);
+                rec[(size_t)s * 3 + 1] = make_float4(cC, mo.w, r, tz);
+                rec[(size_t)s * 3 + 2] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+            }
+        }
+    }
+    key[s] = live ? __float_as_uint(tz) : 0xFFFFFFFFu;
+    rect[s] = rc;
+    ntiles[s] = nt;
+}
+
+int launch_project(int n_splats, const Group *groups, int n_groups, const int32_t *vis,
+                    const float *B, const float *V, const float *Cloc, const float *root,
+                    const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
+                    const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
+                    uint32_t *ids, uint2 *rect, uint32_t *ntiles, cudaStream_t st) {
+    if (n_splats <= 0) return 0;
+    int blocks = (n_splats + kProjThreads - 1) / kProjThreads;
+    k_project<<<blocks, kProjThreads, 0, st>>>(n_splats, groups, n_groups, vis, B, V, Cloc, root, ta,
+                                                tpls, cam, lod, skin_mode, sh_frame, rec, key, ids,
+                                                rect, ntiles);
+    return 1;
+}
+
+}  // namespace cs

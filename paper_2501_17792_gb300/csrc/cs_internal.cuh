@@ -1,0 +1,125 @@
+// cs_internal.cuh -- shared declarations of the CrowdSplat CUDA library
+// (device data layout, per-frame parameters, kernel launchers).
+//
+// Device data layout (structure of arrays, one allocation per array, all
+// templates concatenated; g = global template-Gaussian index):
+//   mean_op[g]  float4 (x, y, z, opacity)          template local frame
+//   cov_a[g]    float4 (xx, xy, xz, yy)            canonical covariance R S S^T R^T
+//   cov_b[g]    float2 (yz, zz)                    at scale multiplier 1
+//   skin_w[g]   float4 top-4 skinning weights
+//   skin_i[g]   uint32 four joint ids, one byte each (little end = first)
+//   sh          float4 planes: plane p of Gaussian k of template t at
+//               sh[t.sh_off + p * t.n + k]; plane p holds the flat SH
+//               coefficients 4p..4p+3 of that Gaussian (flat = k*3 + channel)
+// Per instance: B[i][24][12] instance-local skinning transforms (root not
+// applied), V[i][12] = camera o root (3x4), C[i][4] = camera centre in the
+// instance root frame.
+// Per splat s (Gaussian-instance of a visible instance, dense ids grouped by
+// (template, level)): rec[3s..3s+2] float4 = {u, v, A, B}, {C, opacity,
+// radius, depth}, {r, g, b, 0}; key[s] depth bits (0xFFFFFFFF culled);
+// rect[s] tile rectangle (x0 | y0 << 16, x1 | y1 << 16), inclusive;
+// ntiles[s] tiles touched.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cs {
+
+constexpr int kJoints = 24;
+constexpr int kMaxTemplates = 63;
+constexpr int kMaxLevels = 4;
+constexpr int kTile = 16;
+
+struct TemplateInfo {
+    int32_t g_off;      // first global Gaussian index
+    int32_t n;          // Gaussians
+    int32_t sh_deg;     // 0..3
+    int32_t sh_planes;  // float4 planes per Gaussian
+    int64_t sh_off;     // float4 offset of plane 0
+    int32_t n_level[kMaxLevels];   // Gaussians rendered at each level
+    float reach[kMaxLevels];       // bound of |posed local mean - pelvis rest| per level
+    float sigma_max[kMaxLevels];   // largest scale x level multiplier per level
+    float rest[kJoints * 3];
+    int8_t parent[kJoints];
+    int8_t depth[kJoints];         // depth in the kinematic tree (root 0)
+    int32_t max_depth;
+};
+
+struct Group {         // visible instances of one (template, level)
+    int32_t tpl, lvl;
+    int32_t slot0;     // first slot in the visible list
+    int32_t nslots;
+    int32_t ng;        // Gaussians per instance (template size at level)
+    int32_t splat0;    // first splat id
+};
+
+struct CamParams {
+    float R[9], t[3];
+    float fx, fy, cx, cy;
+    int32_t W, H;
+    float near_z;
+    float center[3];       // camera centre in world coordinates
+    float limx, limy;      // EWA clamp of x/z, y/z (1.3 x half field of view)
+    int32_t tiles_x, tiles_y;
+    float plane[4][4];     // conservative frustum side planes (camera space, unit normals)
+    float cull_sigma_k;    // instance cull: 3D growth per unit of Gaussian scale
+};
+
+struct LodParams {
+    int32_t n_levels;
+    float thresh[kMaxLevels - 1];
+    float mult[kMaxLevels];
+};
+
+struct TemplateArrays {
+    const float4 *mean_op;
+    const float4 *cov_a;
+    const float2 *cov_b;
+    const float4 *skin_w;
+    const uint32_t *skin_i;
+    const float4 *sh;
+};
+
+// meta words written by the cull kernel and read back by the host
+enum MetaIndex { kMetaVisible = 0, kMetaGroups = 1, kMetaSplats = 2, kMetaLevel0 = 3, kMetaWords = 8 };
+
+// Every launch_* function returns the number of kernels it launched.
+// ---- geometry (cs_geometry.cu) ----
+int launch_fk(int n_inst, int n_tpl, const int32_t *tid, const float *pose, const TemplateInfo *tpls,
+              int max_depth, float *B, cudaStream_t st);
+int launch_cull_group(int n_inst, int n_tpl, const int32_t *tid, const float *root,
+                       const TemplateInfo *tpls, const CamParams &cam, const LodParams &lod,
+                       int do_cull, float *V, float *Cloc, int32_t *vis, Group *groups,
+                       int32_t *meta, cudaStream_t st);
+int launch_project(int n_splats, const Group *groups, int n_groups, const int32_t *vis,
+                    const float *B, const float *V, const float *Cloc, const float *root,
+                    const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
+                    const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
+                    uint32_t *ids, uint2 *rect, uint32_t *ntiles, cudaStream_t st);
+
+// ---- sort and binning (cs_sort.cu) ----
+// scratch words needed by exclusive_scan / radix_sort for n elements
+size_t scan_scratch_words(size_t n);
+size_t radix_scratch_words(size_t n);
+// out[0..n] = exclusive prefix sums of in (gathered through idx when idx
+// is non-null: value i = in[idx[i]]); out[n] = total.
+int exclusive_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, uint32_t n,
+                    uint32_t *scratch, cudaStream_t st);
+// Stable LSD radix sort of (key, value) pairs over key bits [0, bits).
+// Ping-pongs between (k0, v0) and (k1, v1); *in_second is set to 0 when the
+// result is in (k0, v0), 1 when in (k1, v1).  Returns kernels launched.
+int radix_sort_u32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t n, int bits,
+                   uint32_t *scratch, cudaStream_t st, int *in_second);
+int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint32_t n, int bits,
+                   uint32_t *scratch, cudaStream_t st, int *in_second);
+int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *pair_off,
+                       const uint2 *rect, int tiles_x, uint16_t *ptile, uint32_t *pval,
+                       cudaStream_t st);
+int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, cudaStream_t st);
+int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cudaStream_t st);
+
+// ---- compositing (cs_blend.cu) ----
+int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges,
+                  const uint32_t *pval, const float4 *rec, float4 *out, cudaStream_t st);
+
+}  // namespace cs

@@ -1,0 +1,328 @@
+// cs_sort.cu -- tile binning and the (tile, depth) sort of a CrowdSplat frame.
+//
+// The 3DGS rasteriser the paper renders with (CrowdSplat Sec. 1 and Sec. 2
+// cite Kerbl et al. 2023) duplicates each splat into every 16x16 tile its
+// support box touches and sorts the (tile, depth) keys so that each tile
+// can composite its splats front to back.  Here the order is reached in two
+// stable stages instead of one 64-bit sort:
+//   1. a stable LSD radix sort of the splats by 32-bit depth (4 passes);
+//   2. pairs are emitted in that depth order (prefix sum of tile counts),
+//      then a stable LSD radix sort by tile index (ceil(bits/8) passes, 16-bit
+//      keys) leaves every tile's pairs in (depth, splat id) order.
+// Each radix pass is reduce-then-scan (histogram, exclusive scan,
+// scatter): no inter-block waits, and the order is deterministic.
+#include "cs_internal.cuh"
+
+namespace cs {
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 (three kernels: tile sums, spine, down-sweep)
+// ---------------------------------------------------------------------------
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive
+// prefix, *total (shared) receives the block sum after the call.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t s = lane < nwarps ? warp_sums[lane] : 0u;
+        const uint32_t si = warp_incl_scan(s);
+        warp_sums[lane] = si - s;
+        if (lane == 31) *total = si;
+    }
+    __syncthreads();
+    return inc - v + warp_sums[warp];
+}
+
+template <bool GATHER>
+__device__ __forceinline__ uint32_t scan_load(const uint32_t *in, const uint32_t *idx, uint32_t i) {
+    return GATHER ? in[idx[i]] : in[i];
+}
+
+template <bool GATHER>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in,
+                                                              const uint32_t *__restrict__ idx,
+                                                              uint32_t n, uint32_t *__restrict__ sums) {
+    __shared__ uint32_t total;
+    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) v += scan_load<GATHER>(in, idx, base + k);
+    block_excl_scan(v, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the tile sums in place, total at sums[nb].
+__global__ void __launch_bounds__(kScanThreads) k_scan_spine(uint32_t *__restrict__ sums, uint32_t nb) {
+    __shared__ uint32_t total;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nb; base += kScanThreads) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t v = i < nb ? sums[i] : 0u;
+        uint32_t ex = block_excl_scan(v, &total);
+        if (i < nb) sums[i] = carry + ex;
+        __syncthreads();
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+template <bool GATHER>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *__restrict__ in,
+                                                            const uint32_t *__restrict__ idx, uint32_t n,
+                                                            const uint32_t *__restrict__ sums,
+                                                            uint32_t nb, uint32_t *__restrict__ out) {
+    __shared__ uint32_t total;
+    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? scan_load<GATHER>(in, idx, base + k) : 0u;
+        s += v[k];
+    }
+    uint32_t ex = block_excl_scan(s, &total) + sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = ex;
+        ex += v[k];
+    }
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = sums[nb];
+}
+
+size_t scan_scratch_words(size_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+int exclusive_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, uint32_t n,
+                   uint32_t *scratch, cudaStream_t st) {
+    if (n == 0) {
+        cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
+        return 0;
+    }
+    uint32_t nb = (n + kScanTile - 1) / kScanTile;
+    if (idx) {
+        k_scan_reduce<true><<<nb, kScanThreads, 0, st>>>(in, idx, n, scratch);
+        k_scan_spine<<<1, kScanThreads, 0, st>>>(scratch, nb);
+        k_scan_down<true><<<nb, kScanThreads, 0, st>>>(in, idx, n, scratch, nb, out);
+    } else {
+        k_scan_reduce<false><<<nb, kScanThreads, 0, st>>>(in, nullptr, n, scratch);
+        k_scan_spine<<<1, kScanThreads, 0, st>>>(scratch, nb);
+        k_scan_down<false><<<nb, kScanThreads, 0, st>>>(in, nullptr, n, scratch, nb, out);
+    }
+    return 3;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits, reduce-then-scan per pass
+// ---------------------------------------------------------------------------
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixItems = 8;                               // per lane
+constexpr int kRadixTile = kRadixThreads * kRadixItems;      // per block
+constexpr int kRadixWarpTile = 32 * kRadixItems;             // per warp
+
+template <typename K>
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const K *__restrict__ keys, uint32_t n,
+                                                              int shift, uint32_t *__restrict__ hist,
+                                                              uint32_t nblocks) {
+    __shared__ uint32_t h[kRadixWarps][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = threadIdx.x; d < kRadixWarps * 256; d += kRadixThreads) (&h[0][0])[d] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * kRadixTile + warp * kRadixWarpTile;
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        uint32_t i = base + r * 32 + lane;
+        if (i < n) atomicAdd(&h[warp][(keys[i] >> shift) & 0xFFu], 1u);
+    }
+    __syncthreads();
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kRadixWarps; ++w) s += h[w][threadIdx.x];
+    hist[threadIdx.x * nblocks + blockIdx.x] = s;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+    const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+    uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ offs,
+    uint32_t nblocks) {
+    __shared__ uint32_t wcnt[kRadixWarps][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = threadIdx.x; d < kRadixWarps * 256; d += kRadixThreads) (&wcnt[0][0])[d] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * kRadixTile + warp * kRadixWarpTile;
+    const uint32_t lt = (1u << lane) - 1u;
+    K k[kRadixItems];
+    uint32_t v[kRadixItems], rank[kRadixItems];
+    int dig[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        const bool ok = i < n;
+        k[r] = ok ? kin[i] : (K)0;
+        v[r] = ok ? vin[i] : 0u;
+        const int d = ok ? (int)((k[r] >> shift) & 0xFFu) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = ok ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (ok && (peers & lt) == 0u) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt);
+        dig[r] = d;
+    }
+    __syncthreads();
+    {
+        // digit d: global base of this block, then exclusive over warps
+        const int d = threadIdx.x;
+        uint32_t run = offs[d * nblocks + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < kRadixWarps; ++w) {
+            uint32_t c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        if (dig[r] < 256) {
+            const uint32_t pos = wcnt[warp][dig[r]] + rank[r];
+            kout[pos] = k[r];
+            vout[pos] = v[r];
+        }
+    }
+}
+
+size_t radix_scratch_words(size_t n) {
+    size_t nb = (n + kRadixTile - 1) / kRadixTile;
+    if (nb == 0) nb = 1;
+    size_t hist = 256 * nb;
+    return 2 * hist + 1 + scan_scratch_words(hist);
+}
+
+template <typename K>
+static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int bits,
+                      uint32_t *scratch, cudaStream_t st, int *in_second) {
+    *in_second = 0;
+    if (n == 0 || bits <= 0) return 0;
+    int launched = 0;
+    const uint32_t nb = (n + kRadixTile - 1) / kRadixTile;
+    const uint32_t hn = 256 * nb;
+    uint32_t *hist = scratch;
+    uint32_t *offs = scratch + hn;
+    uint32_t *sc = scratch + 2 * hn + 1;
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        const K *ki = cur ? k1 : k0;
+        const uint32_t *vi = cur ? v1 : v0;
+        K *ko = cur ? k0 : k1;
+        uint32_t *vo = cur ? v0 : v1;
+        k_radix_hist<K><<<nb, kRadixThreads, 0, st>>>(ki, n, shift, hist, nb);
+        launched += 1 + exclusive_scan(hist, nullptr, offs, hn, sc, st);
+        k_radix_scatter<K><<<nb, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, offs, nb);
+        launched += 1;
+        cur ^= 1;
+    }
+    *in_second = cur;
+    return launched;
+}
+
+int radix_sort_u32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t n, int bits,
+                   uint32_t *scratch, cudaStream_t st, int *in_second) {
+    return radix_sort<uint32_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second);
+}
+
+int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint32_t n, int bits,
+                   uint32_t *scratch, cudaStream_t st, int *in_second) {
+    return radix_sort<uint16_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second);
+}
+
+// ---------------------------------------------------------------------------
+// pair emission in depth order, tile ranges, live count
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *__restrict__ order,
+                                                    const uint32_t *__restrict__ pair_off,
+                                                    const uint2 *__restrict__ rect, int tiles_x,
+                                                    uint16_t *__restrict__ ptile,
+                                                    uint32_t *__restrict__ pval) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t o = pair_off[i];
+    const uint32_t e = pair_off[i + 1];
+    if (o == e) return;
+    const uint32_t s = order[i];
+    const uint2 rc = rect[s];
+    const uint32_t x0 = rc.x & 0xFFFFu, y0 = rc.x >> 16, x1 = rc.y & 0xFFFFu, y1 = rc.y >> 16;
+    for (uint32_t ty = y0; ty <= y1; ++ty)
+        for (uint32_t tx = x0; tx <= x1; ++tx) {
+            if (o >= e) return;
+            ptile[o] = (uint16_t)(ty * (uint32_t)tiles_x + tx);
+            pval[o] = s;
+            ++o;
+        }
+}
+
+int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *pair_off,
+                      const uint2 *rect, int tiles_x, uint16_t *ptile, uint32_t *pval,
+                      cudaStream_t st) {
+    if (n_splats == 0) return 0;
+    k_emit_pairs<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, order, pair_off, rect, tiles_x,
+                                                          ptile, pval);
+    return 1;
+}
+
+__global__ void __launch_bounds__(256) k_tile_ranges(uint32_t n, const uint16_t *__restrict__ ptile,
+                                                     uint2 *__restrict__ ranges) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint16_t t = ptile[i];
+    if (i == 0 || ptile[i - 1] != t) ranges[t].x = i;
+    if (i == n - 1 || ptile[i + 1] != t) ranges[t].y = i + 1;
+}
+
+int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, cudaStream_t st) {
+    if (n_pairs == 0) return 0;
+    k_tile_ranges<<<(n_pairs + 255) / 256, 256, 0, st>>>(n_pairs, ptile, ranges);
+    return 1;
+}
+
+__global__ void __launch_bounds__(256) k_count_live(uint32_t n, const uint32_t *__restrict__ keys,
+                                                    int32_t *__restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool live = keys[i] != 0xFFFFFFFFu;
+    const bool next_live = i + 1 < n && keys[i + 1] != 0xFFFFFFFFu;
+    if (i == 0 && !live) *out = 0;
+    if (live && !next_live) *out = (int32_t)(i + 1);
+}
+
+int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cudaStream_t st) {
+    cudaMemsetAsync(out, 0, sizeof(int32_t), st);
+    if (n == 0) return 0;
+    k_count_live<<<(n + 255) / 256, 256, 0, st>>>(n, sorted_keys, out);
+    return 1;
+}
+
+}  // namespace cs

@@ -1,0 +1,124 @@
+"""Helpers of the GPU-vs-oracle parity tests (host side only)."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+TOL_MAX_ABS = 2e-3   # per-pixel RGB(A) bound on non-boundary pixels (FP32 path)
+TOL_PSNR_DB = 60.0   # over all pixels
+
+
+def splat_ids(r):
+    """(instance, gaussian, template, level) of every GPU splat id."""
+    groups = r.debug("groups")
+    vis = r.debug("visible")
+    S = int(sum(int(g[3]) * int(g[4]) for g in groups))
+    inst = np.full(S, -1, np.int64)
+    gau = np.full(S, -1, np.int64)
+    lvl = np.full(S, -1, np.int64)
+    for tpl, lv, slot0, nslots, ng, splat0 in groups:
+        s = np.arange(int(nslots) * int(ng))
+        inst[splat0 + s] = vis[slot0 + s // ng]
+        gau[splat0 + s] = s % ng
+        lvl[splat0 + s] = lv
+    return inst, gau, lvl
+
+
+def gpu_live(r, S):
+    order = r.debug("depth_order").astype(np.int64)
+    keys = r.debug("depth_keys")
+    live = np.zeros(S, bool)
+    live[order] = keys != 0xFFFFFFFF
+    return live
+
+
+def compare_splats(r, sc, os_=None, max_instances=None):
+    """Per-splat errors of the GPU records against the oracle, over GPU
+    splats whose instance the oracle also projects.  Returns a dict of
+    maxima and the per-splat arrays used for the tile-list checks."""
+    os_ = os_ or oracle.OracleScene(sc)
+    rec = r.debug("records").astype(np.float64)
+    S = rec.shape[0]
+    inst, gau, lvl = splat_ids(r)
+    live = gpu_live(r, S)
+    out = dict(duv=0.0, conic_rel=0.0, depth_rel=0.0, drgb=0.0, radius_mismatch=0, radius_boundary=0,
+               live_mismatch=0, n=0)
+    insts = np.unique(inst)
+    if max_instances is not None:
+        insts = insts[:max_instances]
+    ref = {}
+    for i in insts:
+        p = oracle.project_instance(os_, int(i))
+        ref[int(i)] = p
+        m = np.nonzero(inst == i)[0]
+        g = gau[m]
+        ok_o = p["valid"][g] == 1
+        ok_g = live[m]
+        both = ok_o & ok_g
+        # a splat live on one side only must be a boundary case (checked by caller via counts)
+        out["live_mismatch"] += int((ok_o != ok_g).sum())
+        if not both.any():
+            continue
+        mm, gg = m[both], g[both]
+        R = rec[mm]
+        duv = np.abs(R[:, 0:2] - p["uv"][gg]).max()
+        con = np.stack([R[:, 2], R[:, 3], R[:, 4]], 1)
+        cr = (np.abs(con - p["conic"][gg]) / np.maximum(np.abs(p["conic"][gg]).max(1, keepdims=True), 1e-30)).max()
+        dr = (np.abs(R[:, 7] - p["depth"][gg]) / np.abs(p["depth"][gg])).max()
+        drgb = np.abs(R[:, 8:11] - p["rgb"][gg]).max()
+        rad_g = R[:, 6].astype(np.int64)
+        rad_o = p["radius"][gg]
+        mis = rad_g != rad_o
+        near_int = np.abs(p["r_exact"][gg] - np.round(p["r_exact"][gg])) < 1e-3
+        out["radius_mismatch"] += int(mis.sum())
+        out["radius_boundary"] += int((mis & ~near_int).sum())
+        out["duv"] = max(out["duv"], float(duv))
+        out["conic_rel"] = max(out["conic_rel"], float(cr))
+        out["depth_rel"] = max(out["depth_rel"], float(dr))
+        out["drgb"] = max(out["drgb"], float(drgb))
+        out["n"] += int(both.sum())
+    out["ref"] = ref
+    out["inst"], out["gau"], out["live"], out["rec"] = inst, gau, live, rec
+    return out
+
+
+def eps_from(errs) -> "oracle._Eps":
+    """Boundary windows from measured per-splat errors: 4x each error (floors
+    keep them positive).  The exponent window bounds |dq| <= 6.1 |duv| +
+    5.6 |dQ|/|Q| for the exponents that matter (|q| <= ln 255 + 0.1, conic
+    eigenvalues <= 1/0.3)."""
+    duv = max(errs["duv"], 1e-6)
+    cr = max(errs["conic_rel"], 1e-8)
+    return oracle.default_eps(px=4 * duv + 1e-6, q=4 * (6.1 * duv + 5.6 * cr) + 1e-6,
+                              radius=max(4 * 0.5 * cr * 100.0, 1e-5),
+                              depth_rel=max(4 * errs["depth_rel"], 1e-7), near_z=1e-5)
+
+
+def compare_images(got, ref):
+    """got [H,W,4] float32 (GPU), ref: oracle.render output.  Returns a
+    report dict."""
+    g = np.asarray(got, np.float64)
+    d = np.abs(g - ref["rgba"])
+    boundary = ref["flags"] != 0
+    ok = ~boundary
+    mse = float(np.mean(d ** 2))
+    rep = dict(max_abs=float(d[ok].max()) if ok.any() else 0.0,
+               max_abs_all=float(d.max()),
+               psnr=float(10 * np.log10(1.0 / max(mse, 1e-30))),
+               boundary_px=int(boundary.sum()), boundary_frac=float(boundary.mean()),
+               covered_frac=float((ref["rgba"][..., 3] > 0).mean()),
+               nonfinite=int((~np.isfinite(g)).sum()))
+    return rep
+
+
+def tile_lists_gpu(r, inst, gau):
+    """{tile: int64 keys instance << 32 | gaussian} in GPU order."""
+    rng = r.debug("tile_ranges").astype(np.int64)
+    vals = r.debug("pair_splats").astype(np.int64)
+    out = {}
+    for t, (a, b) in enumerate(rng):
+        if b > a:
+            s = vals[a:b]
+            out[t] = (inst[s] << 32) | gau[s]
+    return out

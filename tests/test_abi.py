@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports
+every function include/crowdsplat.h declares; host-only calls behave."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "crowdsplat.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cs_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2501_17792_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("cs_create", "cs_destroy", "cs_upload_templates", "cs_set_lod", "cs_set_instances",
+                 "cs_render", "cs_render_to_host", "cs_get_stage_times", "cs_memory_stats",
+                 "cs_last_error", "cs_debug_read", "cs_version"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2501_17792_gb300 import binding
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in binding.SIGNATURES, name
+
+
+def test_library_is_built_for_sm103a():
+    from paper_2501_17792_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_host_only_calls(lib):
+    lib.cs_version.restype = C.c_char_p
+    assert b"sm_103a" in lib.cs_version()
+    lib.cs_last_error.restype = C.c_char_p
+    lib.cs_last_error.argtypes = [C.c_void_p]
+    assert lib.cs_last_error(None) == b"null context"
+    lib.cs_destroy.argtypes = [C.c_void_p]
+    lib.cs_destroy(None)  # accepted
+
+
+def test_create_rejects_bad_arguments_without_touching_a_gpu(lib):
+    from paper_2501_17792_gb300 import binding
+    L = binding.load()
+    h = C.c_void_p()
+    assert L.cs_create(C.byref(h), None) == binding.CS_ERR_ARG
+    p = binding.CreateParams(device=0, stream=None, skin_mode=7, sh_frame=0, instance_cull=1, stage_timing=0)
+    assert L.cs_create(C.byref(h), C.byref(p)) == binding.CS_ERR_ARG
+    p = binding.CreateParams(device=0, stream=None, skin_mode=0, sh_frame=5, instance_cull=1, stage_timing=0)
+    assert L.cs_create(C.byref(h), C.byref(p)) == binding.CS_ERR_ARG
+    assert not h.value
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    from paper_2501_17792_gb300 import binding
+    saved = binding._lib
+    try:
+        binding._lib = None
+        with pytest.raises(RuntimeError, match="no CPU fallback"):
+            binding.load(str(tmp_path / "missing.so"))
+    finally:
+        binding._lib = saved
