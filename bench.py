@@ -337,6 +337,8 @@ def main():
     ap.add_argument("--oracle-stride", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small crowd (debugging)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="quarter crowd (875 instances, 960x540) for full ncu captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", 0))
@@ -345,6 +347,8 @@ def main():
     from paper_2501_17792_gb300 import scene as S
     if args.small:
         sc = S.crowd(n_templates=2, n_gauss=4096, cols=10, rows=10, width=640, height=360)
+    elif args.profile_case:
+        sc = S.crowd(cols=25, rows=35, width=960, height=540)
     else:
         sc = S.crowd()
     if args.impl == "reference":

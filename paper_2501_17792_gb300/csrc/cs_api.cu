@@ -633,8 +633,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->pval, Pa, "pair splats"));
     CS_TRY(ensure(ctx, ctx->pval2, Pa, "pair splats (ping-pong)"));
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Pa), radix_scratch_words(Sa)), "scratch"));
-    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, ctx->pair_off.p, ctx->rect.p, cp.tiles_x,
-                                 ctx->ptile.p, ctx->pval.p, st);
+    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, ctx->pair_off.p, ctx->rec.p, cam->width,
+                                             cam->height, cp.tiles_x, ctx->ptile.p, ctx->pval.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[5], st));
     // 6. stable sort of the pairs by tile
     int pb = 0;

@@ -421,17 +421,26 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
             const float u = cam.fx * tx * iz + cam.cx;
             const float v = cam.fy * ty * iz + cam.cy;
             // pixels with centre inside the support box, clipped to the image
-            float fx0 = fmaxf(ceilf(u - r - 0.5f), 0.0f);
-            float fx1 = fminf(floorf(u + r - 0.5f), (float)(cam.W - 1));
-            float fy0 = fmaxf(ceilf(v - r - 0.5f), 0.0f);
-            float fy1 = fminf(floorf(v + r - 0.5f), (float)(cam.H - 1));
-            live = r > 0.0f && fx0 <= fx1 && fy0 <= fy1 && isfinite(u) && isfinite(v) &&
+            int px0, px1, py0, py1;
+            box_range(u, r, cam.W, px0, px1);
+            box_range(v, r, cam.H, py0, py1);
+            live = r > 0.0f && px0 <= px1 && py0 <= py1 && isfinite(u) && isfinite(v) &&
                    isfinite(r) && isfinite(cA) && isfinite(cB) && isfinite(cC);
             if (live) {
-                const uint32_t x0 = (uint32_t)fx0 >> 4, x1 = (uint32_t)fx1 >> 4;
-                const uint32_t y0 = (uint32_t)fy0 >> 4, y1 = (uint32_t)fy1 >> 4;
-                rc = make_uint2(x0 | (y0 << 16), x1 | (y1 << 16));
-                nt = (x1 - x0 + 1) * (y1 - y0 + 1);
+                // tiles of the box holding a pixel the compositing would use
+                const float fcut = splat_fcut(mo.w);
+                const int x0 = px0 >> 4, x1 = px1 >> 4, y0 = py0 >> 4, y1 = py1 >> 4;
+                for (int yy = y0; yy <= y1; ++yy) {
+                    const int qy0 = max(yy * kTile, py0), qy1 = min(yy * kTile + kTile - 1, py1);
+                    for (int xx = x0; xx <= x1; ++xx) {
+                        const int qx0 = max(xx * kTile, px0), qx1 = min(xx * kTile + kTile - 1, px1);
+                        nt += splat_rect_hits(u, v, cA, cB, cC, fcut, qx0, qx1, qy0, qy1) ? 1u : 0u;
+                    }
+                }
+                rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+                live = nt > 0;
+            }
+            if (live) {
                 // colour: SH at the viewing direction (camera centre -> mean)
                 float ddx, ddy, ddz;
                 const float4 cl = __ldg(reinterpret_cast<const float4 *>(Cloc) + inst);

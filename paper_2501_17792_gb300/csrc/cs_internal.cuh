@@ -80,6 +80,57 @@ struct TemplateArrays {
     const float4 *sh;
 };
 
+// ---------------------------------------------------------------------------
+// Exact (conservative) splat-rectangle test shared by binning and blending.
+//
+// A splat contributes to a pixel only where alpha = o e^q >= 1/255, i.e. where
+// f(d) = A dx^2 + 2 B dx dy + C dy^2 <= fcut = 2 ln(255 o) (d = pixel centre -
+// splat centre, conic (A, B, C)).  splat_rect_hits() tells whether f reaches
+// fcut + 2 * kAlphaMargin anywhere on the continuous rectangle spanned by the
+// pixel centres [px0, px1] x [py0, py1]: the minimum of the positive-definite
+// form over a rectangle is 0 if the centre is inside, else it lies on an
+// edge, where it is a clamped 1-D quadratic.  A rectangle that fails holds no
+// pixel the compositing would use (the margin absorbs FP32 rounding), so
+// dropping it leaves every pixel unchanged.  Explicitly rounded intrinsics
+// keep the result bit-identical in every kernel that calls it.
+// ---------------------------------------------------------------------------
+constexpr float kAlphaMargin = 2e-3f;  // in the exponent: alpha within 0.2 %
+
+__device__ __forceinline__ float splat_fcut(float opacity) {
+    // 2 (ln(255 o) + margin); negative when o < 1/255 (never contributes)
+    return __fmul_rn(2.0f, __fadd_rn(logf(__fmul_rn(255.0f, opacity)), kAlphaMargin));
+}
+
+__device__ __forceinline__ float edge_quad(float A, float B, float C, float a, float lo, float hi) {
+    // min over t in [lo, hi] of A a^2 + 2 B a t + C t^2 (C > 0)
+    float t = __fdiv_rn(-__fmul_rn(B, a), C);
+    t = fminf(fmaxf(t, lo), hi);
+    return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, a), a), __fmul_rn(__fmul_rn(2.0f, B), __fmul_rn(a, t))),
+                     __fmul_rn(__fmul_rn(C, t), t));
+}
+
+__device__ __forceinline__ bool splat_rect_hits(float u, float v, float A, float B, float C, float fcut,
+                                                int px0, int px1, int py0, int py1) {
+    if (!(fcut >= 0.0f)) return false;
+    const float a1 = __fsub_rn(__fadd_rn((float)px0, 0.5f), u), a2 = __fsub_rn(__fadd_rn((float)px1, 0.5f), u);
+    const float b1 = __fsub_rn(__fadd_rn((float)py0, 0.5f), v), b2 = __fsub_rn(__fadd_rn((float)py1, 0.5f), v);
+    if (a1 <= 0.0f && a2 >= 0.0f && b1 <= 0.0f && b2 >= 0.0f) return true;
+    float f = edge_quad(A, B, C, a1, b1, b2);
+    f = fminf(f, edge_quad(A, B, C, a2, b1, b2));
+    f = fminf(f, edge_quad(C, B, A, b1, a1, a2));
+    f = fminf(f, edge_quad(C, B, A, b2, a1, a2));
+    return f <= fcut;
+}
+
+// Pixel range [lo, hi] of a splat's support box on one axis (centres within
+// r of the mean), clipped to [0, size - 1]; lo > hi when empty.
+__device__ __forceinline__ void box_range(float c, float r, int size, int &lo, int &hi) {
+    const float l = fmaxf(ceilf(__fsub_rn(__fsub_rn(c, r), 0.5f)), 0.0f);
+    const float h = fminf(floorf(__fsub_rn(__fadd_rn(c, r), 0.5f)), (float)(size - 1));
+    lo = (int)l;
+    hi = (l <= h) ? (int)h : (int)l - 1;
+}
+
 // meta words written by the cull kernel and read back by the host
 enum MetaIndex { kMetaVisible = 0, kMetaGroups = 1, kMetaSplats = 2, kMetaLevel0 = 3, kMetaWords = 8 };
 
@@ -113,8 +164,8 @@ int radix_sort_u32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint3
 int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint32_t n, int bits,
                    uint32_t *scratch, cudaStream_t st, int *in_second);
 int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *pair_off,
-                       const uint2 *rect, int tiles_x, uint16_t *ptile, uint32_t *pval,
-                       cudaStream_t st);
+                      const float4 *rec, int W, int H, int tiles_x, uint16_t *ptile, uint32_t *pval,
+                      cudaStream_t st);
 int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, cudaStream_t st);
 int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cudaStream_t st);
 

@@ -9,6 +9,39 @@ TOL_MAX_ABS = 2e-3   # per-pixel RGB(A) bound on non-boundary pixels (FP32 path)
 TOL_PSNR_DB = 60.0   # over all pixels
 
 
+def rect_fmin(u, v, A, B, C, x0, x1, y0, y1):
+    """FP64 minimum of A dx^2 + 2 B dx dy + C dy^2 over the rectangle spanned
+    by the pixel centres [x0, x1] x [y0, y1] (inclusive pixel indices),
+    d = point - (u, v).  Vectorised over splats."""
+    u, v, A, B, C = (np.asarray(t, np.float64) for t in (u, v, A, B, C))
+    a1, a2 = np.asarray(x0) + 0.5 - u, np.asarray(x1) + 0.5 - u
+    b1, b2 = np.asarray(y0) + 0.5 - v, np.asarray(y1) + 0.5 - v
+
+    def edge(P, Q, R, a, lo, hi):
+        t = np.clip(-Q * a / R, lo, hi)
+        return P * a * a + 2 * Q * a * t + R * t * t
+
+    f = np.minimum.reduce([edge(A, B, C, a1, b1, b2), edge(A, B, C, a2, b1, b2),
+                           edge(C, B, A, b1, a1, a2), edge(C, B, A, b2, a1, a2)])
+    inside = (a1 <= 0) & (a2 >= 0) & (b1 <= 0) & (b2 >= 0)
+    return np.where(inside, 0.0, f)
+
+
+def unreachable(p, g, W, H, slack):
+    """True where splat g (oracle projection p) has no pixel centre of its
+    box with alpha >= 1/255 (up to `slack` in the exponent)."""
+    u, v = p["uv"][g, 0], p["uv"][g, 1]
+    r = p["radius"][g]
+    x0 = np.maximum(0, np.ceil(u - r - 0.5)); x1 = np.minimum(W - 1, np.floor(u + r - 0.5))
+    y0 = np.maximum(0, np.ceil(v - r - 0.5)); y1 = np.minimum(H - 1, np.floor(v + r - 0.5))
+    con = p["conic"][g]
+    f = rect_fmin(u, v, con[:, 0], con[:, 1], con[:, 2], x0, x1, y0, y1)
+    o = p["opacity"][g]
+    with np.errstate(divide="ignore"):
+        cut = 2 * np.log(255.0 * o)
+    return (f > cut - 2 * slack) | (o * 255.0 < 1.0)
+
+
 def splat_ids(r):
     """(instance, gaussian, template, level) of every GPU splat id."""
     groups = r.debug("groups")
@@ -43,7 +76,8 @@ def compare_splats(r, sc, os_=None, max_instances=None):
     inst, gau, lvl = splat_ids(r)
     live = gpu_live(r, S)
     out = dict(duv=0.0, conic_rel=0.0, depth_rel=0.0, drgb=0.0, radius_mismatch=0, radius_boundary=0,
-               live_mismatch=0, n=0)
+               live_mismatch=0, n=0, culled_unreachable=0)
+    W, H = sc.camera.width, sc.camera.height
     insts = np.unique(inst)
     if max_instances is not None:
         insts = insts[:max_instances]
@@ -56,8 +90,14 @@ def compare_splats(r, sc, os_=None, max_instances=None):
         ok_o = p["valid"][g] == 1
         ok_g = live[m]
         both = ok_o & ok_g
-        # a splat live on one side only must be a boundary case (checked by caller via counts)
-        out["live_mismatch"] += int((ok_o != ok_g).sum())
+        # the GPU also drops splats no pixel of which reaches alpha 1/255;
+        # anything else live on one side only is a boundary case (counted)
+        dropped = ok_o & ~ok_g
+        if dropped.any():
+            un = unreachable(p, g[dropped], W, H, slack=1e-3)
+            out["culled_unreachable"] += int(un.sum())
+            out["live_mismatch"] += int((~un).sum())
+        out["live_mismatch"] += int((~ok_o & ok_g).sum())
         if not both.any():
             continue
         mm, gg = m[both], g[both]

@@ -59,7 +59,7 @@ def full_check(sc, *, skin_mode=0, sh_frame=0, label="", max_boundary=0.08, **kw
     print(f"\n[{label}] splats={st['splats']} live={st['splats_live']} pairs={st['pairs']} "
           f"duv={errs['duv']:.2e} conic_rel={errs['conic_rel']:.2e} depth_rel={errs['depth_rel']:.2e} "
           f"drgb={errs['drgb']:.2e} radius_mismatch={errs['radius_mismatch']} "
-          f"live_mismatch={errs['live_mismatch']} | max_abs={rep['max_abs']:.2e} "
+          f"live_mismatch={errs['live_mismatch']} culled_unreachable={errs['culled_unreachable']} | max_abs={rep['max_abs']:.2e} "
           f"(all {rep['max_abs_all']:.2e}) psnr={rep['psnr']:.1f} boundary={rep['boundary_px']} "
           f"({100 * rep['boundary_frac']:.2f}%) covered={100 * rep['covered_frac']:.1f}%")
     assert rep["nonfinite"] == 0
@@ -110,6 +110,7 @@ def test_tile_lists_match_oracle():
     gl = PU.tile_lists_gpu(r, inst, gau)
     ol = oracle.tile_lists(os_, 16)
     p = oracle.project_instance(os_, 0)
+    W = H = 128
     boundary = set()
     depth = {}
     for g in range(p["count"]):
@@ -120,14 +121,31 @@ def test_tile_lists_match_oracle():
         e = np.array([u - rr - 0.5, u + rr - 0.5, v - rr - 0.5, v + rr - 0.5])
         if (np.abs(e - np.round(e)) < eps.px).any() or abs(p["r_exact"][g] - round(p["r_exact"][g])) < eps.radius:
             boundary.add(key)
-    n_pairs = 0
-    perms = 0
+    n_pairs = n_dropped = perms = 0
+    tiles_x = (W + 15) // 16
     for t in set(gl) | set(ol):
         G = [int(k) for k in gl.get(t, [])]
         O = [int(k) for k in ol.get(t, [])]
         n_pairs += len(G)
-        diff = set(G) ^ set(O)
-        assert diff <= boundary, (t, sorted(diff - boundary)[:5])
+        extra = set(G) - set(O)
+        assert extra <= boundary, (t, sorted(extra - boundary)[:5])
+        # pairs the GPU left out: the splat reaches alpha 1/255 nowhere in
+        # the tile's part of its box (FP64 check)
+        missing = sorted(set(O) - set(G) - boundary)
+        if missing:
+            g = np.array(missing)
+            tx, ty = t % tiles_x, t // tiles_x
+            u, v = p["uv"][g, 0], p["uv"][g, 1]
+            rr = p["radius"][g]
+            x0 = np.maximum(tx * 16, np.maximum(0, np.ceil(u - rr - 0.5)))
+            x1 = np.minimum(tx * 16 + 15, np.minimum(W - 1, np.floor(u + rr - 0.5)))
+            y0 = np.maximum(ty * 16, np.maximum(0, np.ceil(v - rr - 0.5)))
+            y1 = np.minimum(ty * 16 + 15, np.minimum(H - 1, np.floor(v + rr - 0.5)))
+            con = p["conic"][g]
+            f = PU.rect_fmin(u, v, con[:, 0], con[:, 1], con[:, 2], x0, x1, y0, y1)
+            cut = 2 * np.log(255.0 * p["opacity"][g])
+            assert (f > cut - 2e-3).all(), (t, g[f <= cut - 2e-3][:5])
+            n_dropped += len(missing)
         common = set(G) & set(O)
         Gc = [k for k in G if k in common]
         Oc = [k for k in O if k in common]
@@ -137,7 +155,8 @@ def test_tile_lists_match_oracle():
             # the GPU order may differ only inside runs of near-equal depth
             assert (np.diff(d) >= -eps.depth_rel * d[1:] * 4).all(), t
     assert n_pairs > 1000
-    print(f"\n[tile lists] tiles={len(gl)} pairs={n_pairs} boundary_splats={len(boundary)} tiles_with_tie_perms={perms}")
+    print(f"\n[tile lists] tiles={len(gl)} pairs={n_pairs} dropped_unreachable={n_dropped} "
+          f"boundary_splats={len(boundary)} tiles_with_tie_perms={perms}")
 
 
 # ---------------------------------------------------------------------------
@@ -345,7 +364,10 @@ def test_paper_scale_sort_properties(paper_scene):
     ntiles = (rects[:, 2] - rects[:, 0] + 1) * (rects[:, 3] - rects[:, 1] + 1)
     lv = np.zeros(order.size, bool)
     lv[order] = keys != 0xFFFFFFFF
-    assert int(ntiles[lv].sum()) == st["pairs"]
+    # pairs are the box tiles that hold a reachable pixel: at most the box tiles
+    assert 0 < st["pairs"] <= int(ntiles[lv].sum())
+    per_splat = np.bincount(r.debug("pair_splats").astype(np.int64), minlength=order.size)
+    assert (per_splat <= ntiles).all() and (per_splat[lv] >= 1).all() and (per_splat[~lv] == 0).all()
     tiles = r.debug("pair_tiles").astype(np.int64)
     vals = r.debug("pair_splats").astype(np.int64)
     assert (np.diff(tiles) >= 0).all()
