@@ -179,6 +179,27 @@ int cs_render(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats
  * after the copy completes.  Same errors as cs_render. */
 int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_frame_stats *stats);
 
+/* cs_render without any device allocation, for callers that may not
+ * allocate device memory while a frame is produced: real-time render
+ * threads where cudaMalloc's implicit synchronisation and latency are not
+ * allowed, and engines that hand the library a fixed memory budget up
+ * front.  CrowdSplat has no counterpart of this call; it renders exactly
+ * what cs_render renders, with the per-frame scratch (splat records, sort
+ * buffers, pair lists, tile ranges) taken from one static device array of
+ * about 8.9 MB that every GPU loading the library holds until the process
+ * exits.  Limits per frame: 65,536 splats, 262,144 (tile, splat) pairs,
+ * 16,384 tiles (e.g. 2048 x 2048); larger frames fail with CS_ERR_CAPACITY
+ * and a message naming the limit, leaving rgba_out unwritten.  The
+ * instance buffers come from cs_set_instances, which allocates as usual.
+ * The first call on a device looks the array's device address up (CUDA may
+ * load the library's device code then): make that first call before any
+ * stream capture.  All contexts of the process share the array and it
+ * keeps the previous call's contents, so calls that overlap on the GPU
+ * (other streams, other contexts on the same device) race; serialise them.
+ * No stage times are recorded, and cs_debug_read is unspecified after this
+ * call until the next cs_render.  Arguments and other errors as cs_render. */
+int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats);
+
 /* Per-stage milliseconds (needs stage_timing = 1), measured with CUDA events
  * on the context's stream: ms[0..n) = fk, cull+lod, skin+project, depth
  * sort, pair emit, tile sort, tile ranges, blend.  average = 0: the last

@@ -73,6 +73,7 @@ SIGNATURES = {
     "cs_set_instances": (C.c_int, [_P, C.c_int32, _P, _P, _P, C.c_int32]),
     "cs_render": (C.c_int, [_P, C.POINTER(Camera), _P, C.POINTER(FrameStats)]),
     "cs_render_to_host": (C.c_int, [_P, C.POINTER(Camera), _P, C.POINTER(FrameStats)]),
+    "cs_render_static": (C.c_int, [_P, C.POINTER(Camera), _P, C.POINTER(FrameStats)]),
     "cs_get_stage_times": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]),
     "cs_memory_stats": (C.c_int, [_P, C.POINTER(MemoryStats)]),
     "cs_last_error": (C.c_char_p, [_P]),

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -773,6 +774,187 @@ int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size
     if (n > 0) {
         if (!host_dst || !src) return fail(ctx, CS_ERR_ARG, "NULL destination or empty buffer");
         CS_CUDA(cudaMemcpy(host_dst, src, n, cudaMemcpyDeviceToHost));
+    }
+    return CS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// cs_render_static: cs_render with its per-frame scratch in one fixed device
+// array instead of context-owned allocations.  For callers that must not
+// allocate device memory during a frame (real-time threads with an
+// allocation ban, engines that own the GPU memory budget).  The array is a
+// file-scope __device__ object: every GPU that loads the library holds it
+// until the process exits.  Host code cannot use its name as a device
+// address; the address comes from cudaGetSymbolAddress, once per device.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+constexpr size_t kStaticSplats = 65536;   // splats of visible instances per frame
+constexpr size_t kStaticPairs = 262144;   // (tile, splat) pairs per frame
+constexpr size_t kStaticTiles = 16384;    // 16x16 tiles per image (e.g. 2048 x 2048)
+constexpr size_t kStaticScratchWords = 98304;  // histograms and scan partials
+
+constexpr size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t kOffRec = 0;
+constexpr size_t kOffKey = kOffRec + a256(kStaticSplats * 3 * sizeof(float4));
+constexpr size_t kOffIds = kOffKey + a256(kStaticSplats * 4);
+constexpr size_t kOffKey2 = kOffIds + a256(kStaticSplats * 4);
+constexpr size_t kOffIds2 = kOffKey2 + a256(kStaticSplats * 4);
+constexpr size_t kOffRect = kOffIds2 + a256(kStaticSplats * 4);
+constexpr size_t kOffNtiles = kOffRect + a256(kStaticSplats * sizeof(uint2));
+constexpr size_t kOffPairOff = kOffNtiles + a256(kStaticSplats * 4);
+constexpr size_t kOffPtile = kOffPairOff + a256((kStaticSplats + 1) * 4);
+constexpr size_t kOffPtile2 = kOffPtile + a256(kStaticPairs * 2);
+constexpr size_t kOffPval = kOffPtile2 + a256(kStaticPairs * 2);
+constexpr size_t kOffPval2 = kOffPval + a256(kStaticPairs * 4);
+constexpr size_t kOffRanges = kOffPval2 + a256(kStaticPairs * 4);
+constexpr size_t kOffScratch = kOffRanges + a256(kStaticTiles * sizeof(uint2));
+constexpr size_t kStaticBytes = kOffScratch + a256(kStaticScratchWords * 4);  // about 8.9 MB
+
+}  // namespace
+
+// The frame scratch of cs_render_static (file scope, internal linkage).
+static __device__ __align__(256) unsigned char g_static_frame[kStaticBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+constexpr int kStaticMaxDevices = 64;
+unsigned char *g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of g_static_frame on the current device (looked up once per
+// device; the device must be current).
+int static_frame_address(cs_ctx *ctx, unsigned char **out) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (ctx->device < 0 || ctx->device >= kStaticMaxDevices)
+        return fail(ctx, CS_ERR_ARG, "cs_render_static supports devices 0..%d", kStaticMaxDevices - 1);
+    if (!g_static_addr[ctx->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_frame);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return fail(ctx, CS_ERR_CUDA, "cudaGetSymbolAddress of the static frame scratch failed: %s",
+                        cudaGetErrorString(e));
+        }
+        g_static_addr[ctx->device] = static_cast<unsigned char *>(p);
+    }
+    *out = g_static_addr[ctx->device];
+    return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats) {
+    if (!ctx) return CS_ERR_ARG;
+    float4 *out = reinterpret_cast<float4 *>(rgba_out);
+    if (!cam || !out) return fail(ctx, CS_ERR_ARG, "NULL camera or output");
+    if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(ctx, CS_ERR_ARG, "rgba_out must be 16-byte aligned");
+    if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "no templates uploaded");
+    if (cam->width < 1 || cam->height < 1 || cam->width > CS_MAX_IMAGE_SIDE || cam->height > CS_MAX_IMAGE_SIDE)
+        return fail(ctx, CS_ERR_ARG, "image size %dx%d outside 1..%d", cam->width, cam->height, CS_MAX_IMAGE_SIDE);
+    if (!(cam->fx > 0.f && cam->fy > 0.f && cam->near_z > 0.f) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
+        return fail(ctx, CS_ERR_ARG, "focal lengths and near plane must be positive and finite");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(cam->R[i])) return fail(ctx, CS_ERR_ARG, "camera rotation not finite");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(cam->t[i])) return fail(ctx, CS_ERR_ARG, "camera translation not finite");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    unsigned char *base = nullptr;
+    CS_TRY(static_frame_address(ctx, &base));
+    cudaStream_t st = ctx->stream;
+    CamParams cp;
+    cam_params(ctx, cam, cp);
+    const int T = cp.tiles_x * cp.tiles_y;
+    if ((size_t)T > kStaticTiles)
+        return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: %d tiles exceed the static limit of %zu "
+                    "(image at most 2048 x 2048)", T, kStaticTiles);
+    const int I = ctx->n_inst;
+    float4 *rec = reinterpret_cast<float4 *>(base + kOffRec);
+    uint32_t *key = reinterpret_cast<uint32_t *>(base + kOffKey);
+    uint32_t *ids = reinterpret_cast<uint32_t *>(base + kOffIds);
+    uint32_t *key2 = reinterpret_cast<uint32_t *>(base + kOffKey2);
+    uint32_t *ids2 = reinterpret_cast<uint32_t *>(base + kOffIds2);
+    uint2 *rect = reinterpret_cast<uint2 *>(base + kOffRect);
+    uint32_t *ntiles = reinterpret_cast<uint32_t *>(base + kOffNtiles);
+    uint32_t *pair_off = reinterpret_cast<uint32_t *>(base + kOffPairOff);
+    uint16_t *ptile0 = reinterpret_cast<uint16_t *>(base + kOffPtile);
+    uint16_t *ptile1 = reinterpret_cast<uint16_t *>(base + kOffPtile2);
+    uint32_t *pval0 = reinterpret_cast<uint32_t *>(base + kOffPval);
+    uint32_t *pval1 = reinterpret_cast<uint32_t *>(base + kOffPval2);
+    uint2 *ranges = reinterpret_cast<uint2 *>(base + kOffRanges);
+    uint32_t *scratch = reinterpret_cast<uint32_t *>(base + kOffScratch);
+    int launched = 0;
+
+    // forward kinematics, LoD, cull and grouping (instance buffers were sized
+    // by cs_set_instances; nothing is allocated here)
+    if (I > 0) launched += launch_fk(I, ctx->n_tpl, ctx->tid.p, ctx->pose.p, ctx->d_tpl, ctx->max_depth, ctx->B.p, st);
+    int64_t S = 0;
+    int visible = 0, n_groups = 0, per_level[kMaxLevels] = {0, 0, 0, 0};
+    if (I > 0) {
+        launched += launch_cull_group(I, ctx->n_tpl, ctx->tid.p, ctx->root.p, ctx->d_tpl, cp, ctx->lod,
+                                      ctx->instance_cull, ctx->V.p, ctx->Cloc.p, ctx->vis.p, ctx->groups.p,
+                                      ctx->d_meta, st);
+        CS_CUDA(cudaGetLastError());
+        CS_CUDA(cudaMemcpyAsync(ctx->h_meta, ctx->d_meta, kMetaWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CS_CUDA(cudaStreamSynchronize(st));
+        visible = ctx->h_meta[kMetaVisible];
+        n_groups = ctx->h_meta[kMetaGroups];
+        S = ctx->h_meta[kMetaSplats];
+        for (int l = 0; l < kMaxLevels; ++l) per_level[l] = ctx->h_meta[kMetaLevel0 + l];
+    }
+    if ((size_t)S > kStaticSplats)
+        return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: %lld splats exceed the static limit of %zu",
+                    (long long)S, kStaticSplats);
+    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh};
+    if (S > 0)
+        launched += launch_project((int)S, ctx->groups.p, n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
+                                   ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
+                                   rec, key, ids, rect, ntiles, st);
+    if (radix_scratch_words((size_t)std::max<int64_t>(S, 1)) > kStaticScratchWords ||
+        scan_scratch_words((size_t)S + 1) > kStaticScratchWords)
+        return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: scratch too small for %lld splats", (long long)S);
+    int ob = 0;
+    if (S > 0) launched += radix_sort_u32(key, ids, key2, ids2, (uint32_t)S, 32, scratch, st, &ob);
+    uint32_t *order = ob ? ids2 : ids;
+    uint32_t *sorted_keys = ob ? key2 : key;
+    launched += exclusive_scan(ntiles, order, pair_off, (uint32_t)S, scratch, st);
+    if (stats && S > 0) launched += launch_count_live((uint32_t)S, sorted_keys, ctx->d_meta + kMetaWords - 1, st);
+    CS_CUDA(cudaGetLastError());
+    CS_CUDA(cudaMemcpyAsync(ctx->h_pairs, pair_off + S, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (stats) CS_CUDA(cudaMemcpyAsync(ctx->h_pairs + 1, ctx->d_meta + kMetaWords - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CS_CUDA(cudaStreamSynchronize(st));
+    const int64_t P = ctx->h_pairs[0];
+    if ((size_t)P > kStaticPairs)
+        return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: %lld pairs exceed the static limit of %zu",
+                    (long long)P, kStaticPairs);
+    if (radix_scratch_words((size_t)std::max<int64_t>(P, 1)) > kStaticScratchWords)
+        return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: scratch too small for %lld pairs", (long long)P);
+    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, pair_off, rec, cam->width, cam->height,
+                                             cp.tiles_x, ptile0, pval0, st);
+    int pb = 0;
+    if (P > 0) launched += radix_sort_u16(ptile0, pval0, ptile1, pval1, (uint32_t)P, bits_for((uint32_t)T),
+                                          scratch, st, &pb);
+    uint16_t *ptile = pb ? ptile1 : ptile0;
+    uint32_t *pval = pb ? pval1 : pval0;
+    // the array keeps the previous call's ranges: clear them
+    CS_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * T, st));
+    launched += launch_tile_ranges((uint32_t)P, ptile, ranges, st);
+    launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ranges, pval, rec, out, st);
+    CS_CUDA(cudaGetLastError());
+    if (stats) {
+        stats->instances = I;
+        stats->instances_visible = visible;
+        for (int l = 0; l < CS_MAX_LEVELS; ++l) stats->instances_per_level[l] = per_level[l];
+        stats->splats = S;
+        stats->splats_live = S > 0 ? (int64_t)ctx->h_pairs[1] : 0;
+        stats->pairs = P;
+        stats->tiles_x = cp.tiles_x;
+        stats->tiles_y = cp.tiles_y;
+        stats->kernel_launches = launched;
     }
     return CS_OK;
 }
