@@ -186,7 +186,7 @@ int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_fr
  * front.  CrowdSplat has no counterpart of this call; it renders exactly
  * what cs_render renders, with the per-frame scratch (splat records, sort
  * buffers, pair lists, tile ranges) taken from one static device array of
- * about 8.9 MB that every GPU loading the library holds until the process
+ * about 9.9 MB that every GPU loading the library holds until the process
  * exits.  Limits per frame: 65,536 splats, 262,144 (tile, splat) pairs,
  * 16,384 tiles (e.g. 2048 x 2048); larger frames fail with CS_ERR_CAPACITY
  * and a message naming the limit, leaving rgba_out unwritten.  The
@@ -224,8 +224,9 @@ const char *cs_last_error(const cs_ctx *ctx);
 #define CS_DBG_VISIBLE 2     /* int32 [V]: visible instance ids in group order         */
 #define CS_DBG_GROUPS 3      /* int32 [G][6]: template, level, first slot, slots,
                                 gaussians per slot, first splat                        */
-#define CS_DBG_RECORDS 4     /* float [S][12]: u, v, conic A, B, C, opacity, radius,
-                                depth, r, g, b, 0                                      */
+#define CS_DBG_RECORDS 4     /* float [S][16]: u, v, conic A, B, C, opacity, radius,
+                                depth, r, g, b, 0, reach x, reach y (pixel ranges lo | hi
+                                << 16 as float bits), fcut, log2 opacity              */
 #define CS_DBG_DEPTH_KEYS 5  /* uint32 [S]: depth bits in depth order, 0xFFFFFFFF = culled */
 #define CS_DBG_RECTS 6       /* uint16 [S][4]: tile rect x0, y0, x1, y1 (inclusive)    */
 #define CS_DBG_DEPTH_ORDER 7 /* uint32 [S]: splat ids sorted by depth                  */

@@ -596,7 +596,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     ctx->S = S;
     // 3. LBS + EWA projection + SH colour
     const size_t Sa = (size_t)std::max<int64_t>(S, 1);
-    CS_TRY(ensure(ctx, ctx->rec, Sa * 3, "splat records"));
+    CS_TRY(ensure(ctx, ctx->rec, Sa * kRecVec, "splat records"));
     CS_TRY(ensure(ctx, ctx->key, Sa, "depth keys"));
     CS_TRY(ensure(ctx, ctx->ids, Sa, "splat ids"));
     CS_TRY(ensure(ctx, ctx->key2, Sa, "depth keys (ping-pong)"));
@@ -634,8 +634,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->pval, Pa, "pair splats"));
     CS_TRY(ensure(ctx, ctx->pval2, Pa, "pair splats (ping-pong)"));
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Pa), radix_scratch_words(Sa)), "scratch"));
-    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, ctx->pair_off.p, ctx->rec.p, cam->width,
-                                             cam->height, cp.tiles_x, ctx->ptile.p, ctx->pval.p, st);
+    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, ctx->pair_off.p, ctx->rec.p, cp.tiles_x,
+                                             ctx->ptile.p, ctx->pval.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[5], st));
     // 6. stable sort of the pairs by tile
     int pb = 0;
@@ -759,7 +759,7 @@ int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size
         case CS_DBG_SKIN_B: src = ctx->B.p; size = (size_t)ctx->n_inst * kJoints * 12 * sizeof(float); break;
         case CS_DBG_VISIBLE: src = ctx->vis.p; size = (size_t)ctx->visible * sizeof(int32_t); break;
         case CS_DBG_GROUPS: src = ctx->groups.p; size = (size_t)ctx->n_groups * sizeof(Group); break;
-        case CS_DBG_RECORDS: src = ctx->rec.p; size = (size_t)ctx->S * 12 * sizeof(float); break;
+        case CS_DBG_RECORDS: src = ctx->rec.p; size = (size_t)ctx->S * kRecVec * sizeof(float4); break;
         case CS_DBG_DEPTH_KEYS: src = ctx->order_buf ? ctx->key2.p : ctx->key.p; size = (size_t)ctx->S * 4; break;
         case CS_DBG_RECTS: src = ctx->rect.p; size = (size_t)ctx->S * 8; break;
         case CS_DBG_DEPTH_ORDER: src = ctx->order_buf ? ctx->ids2.p : ctx->ids.p; size = (size_t)ctx->S * 4; break;
@@ -798,7 +798,7 @@ constexpr size_t kStaticScratchWords = 98304;  // histograms and scan partials
 
 constexpr size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t kOffRec = 0;
-constexpr size_t kOffKey = kOffRec + a256(kStaticSplats * 3 * sizeof(float4));
+constexpr size_t kOffKey = kOffRec + a256(kStaticSplats * kRecVec * sizeof(float4));
 constexpr size_t kOffIds = kOffKey + a256(kStaticSplats * 4);
 constexpr size_t kOffKey2 = kOffIds + a256(kStaticSplats * 4);
 constexpr size_t kOffIds2 = kOffKey2 + a256(kStaticSplats * 4);
@@ -811,7 +811,7 @@ constexpr size_t kOffPval = kOffPtile2 + a256(kStaticPairs * 2);
 constexpr size_t kOffPval2 = kOffPval + a256(kStaticPairs * 4);
 constexpr size_t kOffRanges = kOffPval2 + a256(kStaticPairs * 4);
 constexpr size_t kOffScratch = kOffRanges + a256(kStaticTiles * sizeof(uint2));
-constexpr size_t kStaticBytes = kOffScratch + a256(kStaticScratchWords * 4);  // about 8.9 MB
+constexpr size_t kStaticBytes = kOffScratch + a256(kStaticScratchWords * 4);  // about 9.9 MB
 
 }  // namespace
 
@@ -933,8 +933,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
                     (long long)P, kStaticPairs);
     if (radix_scratch_words((size_t)std::max<int64_t>(P, 1)) > kStaticScratchWords)
         return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: scratch too small for %lld pairs", (long long)P);
-    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, pair_off, rec, cam->width, cam->height,
-                                             cp.tiles_x, ptile0, pval0, st);
+    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, pair_off, rec, cp.tiles_x, ptile0, pval0, st);
     int pb = 0;
     if (P > 0) launched += radix_sort_u16(ptile0, pval0, ptile1, pval1, (uint32_t)P, bits_for((uint32_t)T),
                                           scratch, st, &pb);

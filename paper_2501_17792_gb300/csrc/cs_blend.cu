@@ -11,27 +11,46 @@
 // tile size.
 //
 // One CTA per tile, one thread per pixel, each warp an 8x4 block of the tile.
-// Warps are independent (no CTA-wide barrier): a warp walks the tile's
-// depth-ordered pair list 32 entries at a time; each lane loads one splat
-// (the 8 warps of a tile share the loads through L1), keeps it if the splat
-// can reach a pixel of the warp's block (box overlap, then the exact
-// rectangle test of binning), and stages kept splats in the warp's slice of
-// shared memory with the exponent pre-scaled to base 2 (e^q = 2^(q log2 e),
-// evaluated with the hardware ex2).  The warp then composites the kept splats
-// in order and leaves the tile once all 32 pixels are saturated.
+// The CTA walks the tile's depth-ordered pairs in batches of 256, software
+// pipelined: while the warps composite batch k from one half of a shared
+// double buffer, each thread holds in registers the record it loaded for
+// batch k+1; after compositing it stages that record into the other half
+// (with the warp blocks its reach box overlaps as an 8-bit mask, and the
+// exponent pre-scaled to base 2: e^q = 2^(q log2 e) on the hardware ex2
+// unit) and issues the loads of batch k+2, so global latency hides behind a
+// whole batch of compositing.  Each warp walks only the splats marked for
+// its block (ballot over 32 at a time); the CTA leaves once every pixel of
+// the tile is saturated.
 #include "cs_internal.cuh"
 
 namespace cs {
 
 constexpr int kBlendThreads = kTile * kTile;
-constexpr int kBlendWarps = kBlendThreads / 32;
 constexpr int kBlockW = 8, kBlockH = 4;  // pixels per warp
 constexpr float kLog2e = 1.4426950408889634f;
 
+// e^q evaluated as 2^(q log2 e) on the hardware ex2 unit
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+struct StagedRecord {
+    float4 a, b, c, q;  // {u, v, A, B}, {C, o, r, depth}, {r, g, b, -}, {reach x, reach y, fcut, log2 o}
+    bool have;
+};
+
+__device__ __forceinline__ void load_record(StagedRecord &r, const uint32_t *__restrict__ pval,
+                                            const float4 *__restrict__ rec, uint32_t idx, uint32_t end) {
+    r.have = idx < end;
+    if (r.have) {
+        const float4 *p = rec + (size_t)__ldg(pval + idx) * kRecVec;
+        r.a = __ldg(p + 0);
+        r.b = __ldg(p + 1);
+        r.c = __ldg(p + 2);
+        r.q = __ldg(p + 3);
+    }
 }
 
 __global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int H,
@@ -39,76 +58,89 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int
                                                          const uint32_t *__restrict__ pval,
                                                          const float4 *__restrict__ rec,
                                                          float4 *__restrict__ out) {
-    // per warp, per lane: {u, v, a, b}, {c, log2 o, r, -}, {r, g, b, -} with
-    // a = -A log2e / 2, b = -B log2e, c = -C log2e / 2
-    __shared__ float4 sg[kBlendWarps][32][3];
+    // staged splats: {u, v, a', b'}, {c', log2 o, radius, -}, {r, g, b, -} with
+    // p = q log2 e = a' dx^2 + b' dx dy + c' dy^2
+    __shared__ float4 s0[2][kBlendThreads];
+    __shared__ float4 s1[2][kBlendThreads];
+    __shared__ float4 s2[2][kBlendThreads];
+    __shared__ uint8_t smask[2][kBlendThreads];
     const int tile = blockIdx.x;
     const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bx0 = txi * kTile + (warp & 1) * kBlockW;
-    const int by0 = tyi * kTile + (warp >> 1) * kBlockH;
-    const int bx1 = min(bx0 + kBlockW - 1, W - 1), by1 = min(by0 + kBlockH - 1, H - 1);
-    if (bx0 > bx1 || by0 > by1) return;  // the whole warp block lies outside the image
-    const int px = bx0 + (lane & (kBlockW - 1));
-    const int py = by0 + (lane / kBlockW);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tx0 = txi * kTile, ty0 = tyi * kTile;
+    const int px = tx0 + (warp & 1) * kBlockW + (lane & (kBlockW - 1));
+    const int py = ty0 + (warp >> 1) * kBlockH + (lane / kBlockW);
     const bool inside = px < W && py < H;
     const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const uint32_t wbit = 1u << warp;
     const uint2 rg = ranges[tile];
     float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
     bool done = !inside;
-    float4(*slot)[3] = sg[warp];
-    for (uint32_t base = rg.x; base < rg.y; base += 32) {
-        if (__all_sync(0xffffffffu, done)) break;
-        const uint32_t idx = base + lane;
-        bool keep = false;
-        if (idx < rg.y) {
-            const uint32_t s = __ldg(pval + idx);
-            const float4 a = __ldg(rec + (size_t)s * 3 + 0);  // u, v, A, B
-            const float4 b = __ldg(rec + (size_t)s * 3 + 1);  // C, opacity, radius, depth
-            int qx0, qx1, qy0, qy1;
-            box_range(a.x, b.z, W, qx0, qx1);
-            box_range(a.y, b.z, H, qy0, qy1);
-            qx0 = max(qx0, bx0);
-            qx1 = min(qx1, bx1);
-            qy0 = max(qy0, by0);
-            qy1 = min(qy1, by1);
-            if (qx0 <= qx1 && qy0 <= qy1)
-                keep = splat_rect_hits(a.x, a.y, a.z, a.w, b.x, splat_fcut(b.y), qx0, qx1, qy0, qy1);
-            if (keep) {
-                const float4 c = __ldg(rec + (size_t)s * 3 + 2);
-                slot[lane][0] = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
-                slot[lane][1] = make_float4(-0.5f * kLog2e * b.x, __log2f(b.y), b.z, 0.0f);
-                slot[lane][2] = c;
+
+    // stage a loaded record into half `h`: pre-scaled exponent, warp-block mask
+    auto stage = [&](const StagedRecord &r, int h) {
+        uint32_t m = 0;
+        if (r.have) {
+            const uint32_t rx = __float_as_uint(r.q.x), ry = __float_as_uint(r.q.y);
+            const int x0 = (int)(rx & 0xFFFFu) - tx0, x1 = (int)(rx >> 16) - tx0;
+            const int y0 = (int)(ry & 0xFFFFu) - ty0, y1 = (int)(ry >> 16) - ty0;
+#pragma unroll
+            for (int w = 0; w < kBlendThreads / 32; ++w) {
+                const int bx = (w & 1) * kBlockW, by = (w >> 1) * kBlockH;
+                if (x0 <= bx + kBlockW - 1 && x1 >= bx && y0 <= by + kBlockH - 1 && y1 >= by) m |= 1u << w;
+            }
+            s0[h][tid] = make_float4(r.a.x, r.a.y, -0.5f * kLog2e * r.a.z, -kLog2e * r.a.w);
+            s1[h][tid] = make_float4(-0.5f * kLog2e * r.b.x, r.q.w, r.b.z, 0.0f);
+            s2[h][tid] = r.c;
+        }
+        smask[h][tid] = (uint8_t)m;
+    };
+
+    StagedRecord nxt;
+    load_record(nxt, pval, rec, rg.x + tid, rg.y);
+    stage(nxt, 0);
+    load_record(nxt, pval, rec, rg.x + kBlendThreads + tid, rg.y);
+    __syncthreads();
+    int h = 0;
+    for (uint32_t base = rg.x; base < rg.y; base += kBlendThreads, h ^= 1) {
+        const int nb = (int)min((uint32_t)kBlendThreads, rg.y - base);
+        for (int c = 0; c < nb; c += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            const bool mine = (smask[h][c + lane] & wbit) != 0 && c + lane < nb;
+            uint32_t m = __ballot_sync(0xffffffffu, mine);
+            while (m) {
+                const int j = c + __ffs(m) - 1;
+                m &= m - 1;
+                if (done) continue;
+                const float4 a = s0[h][j];  // u, v, a', b'
+                const float4 b = s1[h][j];  // c', log2 o, radius
+                const float dx = fpx - a.x, dy = fpy - a.y;
+                if (fmaxf(fabsf(dx), fabsf(dy)) > b.z) continue;
+                const float p = dx * (a.z * dx + a.w * dy) + b.x * dy * dy;
+                if (p > 0.0f) continue;
+                const float alpha = fminf(0.99f, ex2_approx(p + b.y));
+                if (alpha < (1.0f / 255.0f)) continue;
+                const float Tn = T * (1.0f - alpha);
+                if (Tn < 1e-4f) {
+                    done = true;
+                    continue;
+                }
+                const float4 col = s2[h][j];
+                const float wgt = alpha * T;
+                cr += col.x * wgt;
+                cg += col.y * wgt;
+                cb += col.z * wgt;
+                T = Tn;
             }
         }
-        uint32_t m = __ballot_sync(0xffffffffu, keep);
-        __syncwarp();
-        while (m) {
-            const int j = __ffs(m) - 1;
-            m &= m - 1;
-            if (done) continue;
-            const float4 a = slot[j][0];
-            const float4 b = slot[j][1];
-            const float dx = fpx - a.x, dy = fpy - a.y;
-            if (fmaxf(fabsf(dx), fabsf(dy)) > b.z) continue;
-            // p = q log2 e
-            const float p = dx * (a.z * dx + a.w * dy) + b.x * dy * dy;
-            if (p > 0.0f) continue;
-            const float alpha = fminf(0.99f, ex2_approx(p + b.y));
-            if (alpha < (1.0f / 255.0f)) continue;
-            const float Tn = T * (1.0f - alpha);
-            if (Tn < 1e-4f) {
-                done = true;
-                continue;
-            }
-            const float4 col = slot[j][2];
-            const float wgt = alpha * T;
-            cr += col.x * wgt;
-            cg += col.y * wgt;
-            cb += col.z * wgt;
-            T = Tn;
+        // the other half was last read before the previous barrier: refill it
+        // with the next batch (loaded while this one was composited) and
+        // start loading the batch after
+        if (base + kBlendThreads < rg.y) {
+            stage(nxt, h ^ 1);
+            load_record(nxt, pval, rec, base + 2 * kBlendThreads + tid, rg.y);
         }
-        __syncwarp();
+        if (__syncthreads_count(done) == kBlendThreads) break;
     }
     if (inside) out[(size_t)py * W + px] = make_float4(cr, cg, cb, 1.0f - T);
 }

@@ -426,18 +426,29 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
             box_range(v, r, cam.H, py0, py1);
             live = r > 0.0f && px0 <= px1 && py0 <= py1 && isfinite(u) && isfinite(v) &&
                    isfinite(r) && isfinite(cA) && isfinite(cB) && isfinite(cC);
-            if (live) {
-                // tiles of the box holding a pixel the compositing would use
-                const float fcut = splat_fcut(mo.w);
-                const int x0 = px0 >> 4, x1 = px1 >> 4, y0 = py0 >> 4, y1 = py1 >> 4;
-                for (int yy = y0; yy <= y1; ++yy) {
-                    const int qy0 = max(yy * kTile, py0), qy1 = min(yy * kTile + kTile - 1, py1);
-                    for (int xx = x0; xx <= x1; ++xx) {
-                        const int qx0 = max(xx * kTile, px0), qx1 = min(xx * kTile + kTile - 1, px1);
+            int ax0 = 0, ax1 = -1, ay0 = 0, ay1 = -1;
+            const float fcut = splat_fcut(mo.w);
+            if (live && fcut >= 0.0f) {
+                // pixel range where alpha can reach 1/255 (ellipse extent),
+                // inside the support box
+                box_range(u, ellipse_reach(fcut, a), cam.W, ax0, ax1);
+                box_range(v, ellipse_reach(fcut, c), cam.H, ay0, ay1);
+                ax0 = max(ax0, px0);
+                ax1 = min(ax1, px1);
+                ay0 = max(ay0, py0);
+                ay1 = min(ay1, py1);
+                // tiles holding a pixel the compositing would use
+                for (int yy = ay0 >> 4; yy <= (ay1 >> 4) && ay0 <= ay1; ++yy) {
+                    const int qy0 = max(yy * kTile, ay0), qy1 = min(yy * kTile + kTile - 1, ay1);
+                    for (int xx = ax0 >> 4; xx <= (ax1 >> 4) && ax0 <= ax1; ++xx) {
+                        const int qx0 = max(xx * kTile, ax0), qx1 = min(xx * kTile + kTile - 1, ax1);
                         nt += splat_rect_hits(u, v, cA, cB, cC, fcut, qx0, qx1, qy0, qy1) ? 1u : 0u;
                     }
                 }
-                rc = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+            }
+            if (live) {
+                rc = make_uint2((uint32_t)(px0 >> 4) | ((uint32_t)(py0 >> 4) << 16),
+                                (uint32_t)(px1 >> 4) | ((uint32_t)(py1 >> 4) << 16));
                 live = nt > 0;
             }
             if (live) {
@@ -464,9 +475,13 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
                     case 2: sh_colour<2>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
                     default: sh_colour<3>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
                 }
-                rec[(size_t)s * 3 + 0] = make_float4(u, v, cA, cB);
-                rec[(size_t)s * 3 + 1] = make_float4(cC, mo.w, r, tz);
-                rec[(size_t)s * 3 + 2] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+                float4 *ro = rec + (size_t)s * kRecVec;
+                ro[0] = make_float4(u, v, cA, cB);
+                ro[1] = make_float4(cC, mo.w, r, tz);
+                ro[2] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+                ro[3] = make_float4(__uint_as_float((uint32_t)ax0 | ((uint32_t)ax1 << 16)),
+                                    __uint_as_float((uint32_t)ay0 | ((uint32_t)ay1 << 16)), fcut,
+                                    __log2f(mo.w));
             }
         }
     }

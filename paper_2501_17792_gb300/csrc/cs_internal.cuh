@@ -15,10 +15,13 @@
 // applied), V[i][12] = camera o root (3x4), C[i][4] = camera centre in the
 // instance root frame.
 // Per splat s (Gaussian-instance of a visible instance, dense ids grouped by
-// (template, level)): rec[3s..3s+2] float4 = {u, v, A, B}, {C, opacity,
-// radius, depth}, {r, g, b, 0}; key[s] depth bits (0xFFFFFFFF culled);
-// rect[s] tile rectangle (x0 | y0 << 16, x1 | y1 << 16), inclusive;
-// ntiles[s] tiles touched.
+// (template, level)): a 64-byte record rec[4s..4s+3] float4 = {u, v, A, B},
+// {C, opacity, radius, depth}, {r, g, b, 0}, {reach x, reach y, fcut,
+// log2 opacity} where reach x/y hold the inclusive pixel range (lo | hi << 16,
+// as float bits) in which alpha can reach 1/255 (see splat_reach_box);
+// key[s] depth bits (0xFFFFFFFF culled); rect[s] tile rectangle of the
+// support box (x0 | y0 << 16, x1 | y1 << 16), inclusive; ntiles[s] tiles
+// holding a pixel the compositing uses (the pairs of the splat).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -29,6 +32,7 @@ constexpr int kJoints = 24;
 constexpr int kMaxTemplates = 63;
 constexpr int kMaxLevels = 4;
 constexpr int kTile = 16;
+constexpr int kRecVec = 4;  // float4 per splat record
 
 struct TemplateInfo {
     int32_t g_off;      // first global Gaussian index
@@ -131,6 +135,14 @@ __device__ __forceinline__ void box_range(float c, float r, int size, int &lo, i
     hi = (l <= h) ? (int)h : (int)l - 1;
 }
 
+// Inclusive pixel range, on one axis, of the pixel centres within half-width
+// `reach` of the mean: the support box (reach = r) or the axis-aligned extent
+// of the ellipse f(d) <= fcut (reach = sqrt(fcut * Sigma2D_axis), widened by
+// 1e-4 relative + 0.01 px so FP32 rounding cannot cut a pixel off).
+__device__ __forceinline__ float ellipse_reach(float fcut, float sigma_axis) {
+    return __fadd_rn(__fmul_rn(sqrtf(__fmul_rn(fcut, sigma_axis)), 1.0001f), 0.01f);
+}
+
 // meta words written by the cull kernel and read back by the host
 enum MetaIndex { kMetaVisible = 0, kMetaGroups = 1, kMetaSplats = 2, kMetaLevel0 = 3, kMetaWords = 8 };
 
@@ -164,8 +176,7 @@ int radix_sort_u32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint3
 int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint32_t n, int bits,
                    uint32_t *scratch, cudaStream_t st, int *in_second);
 int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *pair_off,
-                      const float4 *rec, int W, int H, int tiles_x, uint16_t *ptile, uint32_t *pval,
-                      cudaStream_t st);
+                      const float4 *rec, int tiles_x, uint16_t *ptile, uint32_t *pval, cudaStream_t st);
 int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, cudaStream_t st);
 int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cudaStream_t st);
 

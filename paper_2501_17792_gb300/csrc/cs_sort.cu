@@ -262,12 +262,13 @@ int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint3
 // pair emission in depth order, tile ranges, live count
 // ---------------------------------------------------------------------------
 
-// Pairs of one splat (in depth order): every tile of its support box that
-// holds a pixel the compositing would use (the same test that counted them).
+// Pairs of one splat (in depth order): every tile of its reach box that
+// holds a pixel the compositing would use (the test that counted them, on
+// the values stored in the record).
 __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *__restrict__ order,
                                                     const uint32_t *__restrict__ pair_off,
-                                                    const float4 *__restrict__ rec, int W, int H,
-                                                    int tiles_x, uint16_t *__restrict__ ptile,
+                                                    const float4 *__restrict__ rec, int tiles_x,
+                                                    uint16_t *__restrict__ ptile,
                                                     uint32_t *__restrict__ pval) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -275,18 +276,17 @@ __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *
     const uint32_t e = pair_off[i + 1];
     if (o == e) return;
     const uint32_t s = order[i];
-    const float4 r0 = rec[(size_t)s * 3 + 0];  // u, v, A, B
-    const float4 r1 = rec[(size_t)s * 3 + 1];  // C, opacity, radius, depth
-    int px0, px1, py0, py1;
-    box_range(r0.x, r1.z, W, px0, px1);
-    box_range(r0.y, r1.z, H, py0, py1);
-    const float fcut = splat_fcut(r1.y);
-    const int x0 = px0 >> 4, x1 = px1 >> 4, y0 = py0 >> 4, y1 = py1 >> 4;
-    for (int yy = y0; yy <= y1; ++yy) {
-        const int qy0 = max(yy * kTile, py0), qy1 = min(yy * kTile + kTile - 1, py1);
-        for (int xx = x0; xx <= x1; ++xx) {
-            const int qx0 = max(xx * kTile, px0), qx1 = min(xx * kTile + kTile - 1, px1);
-            if (!splat_rect_hits(r0.x, r0.y, r0.z, r0.w, r1.x, fcut, qx0, qx1, qy0, qy1)) continue;
+    const float4 r0 = rec[(size_t)s * kRecVec + 0];  // u, v, A, B
+    const float4 r1 = rec[(size_t)s * kRecVec + 1];  // C, opacity, radius, depth
+    const float4 r3 = rec[(size_t)s * kRecVec + 3];  // reach x, reach y, fcut, log2 o
+    const uint32_t rx = __float_as_uint(r3.x), ry = __float_as_uint(r3.y);
+    const int ax0 = (int)(rx & 0xFFFFu), ax1 = (int)(rx >> 16);
+    const int ay0 = (int)(ry & 0xFFFFu), ay1 = (int)(ry >> 16);
+    for (int yy = ay0 >> 4; yy <= (ay1 >> 4); ++yy) {
+        const int qy0 = max(yy * kTile, ay0), qy1 = min(yy * kTile + kTile - 1, ay1);
+        for (int xx = ax0 >> 4; xx <= (ax1 >> 4); ++xx) {
+            const int qx0 = max(xx * kTile, ax0), qx1 = min(xx * kTile + kTile - 1, ax1);
+            if (!splat_rect_hits(r0.x, r0.y, r0.z, r0.w, r1.x, r3.z, qx0, qx1, qy0, qy1)) continue;
             if (o >= e) return;
             ptile[o] = (uint16_t)(yy * tiles_x + xx);
             pval[o] = s;
@@ -296,11 +296,10 @@ __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *
 }
 
 int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *pair_off,
-                      const float4 *rec, int W, int H, int tiles_x, uint16_t *ptile, uint32_t *pval,
-                      cudaStream_t st) {
+                      const float4 *rec, int tiles_x, uint16_t *ptile, uint32_t *pval, cudaStream_t st) {
     if (n_splats == 0) return 0;
-    k_emit_pairs<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, order, pair_off, rec, W, H, tiles_x,
-                                                          ptile, pval);
+    k_emit_pairs<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, order, pair_off, rec, tiles_x, ptile,
+                                                          pval);
     return 1;
 }
 
