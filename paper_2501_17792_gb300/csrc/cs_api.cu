@@ -61,7 +61,7 @@ struct cs_ctx {
 
     // per-frame buffers
     DevBuf<float4> rec;
-    DevBuf<uint32_t> key, ids, key2, ids2, ntiles, pair_off, pval, pval2, scratch;
+    DevBuf<uint32_t> key, ids, key2, ids2, bins, bins_sorted, pair_off, pval, pval2, scratch;
     DevBuf<uint2> rect, ranges;
     DevBuf<uint16_t> ptile, ptile2;
     DevBuf<float4> img;  // for cs_render_to_host
@@ -305,7 +305,7 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->tid); release(ctx->vis); release(ctx->root); release(ctx->pose);
     release(ctx->B); release(ctx->V); release(ctx->Cloc); release(ctx->groups);
     release(ctx->rec); release(ctx->key); release(ctx->ids); release(ctx->key2); release(ctx->ids2);
-    release(ctx->ntiles); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
+    release(ctx->bins); release(ctx->bins_sorted); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
     release(ctx->scratch); release(ctx->rect); release(ctx->ranges); release(ctx->ptile);
     release(ctx->ptile2); release(ctx->img);
     if (ctx->d_meta) cudaFree(ctx->d_meta);
@@ -602,25 +602,26 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->key2, Sa, "depth keys (ping-pong)"));
     CS_TRY(ensure(ctx, ctx->ids2, Sa, "splat ids (ping-pong)"));
     CS_TRY(ensure(ctx, ctx->rect, Sa, "tile rects"));
-    CS_TRY(ensure(ctx, ctx->ntiles, Sa, "tile counts"));
+    CS_TRY(ensure(ctx, ctx->bins, Sa, "bin words"));
+    CS_TRY(ensure(ctx, ctx->bins_sorted, Sa, "bin words in depth order"));
     CS_TRY(ensure(ctx, ctx->pair_off, Sa + 1, "pair offsets"));
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Sa), scan_scratch_words(Sa + 1)), "scratch"));
     TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh};
     if (S > 0)
         launched += launch_project((int)S, ctx->groups.p, ctx->n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                        ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
-                       ctx->rec.p, ctx->key.p, ctx->ids.p, ctx->rect.p, ctx->ntiles.p, st);
+                       ctx->rec.p, ctx->key.p, ctx->ids.p, ctx->rect.p, ctx->bins.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[3], st));
     // 4. depth sort of the splats (stable, ties by splat id)
     int ob = 0;
     if (S > 0) launched += radix_sort_u32(ctx->key.p, ctx->ids.p, ctx->key2.p, ctx->ids2.p, (uint32_t)S, 32,
-                                          ctx->scratch.p, st, &ob);
+                                          ctx->scratch.p, st, &ob, ctx->bins.p, ctx->bins_sorted.p);
     ctx->order_buf = ob;
     uint32_t *order = ob ? ctx->ids2.p : ctx->ids.p;
     uint32_t *sorted_keys = ob ? ctx->key2.p : ctx->key.p;
     if (timing) CS_CUDA(cudaEventRecord(ev[4], st));
     // 5. pair offsets in depth order and pair emission
-    launched += exclusive_scan(ctx->ntiles.p, order, ctx->pair_off.p, (uint32_t)S, ctx->scratch.p, st);
+    launched += exclusive_scan_bins(ctx->bins_sorted.p, ctx->pair_off.p, (uint32_t)S, ctx->scratch.p, st);
     CS_CUDA(cudaGetLastError());
     if (stats && S > 0) launched += launch_count_live((uint32_t)S, sorted_keys, ctx->d_meta + kMetaWords - 1, st);
     CS_CUDA(cudaMemcpyAsync(ctx->h_pairs, ctx->pair_off.p + S, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -634,8 +635,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->pval, Pa, "pair splats"));
     CS_TRY(ensure(ctx, ctx->pval2, Pa, "pair splats (ping-pong)"));
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Pa), radix_scratch_words(Sa)), "scratch"));
-    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, ctx->pair_off.p, ctx->rec.p, cp.tiles_x,
-                                             ctx->ptile.p, ctx->pval.p, st);
+    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, ctx->bins_sorted.p, ctx->pair_off.p, ctx->rec.p,
+                                             cp.tiles_x, ctx->ptile.p, ctx->pval.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[5], st));
     // 6. stable sort of the pairs by tile
     int pb = 0;
@@ -739,7 +740,7 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
     int64_t ib = bytes_of(ctx->tid) + bytes_of(ctx->vis) + bytes_of(ctx->root) + bytes_of(ctx->pose) +
                  bytes_of(ctx->B) + bytes_of(ctx->V) + bytes_of(ctx->Cloc) + bytes_of(ctx->groups);
     int64_t fb = bytes_of(ctx->rec) + bytes_of(ctx->key) + bytes_of(ctx->ids) + bytes_of(ctx->key2) +
-                 bytes_of(ctx->ids2) + bytes_of(ctx->ntiles) + bytes_of(ctx->pair_off) + bytes_of(ctx->pval) +
+                 bytes_of(ctx->ids2) + bytes_of(ctx->bins) + bytes_of(ctx->bins_sorted) + bytes_of(ctx->pair_off) + bytes_of(ctx->pval) +
                  bytes_of(ctx->pval2) + bytes_of(ctx->scratch) + bytes_of(ctx->rect) + bytes_of(ctx->ranges) +
                  bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img);
     out->template_bytes = tb;
@@ -803,15 +804,16 @@ constexpr size_t kOffIds = kOffKey + a256(kStaticSplats * 4);
 constexpr size_t kOffKey2 = kOffIds + a256(kStaticSplats * 4);
 constexpr size_t kOffIds2 = kOffKey2 + a256(kStaticSplats * 4);
 constexpr size_t kOffRect = kOffIds2 + a256(kStaticSplats * 4);
-constexpr size_t kOffNtiles = kOffRect + a256(kStaticSplats * sizeof(uint2));
-constexpr size_t kOffPairOff = kOffNtiles + a256(kStaticSplats * 4);
+constexpr size_t kOffBins = kOffRect + a256(kStaticSplats * sizeof(uint2));
+constexpr size_t kOffBinsSorted = kOffBins + a256(kStaticSplats * 4);
+constexpr size_t kOffPairOff = kOffBinsSorted + a256(kStaticSplats * 4);
 constexpr size_t kOffPtile = kOffPairOff + a256((kStaticSplats + 1) * 4);
 constexpr size_t kOffPtile2 = kOffPtile + a256(kStaticPairs * 2);
 constexpr size_t kOffPval = kOffPtile2 + a256(kStaticPairs * 2);
 constexpr size_t kOffPval2 = kOffPval + a256(kStaticPairs * 4);
 constexpr size_t kOffRanges = kOffPval2 + a256(kStaticPairs * 4);
 constexpr size_t kOffScratch = kOffRanges + a256(kStaticTiles * sizeof(uint2));
-constexpr size_t kStaticBytes = kOffScratch + a256(kStaticScratchWords * 4);  // about 9.9 MB
+constexpr size_t kStaticBytes = kOffScratch + a256(kStaticScratchWords * 4);  // about 10.2 MB
 
 }  // namespace
 
@@ -879,7 +881,8 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     uint32_t *key2 = reinterpret_cast<uint32_t *>(base + kOffKey2);
     uint32_t *ids2 = reinterpret_cast<uint32_t *>(base + kOffIds2);
     uint2 *rect = reinterpret_cast<uint2 *>(base + kOffRect);
-    uint32_t *ntiles = reinterpret_cast<uint32_t *>(base + kOffNtiles);
+    uint32_t *bins = reinterpret_cast<uint32_t *>(base + kOffBins);
+    uint32_t *bins_sorted = reinterpret_cast<uint32_t *>(base + kOffBinsSorted);
     uint32_t *pair_off = reinterpret_cast<uint32_t *>(base + kOffPairOff);
     uint16_t *ptile0 = reinterpret_cast<uint16_t *>(base + kOffPtile);
     uint16_t *ptile1 = reinterpret_cast<uint16_t *>(base + kOffPtile2);
@@ -913,15 +916,15 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     if (S > 0)
         launched += launch_project((int)S, ctx->groups.p, n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                                    ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
-                                   rec, key, ids, rect, ntiles, st);
+                                   rec, key, ids, rect, bins, st);
     if (radix_scratch_words((size_t)std::max<int64_t>(S, 1)) > kStaticScratchWords ||
         scan_scratch_words((size_t)S + 1) > kStaticScratchWords)
         return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: scratch too small for %lld splats", (long long)S);
     int ob = 0;
-    if (S > 0) launched += radix_sort_u32(key, ids, key2, ids2, (uint32_t)S, 32, scratch, st, &ob);
+    if (S > 0) launched += radix_sort_u32(key, ids, key2, ids2, (uint32_t)S, 32, scratch, st, &ob, bins, bins_sorted);
     uint32_t *order = ob ? ids2 : ids;
     uint32_t *sorted_keys = ob ? key2 : key;
-    launched += exclusive_scan(ntiles, order, pair_off, (uint32_t)S, scratch, st);
+    launched += exclusive_scan_bins(bins_sorted, pair_off, (uint32_t)S, scratch, st);
     if (stats && S > 0) launched += launch_count_live((uint32_t)S, sorted_keys, ctx->d_meta + kMetaWords - 1, st);
     CS_CUDA(cudaGetLastError());
     CS_CUDA(cudaMemcpyAsync(ctx->h_pairs, pair_off + S, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -933,7 +936,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
                     (long long)P, kStaticPairs);
     if (radix_scratch_words((size_t)std::max<int64_t>(P, 1)) > kStaticScratchWords)
         return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: scratch too small for %lld pairs", (long long)P);
-    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, pair_off, rec, cp.tiles_x, ptile0, pval0, st);
+    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, bins_sorted, pair_off, rec, cp.tiles_x, ptile0, pval0, st);
     int pb = 0;
     if (P > 0) launched += radix_sort_u16(ptile0, pval0, ptile1, pval1, (uint32_t)P, bits_for((uint32_t)T),
                                           scratch, st, &pb);

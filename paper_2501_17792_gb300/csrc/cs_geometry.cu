@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,
     CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
     uint32_t *__restrict__ key, uint32_t *__restrict__ ids, uint2 *__restrict__ rect,
-    uint32_t *__restrict__ ntiles) {
+    uint32_t *__restrict__ bin) {
     __shared__ Group sg[kMaxTemplates * kMaxLevels];
     for (int g = threadIdx.x; g < n_groups; g += blockDim.x) sg[g] = groups[g];
     __syncthreads();
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
 
     bool live = tz > cam.near_z;  // also false for NaN
     uint2 rc = make_uint2(0u, 0u);
-    uint32_t nt = 0;
+    uint32_t nt = 0, bword = 0;
     if (live) {
         // covariance in camera space: Wc = (V_R A) (m^2 Sigma) (V_R A)^T,
         // A = the 3x3 part of M (full LBS) or identity (means only)
@@ -437,14 +437,22 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
                 ax1 = min(ax1, px1);
                 ay0 = max(ay0, py0);
                 ay1 = min(ay1, py1);
-                // tiles holding a pixel the compositing would use
-                for (int yy = ay0 >> 4; yy <= (ay1 >> 4) && ay0 <= ay1; ++yy) {
+                // tiles holding a pixel the compositing would use; a 3x3
+                // window of them is kept as a mask (bin word)
+                const int wx0 = ax0 >> 4, wy0 = ay0 >> 4;
+                uint32_t mask = 0;
+                for (int yy = wy0; yy <= (ay1 >> 4) && ay0 <= ay1; ++yy) {
                     const int qy0 = max(yy * kTile, ay0), qy1 = min(yy * kTile + kTile - 1, ay1);
-                    for (int xx = ax0 >> 4; xx <= (ax1 >> 4) && ax0 <= ax1; ++xx) {
+                    for (int xx = wx0; xx <= (ax1 >> 4) && ax0 <= ax1; ++xx) {
                         const int qx0 = max(xx * kTile, ax0), qx1 = min(xx * kTile + kTile - 1, ax1);
-                        nt += splat_rect_hits(u, v, cA, cB, cC, fcut, qx0, qx1, qy0, qy1) ? 1u : 0u;
+                        if (splat_rect_hits(u, v, cA, cB, cC, fcut, qx0, qx1, qy0, qy1)) {
+                            ++nt;
+                            if (xx - wx0 < 3 && yy - wy0 < 3) mask |= 1u << ((yy - wy0) * 3 + (xx - wx0));
+                        }
                     }
                 }
+                const bool small = ax0 <= ax1 && ay0 <= ay1 && (ax1 >> 4) - wx0 < 3 && (ay1 >> 4) - wy0 < 3;
+                bword = small ? ((uint32_t)wx0 | ((uint32_t)wy0 << 8) | (mask << 16)) : (kBinLarge | nt);
             }
             if (live) {
                 rc = make_uint2((uint32_t)(px0 >> 4) | ((uint32_t)(py0 >> 4) << 16),
@@ -487,19 +495,19 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     }
     key[s] = live ? __float_as_uint(tz) : 0xFFFFFFFFu;
     rect[s] = rc;
-    ntiles[s] = nt;
+    bin[s] = live ? bword : 0u;
 }
 
 int launch_project(int n_splats, const Group *groups, int n_groups, const int32_t *vis,
                     const float *B, const float *V, const float *Cloc, const float *root,
                     const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
                     const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
-                    uint32_t *ids, uint2 *rect, uint32_t *ntiles, cudaStream_t st) {
+                    uint32_t *ids, uint2 *rect, uint32_t *bin, cudaStream_t st) {
     if (n_splats <= 0) return 0;
     int blocks = (n_splats + kProjThreads - 1) / kProjThreads;
     k_project<<<blocks, kProjThreads, 0, st>>>(n_splats, groups, n_groups, vis, B, V, Cloc, root, ta,
                                                 tpls, cam, lod, skin_mode, sh_frame, rec, key, ids,
-                                                rect, ntiles);
+                                                rect, bin);
     return 1;
 }
 

@@ -20,8 +20,11 @@
 // log2 opacity} where reach x/y hold the inclusive pixel range (lo | hi << 16,
 // as float bits) in which alpha can reach 1/255 (see splat_reach_box);
 // key[s] depth bits (0xFFFFFFFF culled); rect[s] tile rectangle of the
-// support box (x0 | y0 << 16, x1 | y1 << 16), inclusive; ntiles[s] tiles
-// holding a pixel the compositing uses (the pairs of the splat).
+// support box (x0 | y0 << 16, x1 | y1 << 16), inclusive; bin[s] the tiles
+// holding a pixel the compositing uses (the pairs of the splat), as a bin
+// word: small splats (reach box within a 3x3 tile window) store the
+// window's tile origin and a 9-bit mask, x0 | y0 << 8 | mask << 16; larger
+// ones store kBinLarge | count and are re-tested from their record.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,6 +36,16 @@ constexpr int kMaxTemplates = 63;
 constexpr int kMaxLevels = 4;
 constexpr int kTile = 16;
 constexpr int kRecVec = 4;  // float4 per splat record
+constexpr uint32_t kBinLarge = 0x80000000u;
+
+// number of pairs (tiles) described by a bin word
+__host__ __device__ __forceinline__ uint32_t bin_count(uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return (b & kBinLarge) ? (b & ~kBinLarge) : (uint32_t)__popc((b >> 16) & 0x1FFu);
+#else
+    return (b & kBinLarge) ? (b & ~kBinLarge) : (uint32_t)__builtin_popcount((b >> 16) & 0x1FFu);
+#endif
+}
 
 struct TemplateInfo {
     int32_t g_off;      // first global Gaussian index
@@ -158,25 +171,30 @@ int launch_project(int n_splats, const Group *groups, int n_groups, const int32_
                     const float *B, const float *V, const float *Cloc, const float *root,
                     const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
                     const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
-                    uint32_t *ids, uint2 *rect, uint32_t *ntiles, cudaStream_t st);
+                    uint32_t *ids, uint2 *rect, uint32_t *bin, cudaStream_t st);
 
 // ---- sort and binning (cs_sort.cu) ----
 // scratch words needed by exclusive_scan / radix_sort for n elements
 size_t scan_scratch_words(size_t n);
 size_t radix_scratch_words(size_t n);
-// out[0..n] = exclusive prefix sums of in (gathered through idx when idx
-// is non-null: value i = in[idx[i]]); out[n] = total.
-int exclusive_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, uint32_t n,
-                    uint32_t *scratch, cudaStream_t st);
+// out[0..n] = exclusive prefix sums of in; out[n] = total.
+int exclusive_scan(const uint32_t *in, const uint32_t *idx_unused, uint32_t *out, uint32_t n,
+                   uint32_t *scratch, cudaStream_t st);
+// out[0..n] = exclusive prefix sums of bin_count(bins[i]); out[n] = total.
+int exclusive_scan_bins(const uint32_t *bins, uint32_t *out, uint32_t n, uint32_t *scratch, cudaStream_t st);
 // Stable LSD radix sort of (key, value) pairs over key bits [0, bits).
 // Ping-pongs between (k0, v0) and (k1, v1); *in_second is set to 0 when the
 // result is in (k0, v0), 1 when in (k1, v1).  Returns kernels launched.
+// When gather_dst is non-null, the last pass also writes, for every output
+// position, gather_src[value] to gather_dst (a payload in sorted order).
 int radix_sort_u32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t n, int bits,
-                   uint32_t *scratch, cudaStream_t st, int *in_second);
+                   uint32_t *scratch, cudaStream_t st, int *in_second,
+                   const uint32_t *gather_src = nullptr, uint32_t *gather_dst = nullptr);
 int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint32_t n, int bits,
                    uint32_t *scratch, cudaStream_t st, int *in_second);
-int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *pair_off,
-                      const float4 *rec, int tiles_x, uint16_t *ptile, uint32_t *pval, cudaStream_t st);
+int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
+                      const uint32_t *pair_off, const float4 *rec, int tiles_x, uint16_t *ptile,
+                      uint32_t *pval, cudaStream_t st);
 int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, cudaStream_t st);
 int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cudaStream_t st);
 

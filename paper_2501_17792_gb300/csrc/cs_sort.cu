@@ -52,21 +52,22 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
     return inc - v + warp_sums[warp];
 }
 
-template <bool GATHER>
-__device__ __forceinline__ uint32_t scan_load(const uint32_t *in, const uint32_t *idx, uint32_t i) {
-    return GATHER ? in[idx[i]] : in[i];
+// element i of a scan input: plain value (MODE 0) or pair count of a bin
+// word (MODE 1)
+template <int MODE>
+__device__ __forceinline__ uint32_t scan_load(const uint32_t *in, uint32_t i) {
+    return MODE == 1 ? bin_count(in[i]) : in[i];
 }
 
-template <bool GATHER>
+template <int MODE>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in,
-                                                              const uint32_t *__restrict__ idx,
                                                               uint32_t n, uint32_t *__restrict__ sums) {
     __shared__ uint32_t total;
     const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t v = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k)
-        if (base + k < n) v += scan_load<GATHER>(in, idx, base + k);
+        if (base + k < n) v += scan_load<MODE>(in, base + k);
     block_excl_scan(v, &total);
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
@@ -87,9 +88,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_spine(uint32_t *__restric
     if (threadIdx.x == 0) sums[nb] = carry;
 }
 
-template <bool GATHER>
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *__restrict__ in,
-                                                            const uint32_t *__restrict__ idx, uint32_t n,
+template <int MODE>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *__restrict__ in, uint32_t n,
                                                             const uint32_t *__restrict__ sums,
                                                             uint32_t nb, uint32_t *__restrict__ out) {
     __shared__ uint32_t total;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *__re
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        v[k] = base + k < n ? scan_load<GATHER>(in, idx, base + k) : 0u;
+        v[k] = base + k < n ? scan_load<MODE>(in, base + k) : 0u;
         s += v[k];
     }
     uint32_t ex = block_excl_scan(s, &total) + sums[blockIdx.x];
@@ -112,123 +112,178 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *__re
 
 size_t scan_scratch_words(size_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-int exclusive_scan(const uint32_t *in, const uint32_t *idx, uint32_t *out, uint32_t n,
-                   uint32_t *scratch, cudaStream_t st) {
+template <int MODE>
+static int scan_impl(const uint32_t *in, uint32_t *out, uint32_t n, uint32_t *scratch, cudaStream_t st) {
     if (n == 0) {
         cudaMemsetAsync(out, 0, sizeof(uint32_t), st);
         return 0;
     }
-    uint32_t nb = (n + kScanTile - 1) / kScanTile;
-    if (idx) {
-        k_scan_reduce<true><<<nb, kScanThreads, 0, st>>>(in, idx, n, scratch);
-        k_scan_spine<<<1, kScanThreads, 0, st>>>(scratch, nb);
-        k_scan_down<true><<<nb, kScanThreads, 0, st>>>(in, idx, n, scratch, nb, out);
-    } else {
-        k_scan_reduce<false><<<nb, kScanThreads, 0, st>>>(in, nullptr, n, scratch);
-        k_scan_spine<<<1, kScanThreads, 0, st>>>(scratch, nb);
-        k_scan_down<false><<<nb, kScanThreads, 0, st>>>(in, nullptr, n, scratch, nb, out);
-    }
+    const uint32_t nb = (n + kScanTile - 1) / kScanTile;
+    k_scan_reduce<MODE><<<nb, kScanThreads, 0, st>>>(in, n, scratch);
+    k_scan_spine<<<1, kScanThreads, 0, st>>>(scratch, nb);
+    k_scan_down<MODE><<<nb, kScanThreads, 0, st>>>(in, n, scratch, nb, out);
     return 3;
+}
+
+int exclusive_scan(const uint32_t *in, const uint32_t *, uint32_t *out, uint32_t n, uint32_t *scratch,
+                   cudaStream_t st) {
+    return scan_impl<0>(in, out, n, scratch, st);
+}
+
+int exclusive_scan_bins(const uint32_t *bins, uint32_t *out, uint32_t n, uint32_t *scratch, cudaStream_t st) {
+    return scan_impl<1>(bins, out, n, scratch, st);
 }
 
 // ---------------------------------------------------------------------------
 // stable LSD radix sort, 8-bit digits, reduce-then-scan per pass
+//
+// A block owns 4,096 consecutive elements; warp w owns 512 of them, read in
+// 16 rounds of 32 consecutive elements (coalesced, all loads issued before
+// any shared-memory update).  Histogram pass: per-warp digit counts with
+// warp-aggregated increments (match_any), one row per digit in the global
+// count matrix (digit-major), which an exclusive scan turns into each
+// block's global digit offsets.  Scatter pass: stable ranks from per-warp
+// running counts (match_any per round), then a block-local sort in shared
+// memory, then each digit's run is written out with consecutive threads on
+// consecutive addresses.
 // ---------------------------------------------------------------------------
 
 constexpr int kRadixThreads = 256;
 constexpr int kRadixWarps = kRadixThreads / 32;
-constexpr int kRadixItems = 8;                               // per lane
-constexpr int kRadixTile = kRadixThreads * kRadixItems;      // per block
-constexpr int kRadixWarpTile = 32 * kRadixItems;             // per warp
+constexpr int kRadixItems = 16;                              // per lane
+constexpr int kRadixTile = kRadixThreads * kRadixItems;      // per block (4,096)
+constexpr int kRadixWarpTile = 32 * kRadixItems;             // per warp (512)
+constexpr int kRadixDigits = 256;
 
 template <typename K>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const K *__restrict__ keys, uint32_t n,
                                                               int shift, uint32_t *__restrict__ hist,
                                                               uint32_t nblocks) {
-    __shared__ uint32_t h[kRadixWarps][256];
+    __shared__ uint32_t h[kRadixWarps][kRadixDigits];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int d = threadIdx.x; d < kRadixWarps * 256; d += kRadixThreads) (&h[0][0])[d] = 0;
-    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixWarps * kRadixDigits; d += kRadixThreads) (&h[0][0])[d] = 0;
     const uint32_t base = blockIdx.x * kRadixTile + warp * kRadixWarpTile;
+    uint32_t dig[kRadixItems];
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
-        uint32_t i = base + r * 32 + lane;
-        if (i < n) atomicAdd(&h[warp][(keys[i] >> shift) & 0xFFu], 1u);
+        const uint32_t i = base + r * 32 + lane;
+        dig[r] = i < n ? (uint32_t)((keys[i] >> shift) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
     }
     __syncthreads();
-    uint32_t s = 0;
+    const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int w = 0; w < kRadixWarps; ++w) s += h[w][threadIdx.x];
-    hist[threadIdx.x * nblocks + blockIdx.x] = s;
+    for (int r = 0; r < kRadixItems; ++r) {
+        const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+        if (dig[r] < kRadixDigits && (peers & lt) == 0u) atomicAdd(&h[warp][dig[r]], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixDigits; d += kRadixThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kRadixWarps; ++w) s += h[w][d];
+        hist[(size_t)d * nblocks + blockIdx.x] = s;
+    }
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+__global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ offs,
-    uint32_t nblocks) {
-    __shared__ uint32_t wcnt[kRadixWarps][256];
+    uint32_t nblocks, const uint32_t *__restrict__ gsrc, uint32_t *__restrict__ gdst) {
+    __shared__ uint32_t wcnt[kRadixWarps][kRadixDigits];  // running counts, then warp offsets
+    __shared__ uint32_t dstart[kRadixDigits];              // block-local start of each digit
+    __shared__ uint32_t gbase[kRadixDigits];               // global start of each digit
+    __shared__ uint32_t total;
+    __shared__ K skey[kRadixTile];
+    __shared__ uint32_t sval[kRadixTile];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int d = threadIdx.x; d < kRadixWarps * 256; d += kRadixThreads) (&wcnt[0][0])[d] = 0;
-    __syncthreads();
-    const uint32_t base = blockIdx.x * kRadixTile + warp * kRadixWarpTile;
-    const uint32_t lt = (1u << lane) - 1u;
+    for (int d = threadIdx.x; d < kRadixWarps * kRadixDigits; d += kRadixThreads) (&wcnt[0][0])[d] = 0;
+    const uint32_t blk0 = blockIdx.x * kRadixTile;
+    const uint32_t base = blk0 + warp * kRadixWarpTile;
     K k[kRadixItems];
-    uint32_t v[kRadixItems], rank[kRadixItems];
-    int dig[kRadixItems];
+    uint32_t v[kRadixItems];
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
         const uint32_t i = base + r * 32 + lane;
         const bool ok = i < n;
         k[r] = ok ? kin[i] : (K)0;
         v[r] = ok ? vin[i] : 0u;
-        const int d = ok ? (int)((k[r] >> shift) & 0xFFu) : 256;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const uint32_t before = ok ? wcnt[warp][d] : 0u;
-        __syncwarp();
-        if (ok && (peers & lt) == 0u) wcnt[warp][d] = before + __popc(peers);
-        __syncwarp();
-        rank[r] = before + __popc(peers & lt);
-        dig[r] = d;
     }
     __syncthreads();
+    // stable rank within the warp's 512 elements; packed as digit | rank << 16
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t dr[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const uint32_t i = base + r * 32 + lane;
+        const uint32_t d = i < n ? (uint32_t)((k[r] >> shift) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = d < kRadixDigits ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (d < kRadixDigits && (peers & lt) == 0u) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        dr[r] = d | ((before + __popc(peers & lt)) << 16);
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, and the digit's block total
+    uint32_t tot = 0;
     {
-        // digit d: global base of this block, then exclusive over warps
-        const int d = threadIdx.x;
-        uint32_t run = offs[d * nblocks + blockIdx.x];
+        const int d = threadIdx.x;  // kRadixThreads == kRadixDigits
+        uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kRadixWarps; ++w) {
-            uint32_t c = wcnt[w][d];
+            const uint32_t c = wcnt[w][d];
             wcnt[w][d] = run;
             run += c;
         }
+        tot = run;
+        gbase[d] = offs[(size_t)d * nblocks + blockIdx.x];
     }
+    // block-local digit starts
+    const uint32_t ex = block_excl_scan(tot, &total);
+    dstart[threadIdx.x] = ex;
     __syncthreads();
+    // block-local sort in shared memory
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
-        if (dig[r] < 256) {
-            const uint32_t pos = wcnt[warp][dig[r]] + rank[r];
-            kout[pos] = k[r];
-            vout[pos] = v[r];
+        const uint32_t d = dr[r] & 0xFFFFu;
+        if (d < kRadixDigits) {
+            const uint32_t lp = dstart[d] + wcnt[warp][d] + (dr[r] >> 16);
+            skey[lp] = k[r];
+            sval[lp] = v[r];
         }
+    }
+    __syncthreads();
+    // runs of equal digits go to consecutive global addresses
+    const uint32_t cnt = min((uint32_t)kRadixTile, n - blk0);
+#pragma unroll 4
+    for (uint32_t p = threadIdx.x; p < cnt; p += kRadixThreads) {
+        const K key = skey[p];
+        const uint32_t d = (uint32_t)((key >> shift) & (kRadixDigits - 1));
+        const uint32_t g = gbase[d] + (p - dstart[d]);
+        const uint32_t val = sval[p];
+        kout[g] = key;
+        vout[g] = val;
+        if (gdst) gdst[g] = gsrc[val];
     }
 }
 
 size_t radix_scratch_words(size_t n) {
     size_t nb = (n + kRadixTile - 1) / kRadixTile;
     if (nb == 0) nb = 1;
-    size_t hist = 256 * nb;
+    size_t hist = (size_t)kRadixDigits * nb;
     return 2 * hist + 1 + scan_scratch_words(hist);
 }
 
 template <typename K>
 static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int bits,
-                      uint32_t *scratch, cudaStream_t st, int *in_second) {
+                      uint32_t *scratch, cudaStream_t st, int *in_second, const uint32_t *gsrc,
+                      uint32_t *gdst) {
     *in_second = 0;
     if (n == 0 || bits <= 0) return 0;
     int launched = 0;
     const uint32_t nb = (n + kRadixTile - 1) / kRadixTile;
-    const uint32_t hn = 256 * nb;
+    const uint32_t hn = kRadixDigits * nb;
     uint32_t *hist = scratch;
     uint32_t *offs = scratch + hn;
     uint32_t *sc = scratch + 2 * hn + 1;
@@ -238,9 +293,11 @@ static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int 
         const uint32_t *vi = cur ? v1 : v0;
         K *ko = cur ? k0 : k1;
         uint32_t *vo = cur ? v0 : v1;
+        const bool last = shift + 8 >= bits;
         k_radix_hist<K><<<nb, kRadixThreads, 0, st>>>(ki, n, shift, hist, nb);
         launched += 1 + exclusive_scan(hist, nullptr, offs, hn, sc, st);
-        k_radix_scatter<K><<<nb, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, offs, nb);
+        k_radix_scatter<K><<<nb, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, offs, nb,
+                                                          last ? gsrc : nullptr, last ? gdst : nullptr);
         launched += 1;
         cur ^= 1;
     }
@@ -249,13 +306,14 @@ static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int 
 }
 
 int radix_sort_u32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t n, int bits,
-                   uint32_t *scratch, cudaStream_t st, int *in_second) {
-    return radix_sort<uint32_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second);
+                   uint32_t *scratch, cudaStream_t st, int *in_second, const uint32_t *gather_src,
+                   uint32_t *gather_dst) {
+    return radix_sort<uint32_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second, gather_src, gather_dst);
 }
 
 int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint32_t n, int bits,
                    uint32_t *scratch, cudaStream_t st, int *in_second) {
-    return radix_sort<uint16_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second);
+    return radix_sort<uint16_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -263,9 +321,11 @@ int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint3
 // ---------------------------------------------------------------------------
 
 // Pairs of one splat (in depth order): every tile of its reach box that
-// holds a pixel the compositing would use (the test that counted them, on
-// the values stored in the record).
+// holds a pixel the compositing would use.  Small splats carry those tiles
+// as a 3x3 mask in their bin word (gathered into depth order by the depth
+// sort); larger ones repeat the counting test on the values in the record.
 __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *__restrict__ order,
+                                                    const uint32_t *__restrict__ bins,
                                                     const uint32_t *__restrict__ pair_off,
                                                     const float4 *__restrict__ rec, int tiles_x,
                                                     uint16_t *__restrict__ ptile,
@@ -276,6 +336,19 @@ __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *
     const uint32_t e = pair_off[i + 1];
     if (o == e) return;
     const uint32_t s = order[i];
+    const uint32_t b = bins[i];
+    if (!(b & kBinLarge)) {
+        const uint32_t x0 = b & 0xFFu, y0 = (b >> 8) & 0xFFu;
+        uint32_t m = (b >> 16) & 0x1FFu;
+        while (m && o < e) {
+            const uint32_t k = __ffs(m) - 1;
+            m &= m - 1;
+            ptile[o] = (uint16_t)((y0 + k / 3) * (uint32_t)tiles_x + x0 + k % 3);
+            pval[o] = s;
+            ++o;
+        }
+        return;
+    }
     const float4 r0 = rec[(size_t)s * kRecVec + 0];  // u, v, A, B
     const float4 r1 = rec[(size_t)s * kRecVec + 1];  // C, opacity, radius, depth
     const float4 r3 = rec[(size_t)s * kRecVec + 3];  // reach x, reach y, fcut, log2 o
@@ -295,11 +368,12 @@ __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *
     }
 }
 
-int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *pair_off,
-                      const float4 *rec, int tiles_x, uint16_t *ptile, uint32_t *pval, cudaStream_t st) {
+int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
+                      const uint32_t *pair_off, const float4 *rec, int tiles_x, uint16_t *ptile,
+                      uint32_t *pval, cudaStream_t st) {
     if (n_splats == 0) return 0;
-    k_emit_pairs<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, order, pair_off, rec, tiles_x, ptile,
-                                                          pval);
+    k_emit_pairs<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, order, bins_sorted, pair_off, rec,
+                                                          tiles_x, ptile, pval);
     return 1;
 }
 
