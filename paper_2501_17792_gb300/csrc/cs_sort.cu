@@ -139,13 +139,13 @@ int exclusive_scan_bins(const uint32_t *bins, uint32_t *out, uint32_t n, uint32_
 //
 // A block owns 4,096 consecutive elements; warp w owns 512 of them, read in
 // 16 rounds of 32 consecutive elements (coalesced, all loads issued before
-// any shared-memory update).  Histogram pass: per-warp digit counts with
-// warp-aggregated increments (match_any), one row per digit in the global
-// count matrix (digit-major), which an exclusive scan turns into each
-// block's global digit offsets.  Scatter pass: stable ranks from per-warp
-// running counts (match_any per round), then a block-local sort in shared
-// memory, then each digit's run is written out with consecutive threads on
-// consecutive addresses.
+// any shared-memory update).  Histogram pass: per-warp digit counts (shared
+// atomics), one row per digit in the global count matrix (digit-major),
+// which an exclusive scan turns into each block's global digit offsets.
+// Scatter pass: stable ranks from per-warp running counts, the lanes that
+// share a digit found with 8 ballots (one per digit bit), then a block-local
+// sort in shared memory, then each digit's run is written out with
+// consecutive threads on consecutive addresses.
 // ---------------------------------------------------------------------------
 
 constexpr int kRadixThreads = 256;
@@ -170,12 +170,9 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const K *__restric
         dig[r] = i < n ? (uint32_t)((keys[i] >> shift) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
     }
     __syncthreads();
-    const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int r = 0; r < kRadixItems; ++r) {
-        const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
-        if (dig[r] < kRadixDigits && (peers & lt) == 0u) atomicAdd(&h[warp][dig[r]], (uint32_t)__popc(peers));
-    }
+    for (int r = 0; r < kRadixItems; ++r)
+        if (dig[r] < kRadixDigits) atomicAdd(&h[warp][dig[r]], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadixDigits; d += kRadixThreads) {
         uint32_t s = 0;
@@ -216,8 +213,15 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
         const uint32_t i = base + r * 32 + lane;
-        const uint32_t d = i < n ? (uint32_t)((k[r] >> shift) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const bool ok = i < n;
+        const uint32_t d = ok ? (uint32_t)((k[r] >> shift) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
+        // lanes holding the same digit: agree on all 8 bits, among valid lanes
+        unsigned peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? m : ~m;
+        }
         const uint32_t before = d < kRadixDigits ? wcnt[warp][d] : 0u;
         __syncwarp();
         if (d < kRadixDigits && (peers & lt) == 0u) wcnt[warp][d] = before + __popc(peers);
