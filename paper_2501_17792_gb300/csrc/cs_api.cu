@@ -65,6 +65,10 @@ struct cs_ctx {
     DevBuf<uint2> rect, ranges;
     DevBuf<uint16_t> ptile, ptile2;
     DevBuf<float4> img;  // for cs_render_to_host
+    // split compositing of long tile lists
+    DevBuf<int32_t> bw_slot, bw_tile, bw_meta;
+    DevBuf<uint32_t> bw_chunk0, bw_done;
+    DevBuf<float4> bw_state, bw_part;
 
     // last frame
     int64_t S = 0, P = 0;
@@ -308,6 +312,8 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->bins); release(ctx->bins_sorted); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
     release(ctx->scratch); release(ctx->rect); release(ctx->ranges); release(ctx->ptile);
     release(ctx->ptile2); release(ctx->img);
+    release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_chunk0);
+    release(ctx->bw_done); release(ctx->bw_state); release(ctx->bw_part);
     if (ctx->d_meta) cudaFree(ctx->d_meta);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
     if (ctx->h_pairs) cudaFreeHost(ctx->h_pairs);
@@ -651,7 +657,20 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     launched += launch_tile_ranges((uint32_t)P, ptile, ctx->ranges.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[7], st));
     // 8. compositing
-    launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ctx->ranges.p, pval, ctx->rec.p, out, st);
+    {
+        const size_t ms = blend_max_slots((size_t)T, (size_t)P), mc = blend_max_chunks((size_t)T, (size_t)P);
+        CS_TRY(ensure(ctx, ctx->bw_slot, (size_t)T, "blend slots"));
+        CS_TRY(ensure(ctx, ctx->bw_tile, ms, "blend slot tiles"));
+        CS_TRY(ensure(ctx, ctx->bw_meta, 2, "blend plan"));
+        CS_TRY(ensure(ctx, ctx->bw_chunk0, ms + 1, "blend chunk offsets"));
+        CS_TRY(ensure(ctx, ctx->bw_done, ms, "blend slot flags"));
+        CS_TRY(ensure(ctx, ctx->bw_state, ms * 256, "blend pass-1 state"));
+        CS_TRY(ensure(ctx, ctx->bw_part, mc * 256, "blend chunk partials"));
+    }
+    BlendWork bw{ctx->bw_slot.p, ctx->bw_tile.p, ctx->bw_chunk0.p, ctx->bw_done.p, ctx->bw_state.p, ctx->bw_part.p,
+                 ctx->bw_meta.p};
+    launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ctx->ranges.p, pval, ctx->rec.p, out,
+                             bw, (uint32_t)P, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[8], st));
     CS_CUDA(cudaGetLastError());
     ctx->timed = timing;
@@ -742,7 +761,9 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
     int64_t fb = bytes_of(ctx->rec) + bytes_of(ctx->key) + bytes_of(ctx->ids) + bytes_of(ctx->key2) +
                  bytes_of(ctx->ids2) + bytes_of(ctx->bins) + bytes_of(ctx->bins_sorted) + bytes_of(ctx->pair_off) + bytes_of(ctx->pval) +
                  bytes_of(ctx->pval2) + bytes_of(ctx->scratch) + bytes_of(ctx->rect) + bytes_of(ctx->ranges) +
-                 bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img);
+                 bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img) + bytes_of(ctx->bw_slot) +
+                 bytes_of(ctx->bw_tile) + bytes_of(ctx->bw_meta) + bytes_of(ctx->bw_chunk0) + bytes_of(ctx->bw_done) +
+                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part);
     out->template_bytes = tb;
     out->instance_bytes = ib;
     out->frame_bytes = fb;
@@ -813,7 +834,16 @@ constexpr size_t kOffPval = kOffPtile2 + a256(kStaticPairs * 2);
 constexpr size_t kOffPval2 = kOffPval + a256(kStaticPairs * 4);
 constexpr size_t kOffRanges = kOffPval2 + a256(kStaticPairs * 4);
 constexpr size_t kOffScratch = kOffRanges + a256(kStaticTiles * sizeof(uint2));
-constexpr size_t kStaticBytes = kOffScratch + a256(kStaticScratchWords * 4);  // about 10.2 MB
+constexpr size_t kStaticSlots = blend_max_slots(kStaticTiles, kStaticPairs);
+constexpr size_t kStaticChunks = blend_max_chunks(kStaticTiles, kStaticPairs);
+constexpr size_t kOffBwSlot = kOffScratch + a256(kStaticScratchWords * 4);
+constexpr size_t kOffBwTile = kOffBwSlot + a256(kStaticTiles * 4);
+constexpr size_t kOffBwMeta = kOffBwTile + a256(kStaticSlots * 4);
+constexpr size_t kOffBwChunk0 = kOffBwMeta + a256(2 * 4);
+constexpr size_t kOffBwDone = kOffBwChunk0 + a256((kStaticSlots + 1) * 4);
+constexpr size_t kOffBwState = kOffBwDone + a256(kStaticSlots * 4);
+constexpr size_t kOffBwPart = kOffBwState + a256(kStaticSlots * 256 * sizeof(float4));
+constexpr size_t kStaticBytes = kOffBwPart + a256(kStaticChunks * 256 * sizeof(float4));  // about 10.7 MB
 
 }  // namespace
 
@@ -945,7 +975,12 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     // the array keeps the previous call's ranges: clear them
     CS_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * T, st));
     launched += launch_tile_ranges((uint32_t)P, ptile, ranges, st);
-    launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ranges, pval, rec, out, st);
+    BlendWork bw{reinterpret_cast<int32_t *>(base + kOffBwSlot), reinterpret_cast<int32_t *>(base + kOffBwTile),
+                 reinterpret_cast<uint32_t *>(base + kOffBwChunk0), reinterpret_cast<uint32_t *>(base + kOffBwDone),
+                 reinterpret_cast<float4 *>(base + kOffBwState), reinterpret_cast<float4 *>(base + kOffBwPart),
+                 reinterpret_cast<int32_t *>(base + kOffBwMeta)};
+    launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ranges, pval, rec, out, bw,
+                             (uint32_t)P, st);
     CS_CUDA(cudaGetLastError());
     if (stats) {
         stats->instances = I;

@@ -11,16 +11,25 @@
 // tile size.
 //
 // One CTA per tile, one thread per pixel, each warp an 8x4 block of the tile.
-// The CTA walks the tile's depth-ordered pairs in batches of 256, software
-// pipelined: while the warps composite batch k from one half of a shared
-// double buffer, each thread holds in registers the record it loaded for
-// batch k+1; after compositing it stages that record into the other half
-// (with the warp blocks its reach box overlaps as an 8-bit mask, and the
-// exponent pre-scaled to base 2: e^q = 2^(q log2 e) on the hardware ex2
-// unit) and issues the loads of batch k+2, so global latency hides behind a
-// whole batch of compositing.  Each warp walks only the splats marked for
-// its block (ballot over 32 at a time); the CTA leaves once every pixel of
-// the tile is saturated.
+// A CTA walks depth-ordered pairs in batches of 256, software pipelined:
+// while the warps composite batch k from one half of a shared double buffer,
+// each thread holds in registers the record it loaded for batch k+1; after
+// compositing it stages that record into the other half (with the warp
+// blocks its reach box overlaps as an 8-bit mask, and the exponent
+// pre-scaled to base 2: e^q = 2^(q log2 e) on the hardware ex2 unit) and
+// issues the loads of batch k+2.  Each warp walks only the splats marked for
+// its block; the CTA leaves once every pixel is saturated.
+//
+// Long lists are split in depth order (the compositing operator is
+// associative): pass 1 composites the first kBudget pairs of every tile;
+// tiles with unsaturated pixels left hand the rest to pass 2, which
+// composites chunks of kChunk pairs in parallel, each from T = 1 and only
+// for pixels pass 1 left open; the merge pass then combines, per pixel,
+// C += T C_k, T *= T_k in order.  A chunk inside which the pixel would meet
+// the stop rule (T T_k < 1e-4) is composited again for that pixel from its
+// true T, so the stop rule holds exactly as in the definition.
+#include <algorithm>
+
 #include "cs_internal.cuh"
 
 namespace cs {
@@ -28,6 +37,8 @@ namespace cs {
 constexpr int kBlendThreads = kTile * kTile;
 constexpr int kBlockW = 8, kBlockH = 4;  // pixels per warp
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr uint32_t kBudget = kBlendBudget;  // pairs of pass 1 per tile
+constexpr uint32_t kChunk = kBlendChunk;    // pairs per pass-2 chunk
 
 // e^q evaluated as 2^(q log2 e) on the hardware ex2 unit
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -53,31 +64,29 @@ __device__ __forceinline__ void load_record(StagedRecord &r, const uint32_t *__r
     }
 }
 
-__global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int H,
-                                                         const uint2 *__restrict__ ranges,
-                                                         const uint32_t *__restrict__ pval,
-                                                         const float4 *__restrict__ rec,
-                                                         float4 *__restrict__ out) {
+struct BlendShared {
     // staged splats: {u, v, a', b'}, {c', log2 o, radius, -}, {r, g, b, -} with
     // p = q log2 e = a' dx^2 + b' dx dy + c' dy^2
-    __shared__ float4 s0[2][kBlendThreads];
-    __shared__ float4 s1[2][kBlendThreads];
-    __shared__ float4 s2[2][kBlendThreads];
-    __shared__ uint8_t smask[2][kBlendThreads];
-    const int tile = blockIdx.x;
-    const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tx0 = txi * kTile, ty0 = tyi * kTile;
-    const int px = tx0 + (warp & 1) * kBlockW + (lane & (kBlockW - 1));
-    const int py = ty0 + (warp >> 1) * kBlockH + (lane / kBlockW);
-    const bool inside = px < W && py < H;
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-    const uint32_t wbit = 1u << warp;
-    const uint2 rg = ranges[tile];
-    float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-    bool done = !inside;
+    float4 s0[2][kBlendThreads];
+    float4 s1[2][kBlendThreads];
+    float4 s2[2][kBlendThreads];
+    uint8_t mask[2][kBlendThreads];
+};
 
-    // stage a loaded record into half `h`: pre-scaled exponent, warp-block mask
+struct Pixel {
+    float T, r, g, b;
+    bool done;     // saturated, outside the image, or not composited here
+    bool stopped;  // met the stop rule in this call
+};
+
+// Composite pairs [start, end) of a tile into the calling thread's pixel.
+// Every thread of the CTA must call it with the same range.
+__device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start, uint32_t end,
+                                                const uint32_t *__restrict__ pval,
+                                                const float4 *__restrict__ rec, int tx0, int ty0,
+                                                float fpx, float fpy, Pixel &px) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t wbit = 1u << warp;
     auto stage = [&](const StagedRecord &r, int h) {
         uint32_t m = 0;
         if (r.have) {
@@ -89,68 +98,245 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int
                 const int bx = (w & 1) * kBlockW, by = (w >> 1) * kBlockH;
                 if (x0 <= bx + kBlockW - 1 && x1 >= bx && y0 <= by + kBlockH - 1 && y1 >= by) m |= 1u << w;
             }
-            s0[h][tid] = make_float4(r.a.x, r.a.y, -0.5f * kLog2e * r.a.z, -kLog2e * r.a.w);
-            s1[h][tid] = make_float4(-0.5f * kLog2e * r.b.x, r.q.w, r.b.z, 0.0f);
-            s2[h][tid] = r.c;
+            sh.s0[h][tid] = make_float4(r.a.x, r.a.y, -0.5f * kLog2e * r.a.z, -kLog2e * r.a.w);
+            sh.s1[h][tid] = make_float4(-0.5f * kLog2e * r.b.x, r.q.w, r.b.z, 0.0f);
+            sh.s2[h][tid] = r.c;
         }
-        smask[h][tid] = (uint8_t)m;
+        sh.mask[h][tid] = (uint8_t)m;
     };
-
+    // the buffers may still be read by a previous call; leave when no pixel is open
+    if (__syncthreads_count(px.done) == kBlendThreads || start >= end) return;
     StagedRecord nxt;
-    load_record(nxt, pval, rec, rg.x + tid, rg.y);
+    load_record(nxt, pval, rec, start + tid, end);
     stage(nxt, 0);
-    load_record(nxt, pval, rec, rg.x + kBlendThreads + tid, rg.y);
+    load_record(nxt, pval, rec, start + kBlendThreads + tid, end);
     __syncthreads();
     int h = 0;
-    for (uint32_t base = rg.x; base < rg.y; base += kBlendThreads, h ^= 1) {
-        const int nb = (int)min((uint32_t)kBlendThreads, rg.y - base);
+    for (uint32_t base = start; base < end; base += kBlendThreads, h ^= 1) {
+        const int nb = (int)min((uint32_t)kBlendThreads, end - base);
         for (int c = 0; c < nb; c += 32) {
-            if (__all_sync(0xffffffffu, done)) break;
-            const bool mine = (smask[h][c + lane] & wbit) != 0 && c + lane < nb;
+            if (__all_sync(0xffffffffu, px.done)) break;
+            const bool mine = (sh.mask[h][c + lane] & wbit) != 0 && c + lane < nb;
             uint32_t m = __ballot_sync(0xffffffffu, mine);
             while (m) {
                 const int j = c + __ffs(m) - 1;
                 m &= m - 1;
-                if (done) continue;
-                const float4 a = s0[h][j];  // u, v, a', b'
-                const float4 b = s1[h][j];  // c', log2 o, radius
+                if (px.done) continue;
+                const float4 a = sh.s0[h][j];  // u, v, a', b'
+                const float4 b = sh.s1[h][j];  // c', log2 o, radius
                 const float dx = fpx - a.x, dy = fpy - a.y;
                 if (fmaxf(fabsf(dx), fabsf(dy)) > b.z) continue;
                 const float p = dx * (a.z * dx + a.w * dy) + b.x * dy * dy;
                 if (p > 0.0f) continue;
                 const float alpha = fminf(0.99f, ex2_approx(p + b.y));
                 if (alpha < (1.0f / 255.0f)) continue;
-                const float Tn = T * (1.0f - alpha);
+                const float Tn = px.T * (1.0f - alpha);
                 if (Tn < 1e-4f) {
-                    done = true;
+                    px.done = true;
+                    px.stopped = true;
                     continue;
                 }
-                const float4 col = s2[h][j];
-                const float wgt = alpha * T;
-                cr += col.x * wgt;
-                cg += col.y * wgt;
-                cb += col.z * wgt;
-                T = Tn;
+                const float4 col = sh.s2[h][j];
+                const float wgt = alpha * px.T;
+                px.r += col.x * wgt;
+                px.g += col.y * wgt;
+                px.b += col.z * wgt;
+                px.T = Tn;
             }
         }
         // the other half was last read before the previous barrier: refill it
         // with the next batch (loaded while this one was composited) and
         // start loading the batch after
-        if (base + kBlendThreads < rg.y) {
+        if (base + kBlendThreads < end) {
             stage(nxt, h ^ 1);
-            load_record(nxt, pval, rec, base + 2 * kBlendThreads + tid, rg.y);
+            load_record(nxt, pval, rec, base + 2 * kBlendThreads + tid, end);
         }
-        if (__syncthreads_count(done) == kBlendThreads) break;
+        if (__syncthreads_count(px.done) == kBlendThreads) break;
     }
-    if (inside) out[(size_t)py * W + px] = make_float4(cr, cg, cb, 1.0f - T);
+}
+
+struct TileGeom {
+    int tx0, ty0, px, py;
+    bool inside;
+    float fpx, fpy;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int H) {
+    TileGeom g;
+    const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    g.tx0 = txi * kTile;
+    g.ty0 = tyi * kTile;
+    g.px = g.tx0 + (warp & 1) * kBlockW + (lane & (kBlockW - 1));
+    g.py = g.ty0 + (warp >> 1) * kBlockH + (lane / kBlockW);
+    g.inside = g.px < W && g.py < H;
+    g.fpx = (float)g.px + 0.5f;
+    g.fpy = (float)g.py + 0.5f;
+    return g;
+}
+
+// Pass 1: the first kBudget pairs of every tile.
+__global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int H,
+                                                         const uint2 *__restrict__ ranges,
+                                                         const uint32_t *__restrict__ pval,
+                                                         const float4 *__restrict__ rec,
+                                                         float4 *__restrict__ out, BlendWork work) {
+    __shared__ BlendShared sh;
+    const int tile = blockIdx.x;
+    const TileGeom g = tile_geom(tile, tiles_x, W, H);
+    const uint2 rg = ranges[tile];
+    Pixel px{1.0f, 0.0f, 0.0f, 0.0f, !g.inside, false};
+    const uint32_t end1 = rg.y - rg.x > kBudget ? rg.x + kBudget : rg.y;
+    composite_range(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
+    if (end1 < rg.y) {
+        // pairs remain: record the pixel state for pass 2 and the merge
+        const int slot = work.cand_slot[tile];
+        const int all = __syncthreads_count(px.done) == kBlendThreads;
+        if (threadIdx.x == 0) work.cand_done[slot] = (uint32_t)all;
+        work.state[(size_t)slot * kBlendThreads + threadIdx.x] =
+            make_float4(px.r, px.g, px.b, px.done ? -px.T : px.T);
+        if (!all) return;
+    }
+    if (g.inside) out[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, 1.0f - px.T);
+}
+
+// Pass 2: chunk c of a tile's remaining pairs, from T = 1, for the pixels
+// pass 1 left open.  Writes (r, g, b, T) with T negated when the chunk met
+// the stop rule.
+__global__ void __launch_bounds__(kBlendThreads) k_blend_chunks(int tiles_x, int W, int H,
+                                                                const uint2 *__restrict__ ranges,
+                                                                const uint32_t *__restrict__ pval,
+                                                                const float4 *__restrict__ rec,
+                                                                BlendWork work) {
+    __shared__ BlendShared sh;
+    const uint32_t w = blockIdx.x;
+    const int n_cand = work.meta[0];
+    if (w >= (uint32_t)work.meta[1]) return;
+    // slot: last candidate whose first chunk <= w
+    int lo = 0, hi = n_cand - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (work.cand_chunk0[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const int slot = lo;
+    if (work.cand_done[slot]) return;
+    const int tile = work.cand_tile[slot];
+    const TileGeom g = tile_geom(tile, tiles_x, W, H);
+    const uint2 rg = ranges[tile];
+    const uint32_t c = w - work.cand_chunk0[slot];
+    const uint32_t start = rg.x + kBudget + c * kChunk;
+    const uint32_t end = min(rg.y, start + kChunk);
+    const float4 s1 = work.state[(size_t)slot * kBlendThreads + threadIdx.x];
+    Pixel px{1.0f, 0.0f, 0.0f, 0.0f, !g.inside || s1.w < 0.0f, false};
+    composite_range(sh, start, end, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
+    work.part[(size_t)w * kBlendThreads + threadIdx.x] = make_float4(px.r, px.g, px.b, px.stopped ? -px.T : px.T);
+}
+
+// Merge: pass-1 state then the chunks in depth order, per pixel.
+__global__ void __launch_bounds__(kBlendThreads) k_blend_merge(int tiles_x, int W, int H,
+                                                               const uint2 *__restrict__ ranges,
+                                                               const uint32_t *__restrict__ pval,
+                                                               const float4 *__restrict__ rec,
+                                                               float4 *__restrict__ out, BlendWork work) {
+    __shared__ BlendShared sh;
+    const int slot = blockIdx.x;
+    if (slot >= work.meta[0] || work.cand_done[slot]) return;
+    const int tile = work.cand_tile[slot];
+    const TileGeom g = tile_geom(tile, tiles_x, W, H);
+    const uint2 rg = ranges[tile];
+    const float4 s1 = work.state[(size_t)slot * kBlendThreads + threadIdx.x];
+    float T = fabsf(s1.w), r = s1.x, gg = s1.y, b = s1.z;
+    bool done = !g.inside || s1.w < 0.0f;
+    const uint32_t c0 = work.cand_chunk0[slot], c1 = work.cand_chunk0[slot + 1];
+    for (uint32_t w = c0; w < c1; ++w) {
+        const float4 pk = work.part[(size_t)w * kBlendThreads + threadIdx.x];
+        const float Tk = fabsf(pk.w);
+        const bool stopped = pk.w < 0.0f;
+        bool redo = false;
+        if (!done) {
+            if (T * Tk >= 1e-4f) {
+                // no splat of the chunk reaches the stop rule from this T:
+                // the chunk's composite applies as a whole
+                r += T * pk.x;
+                gg += T * pk.y;
+                b += T * pk.z;
+                T *= Tk;
+                done = stopped;
+            } else {
+                redo = true;
+            }
+        }
+        if (__syncthreads_or(redo)) {
+            // the pixel meets the stop rule inside this chunk: composite the
+            // chunk again from the pixel's true transmittance
+            Pixel px{T, r, gg, b, !redo, false};
+            const uint32_t start = rg.x + kBudget + (w - c0) * kChunk;
+            composite_range(sh, start, min(rg.y, start + kChunk), pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
+            if (redo) {
+                T = px.T;
+                r = px.r;
+                gg = px.g;
+                b = px.b;
+                done = true;
+            }
+        }
+    }
+    if (g.inside) out[(size_t)g.py * W + g.px] = make_float4(r, gg, b, 1.0f - T);
+}
+
+// Plan of the split: tiles with more than kBudget pairs get a slot and
+// ceil((n - kBudget) / kChunk) chunks (one block, deterministic scans).
+__global__ void __launch_bounds__(1024) k_blend_plan(int n_tiles, const uint2 *__restrict__ ranges,
+                                                     BlendWork work) {
+    __shared__ uint32_t tot_c, tot_k;
+    __shared__ uint32_t run_c, run_k;
+    if (threadIdx.x == 0) {
+        run_c = 0;
+        run_k = 0;
+    }
+    __syncthreads();
+    for (int base = 0; base < n_tiles; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        uint32_t n = 0;
+        if (t < n_tiles) n = ranges[t].y - ranges[t].x;
+        const uint32_t cand = n > kBudget ? 1u : 0u;
+        const uint32_t nk = cand ? (n - kBudget + kChunk - 1) / kChunk : 0u;
+        const uint32_t ec = block_exclusive_scan(cand, &tot_c);
+        const uint32_t ek = block_exclusive_scan(nk, &tot_k);
+        if (t < n_tiles) {
+            const int slot = cand ? (int)(run_c + ec) : -1;
+            work.cand_slot[t] = slot;
+            if (cand) {
+                work.cand_tile[slot] = t;
+                work.cand_chunk0[slot] = run_k + ek;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            run_c += tot_c;
+            run_k += tot_k;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        work.cand_chunk0[run_c] = run_k;
+        work.meta[0] = (int)run_c;
+        work.meta[1] = (int)run_k;
+    }
 }
 
 int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, const uint32_t *pval,
-                 const float4 *rec, float4 *out, cudaStream_t st) {
+                 const float4 *rec, float4 *out, const BlendWork &work, uint32_t n_pairs, cudaStream_t st) {
     const int n = tiles_x * tiles_y;
     if (n <= 0) return 0;
-    k_blend<<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out);
-    return 1;
+    const size_t max_cand = blend_max_slots((size_t)n, n_pairs);
+    const size_t max_chunks = blend_max_chunks((size_t)n, n_pairs);
+    k_blend_plan<<<1, 1024, 0, st>>>(n, ranges, work);
+    k_blend<<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+    if (n_pairs <= kBudget) return 2;  // no tile can have pairs left after pass 1
+    k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);
+    k_blend_merge<<<(unsigned)max_cand, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+    return 4;
 }
 
 }  // namespace cs

@@ -115,12 +115,12 @@ constexpr float kAlphaMargin = 2e-3f;  // in the exponent: alpha within 0.2 %
 
 __device__ __forceinline__ float splat_fcut(float opacity) {
     // 2 (ln(255 o) + margin); negative when o < 1/255 (never contributes)
-    return __fmul_rn(2.0f, __fadd_rn(logf(__fmul_rn(255.0f, opacity)), kAlphaMargin));
+    return __fmul_rn(2.0f, __fadd_rn(__logf(__fmul_rn(255.0f, opacity)), kAlphaMargin));
 }
 
-__device__ __forceinline__ float edge_quad(float A, float B, float C, float a, float lo, float hi) {
-    // min over t in [lo, hi] of A a^2 + 2 B a t + C t^2 (C > 0)
-    float t = __fdiv_rn(-__fmul_rn(B, a), C);
+__device__ __forceinline__ float edge_quad(float A, float B, float C, float invC, float a, float lo, float hi) {
+    // min over t in [lo, hi] of A a^2 + 2 B a t + C t^2 (C > 0), at t = -B a / C
+    float t = __fmul_rn(-__fmul_rn(B, a), invC);
     t = fminf(fmaxf(t, lo), hi);
     return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, a), a), __fmul_rn(__fmul_rn(2.0f, B), __fmul_rn(a, t))),
                      __fmul_rn(__fmul_rn(C, t), t));
@@ -132,10 +132,11 @@ __device__ __forceinline__ bool splat_rect_hits(float u, float v, float A, float
     const float a1 = __fsub_rn(__fadd_rn((float)px0, 0.5f), u), a2 = __fsub_rn(__fadd_rn((float)px1, 0.5f), u);
     const float b1 = __fsub_rn(__fadd_rn((float)py0, 0.5f), v), b2 = __fsub_rn(__fadd_rn((float)py1, 0.5f), v);
     if (a1 <= 0.0f && a2 >= 0.0f && b1 <= 0.0f && b2 >= 0.0f) return true;
-    float f = edge_quad(A, B, C, a1, b1, b2);
-    f = fminf(f, edge_quad(A, B, C, a2, b1, b2));
-    f = fminf(f, edge_quad(C, B, A, b1, a1, a2));
-    f = fminf(f, edge_quad(C, B, A, b2, a1, a2));
+    const float iA = __frcp_rn(A), iC = __frcp_rn(C);
+    float f = edge_quad(A, B, C, iC, a1, b1, b2);
+    f = fminf(f, edge_quad(A, B, C, iC, a2, b1, b2));
+    f = fminf(f, edge_quad(C, B, A, iA, b1, a1, a2));
+    f = fminf(f, edge_quad(C, B, A, iA, b2, a1, a2));
     return f <= fcut;
 }
 
@@ -154,6 +155,36 @@ __device__ __forceinline__ void box_range(float c, float r, int size, int &lo, i
 // 1e-4 relative + 0.01 px so FP32 rounding cannot cut a pixel off).
 __device__ __forceinline__ float ellipse_reach(float fcut, float sigma_axis) {
     return __fadd_rn(__fmul_rn(sqrtf(__fmul_rn(fcut, sigma_axis)), 1.0001f), 0.01f);
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim a multiple of
+// 32); returns the exclusive prefix, *total (shared) receives the block sum.
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const uint32_t inc = warp_inclusive_scan(v);
+    __syncthreads();  // warp_sums may still be read by a previous call
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t s = lane < nwarps ? warp_sums[lane] : 0u;
+        const uint32_t si = warp_inclusive_scan(s);
+        warp_sums[lane] = si - s;
+        if (lane == 31) *total = si;
+    }
+    __syncthreads();
+    return inc - v + warp_sums[warp];
 }
 
 // meta words written by the cull kernel and read back by the host
@@ -199,7 +230,31 @@ int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, c
 int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cudaStream_t st);
 
 // ---- compositing (cs_blend.cu) ----
-int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges,
-                  const uint32_t *pval, const float4 *rec, float4 *out, cudaStream_t st);
+// Work buffers of the split compositing of long tile lists (sizes from
+// blend_work_sizes): per tile, the slot of a tile with pairs left after the
+// first pass (-1 if none); per slot, its tile, its first chunk (one extra
+// entry holds the chunk total), whether pass 1 finished it, and the pass-1
+// pixel state (r, g, b, T; T negated when saturated); per chunk, the chunk's
+// pixel composite (r, g, b, T; T negated when it met the stop rule);
+// meta[0] = slots, meta[1] = chunks.
+struct BlendWork {
+    int32_t *cand_slot;
+    int32_t *cand_tile;
+    uint32_t *cand_chunk0;
+    uint32_t *cand_done;
+    float4 *state;
+    float4 *part;
+    int32_t *meta;
+};
+constexpr uint32_t kBlendBudget = 8192;  // pairs composited by pass 1 per tile
+constexpr uint32_t kBlendChunk = 8192;   // pairs per pass-2 chunk
+constexpr size_t blend_max_slots(size_t n_tiles, size_t n_pairs) {
+    return n_tiles < n_pairs / kBlendBudget + 1 ? n_tiles : n_pairs / kBlendBudget + 1;
+}
+constexpr size_t blend_max_chunks(size_t n_tiles, size_t n_pairs) {
+    return n_pairs / kBlendChunk + blend_max_slots(n_tiles, n_pairs) + 1;
+}
+int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, const uint32_t *pval,
+                 const float4 *rec, float4 *out, const BlendWork &work, uint32_t n_pairs, cudaStream_t st);
 
 }  // namespace cs

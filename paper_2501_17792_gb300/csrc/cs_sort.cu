@@ -23,33 +23,8 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += n;
-    }
-    return v;
-}
-
-// Block-wide exclusive scan of one value per thread; returns the exclusive
-// prefix, *total (shared) receives the block sum after the call.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total) {
-    __shared__ uint32_t warp_sums[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const uint32_t inc = warp_incl_scan(v);
-    if (lane == 31) warp_sums[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t s = lane < nwarps ? warp_sums[lane] : 0u;
-        const uint32_t si = warp_incl_scan(s);
-        warp_sums[lane] = si - s;
-        if (lane == 31) *total = si;
-    }
-    __syncthreads();
-    return inc - v + warp_sums[warp];
+    return block_exclusive_scan(v, total);
 }
 
 // element i of a scan input: plain value (MODE 0) or pair count of a bin

@@ -261,6 +261,36 @@ def test_nan_pose_is_culled_and_others_unchanged():
     assert np.abs(img - ref).max() <= 1e-6
 
 
+def _deep_field(seed=5, n=60000, w=48, h=32):
+    """Many faint small splats over a tiny image: every tile holds several
+    compositing chunks of pairs, and the accumulated opacity is tuned so
+    that pixels saturate at all depths of their lists, or never."""
+    rng = np.random.default_rng(seed)
+    f = 60.0
+    z = rng.uniform(2.0, 6.0, n)
+    px = rng.uniform(0, w, n)
+    py = rng.uniform(0, h, n)
+    x = (px - w / 2) * z / f
+    y = (py - h / 2) * z / f
+    s = (1.5 * z / f)[:, None] * np.exp(rng.normal(0, 0.3, (n, 3)))
+    q = rng.standard_normal((n, 4))
+    op = rng.uniform(0.008, 0.026, n)
+    sh = 0.3 * rng.standard_normal((n, 4, 3))
+    tpl = U.template_from(np.stack([x, y, z], 1), s, q, op, sh)
+    return U.scene_of([tpl], U.instances(1), U.identity_camera(w, h, f))
+
+
+def test_split_compositing_of_long_tile_lists():
+    sc = _deep_field()
+    r, img, ref, errs, st = full_check(sc, label="deep_field_split", max_boundary=0.2)
+    rng = r.debug("tile_ranges").astype(np.int64)
+    counts = rng[:, 1] - rng[:, 0]
+    assert counts.max() > 3 * 8192, counts  # several pass-2 chunks per tile
+    # some pixels saturate (late in their lists), others never do
+    A = ref["rgba"][..., 3]
+    assert (A < 0.999).mean() > 0.05 and (A > 0.9998).mean() > 0.5
+
+
 def test_error_codes():
     from paper_2501_17792_gb300 import binding
     sc = _small_crowd(width=64, height=40)
