@@ -66,7 +66,7 @@ struct cs_ctx {
     DevBuf<uint16_t> ptile, ptile2;
     DevBuf<float4> img;  // for cs_render_to_host
     // split compositing of long tile lists
-    DevBuf<int32_t> bw_slot, bw_tile, bw_meta;
+    DevBuf<int32_t> bw_slot, bw_tile, bw_meta, bw_stop;
     DevBuf<uint32_t> bw_chunk0, bw_done;
     DevBuf<float4> bw_state, bw_part;
 
@@ -312,7 +312,7 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->bins); release(ctx->bins_sorted); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
     release(ctx->scratch); release(ctx->rect); release(ctx->ranges); release(ctx->ptile);
     release(ctx->ptile2); release(ctx->img);
-    release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_chunk0);
+    release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_chunk0);
     release(ctx->bw_done); release(ctx->bw_state); release(ctx->bw_part);
     if (ctx->d_meta) cudaFree(ctx->d_meta);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
@@ -666,9 +666,10 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         CS_TRY(ensure(ctx, ctx->bw_done, ms, "blend slot flags"));
         CS_TRY(ensure(ctx, ctx->bw_state, ms * 256, "blend pass-1 state"));
         CS_TRY(ensure(ctx, ctx->bw_part, mc * 256, "blend chunk partials"));
+        CS_TRY(ensure(ctx, ctx->bw_stop, ms * 256, "blend stop chunks"));
     }
     BlendWork bw{ctx->bw_slot.p, ctx->bw_tile.p, ctx->bw_chunk0.p, ctx->bw_done.p, ctx->bw_state.p, ctx->bw_part.p,
-                 ctx->bw_meta.p};
+                 ctx->bw_meta.p, ctx->bw_stop.p};
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ctx->ranges.p, pval, ctx->rec.p, out,
                              bw, (uint32_t)P, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[8], st));
@@ -763,7 +764,7 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
                  bytes_of(ctx->pval2) + bytes_of(ctx->scratch) + bytes_of(ctx->rect) + bytes_of(ctx->ranges) +
                  bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img) + bytes_of(ctx->bw_slot) +
                  bytes_of(ctx->bw_tile) + bytes_of(ctx->bw_meta) + bytes_of(ctx->bw_chunk0) + bytes_of(ctx->bw_done) +
-                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part);
+                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop);
     out->template_bytes = tb;
     out->instance_bytes = ib;
     out->frame_bytes = fb;
@@ -843,7 +844,8 @@ constexpr size_t kOffBwChunk0 = kOffBwMeta + a256(2 * 4);
 constexpr size_t kOffBwDone = kOffBwChunk0 + a256((kStaticSlots + 1) * 4);
 constexpr size_t kOffBwState = kOffBwDone + a256(kStaticSlots * 4);
 constexpr size_t kOffBwPart = kOffBwState + a256(kStaticSlots * 256 * sizeof(float4));
-constexpr size_t kStaticBytes = kOffBwPart + a256(kStaticChunks * 256 * sizeof(float4));  // about 10.7 MB
+constexpr size_t kOffBwStop = kOffBwPart + a256(kStaticChunks * 256 * sizeof(float4));
+constexpr size_t kStaticBytes = kOffBwStop + a256(kStaticSlots * 256 * 4);  // about 10.7 MB
 
 }  // namespace
 
@@ -978,7 +980,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     BlendWork bw{reinterpret_cast<int32_t *>(base + kOffBwSlot), reinterpret_cast<int32_t *>(base + kOffBwTile),
                  reinterpret_cast<uint32_t *>(base + kOffBwChunk0), reinterpret_cast<uint32_t *>(base + kOffBwDone),
                  reinterpret_cast<float4 *>(base + kOffBwState), reinterpret_cast<float4 *>(base + kOffBwPart),
-                 reinterpret_cast<int32_t *>(base + kOffBwMeta)};
+                 reinterpret_cast<int32_t *>(base + kOffBwMeta), reinterpret_cast<int32_t *>(base + kOffBwStop)};
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ranges, pval, rec, out, bw,
                              (uint32_t)P, st);
     CS_CUDA(cudaGetLastError());

@@ -25,9 +25,10 @@
 // tiles with unsaturated pixels left hand the rest to pass 2, which
 // composites chunks of kChunk pairs in parallel, each from T = 1 and only
 // for pixels pass 1 left open; the merge pass then combines, per pixel,
-// C += T C_k, T *= T_k in order.  A chunk inside which the pixel would meet
-// the stop rule (T T_k < 1e-4) is composited again for that pixel from its
-// true T, so the stop rule holds exactly as in the definition.
+// C += T C_k, T *= T_k in order, up to the chunk (if any) inside which the
+// pixel meets the stop rule (T T_k < 1e-4); the fix-up pass composites each
+// such chunk again, in parallel over chunks, for its stopping pixels from
+// their true T, so the stop rule holds exactly as in the definition.
 #include <algorithm>
 
 #include "cs_internal.cuh"
@@ -232,56 +233,72 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_chunks(int tiles_x, int
     work.part[(size_t)w * kBlendThreads + threadIdx.x] = make_float4(px.r, px.g, px.b, px.stopped ? -px.T : px.T);
 }
 
-// Merge: pass-1 state then the chunks in depth order, per pixel.
+// Merge: pass-1 state then the chunks in depth order, per pixel, up to the
+// chunk in which the pixel meets the stop rule: such pixels keep their
+// state before that chunk (in work.state) and its index (work.stop) for the
+// fix-up pass; the others are final.
 __global__ void __launch_bounds__(kBlendThreads) k_blend_merge(int tiles_x, int W, int H,
-                                                               const uint2 *__restrict__ ranges,
-                                                               const uint32_t *__restrict__ pval,
-                                                               const float4 *__restrict__ rec,
                                                                float4 *__restrict__ out, BlendWork work) {
-    __shared__ BlendShared sh;
     const int slot = blockIdx.x;
     if (slot >= work.meta[0] || work.cand_done[slot]) return;
     const int tile = work.cand_tile[slot];
     const TileGeom g = tile_geom(tile, tiles_x, W, H);
-    const uint2 rg = ranges[tile];
-    const float4 s1 = work.state[(size_t)slot * kBlendThreads + threadIdx.x];
+    const size_t pix = (size_t)slot * kBlendThreads + threadIdx.x;
+    const float4 s1 = work.state[pix];
     float T = fabsf(s1.w), r = s1.x, gg = s1.y, b = s1.z;
     bool done = !g.inside || s1.w < 0.0f;
+    int32_t stop = -1;
     const uint32_t c0 = work.cand_chunk0[slot], c1 = work.cand_chunk0[slot + 1];
-    for (uint32_t w = c0; w < c1; ++w) {
+    for (uint32_t w = c0; w < c1 && !done; ++w) {
         const float4 pk = work.part[(size_t)w * kBlendThreads + threadIdx.x];
         const float Tk = fabsf(pk.w);
-        const bool stopped = pk.w < 0.0f;
-        bool redo = false;
-        if (!done) {
-            if (T * Tk >= 1e-4f) {
-                // no splat of the chunk reaches the stop rule from this T:
-                // the chunk's composite applies as a whole
-                r += T * pk.x;
-                gg += T * pk.y;
-                b += T * pk.z;
-                T *= Tk;
-                done = stopped;
-            } else {
-                redo = true;
-            }
-        }
-        if (__syncthreads_or(redo)) {
-            // the pixel meets the stop rule inside this chunk: composite the
-            // chunk again from the pixel's true transmittance
-            Pixel px{T, r, gg, b, !redo, false};
-            const uint32_t start = rg.x + kBudget + (w - c0) * kChunk;
-            composite_range(sh, start, min(rg.y, start + kChunk), pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
-            if (redo) {
-                T = px.T;
-                r = px.r;
-                gg = px.g;
-                b = px.b;
-                done = true;
-            }
+        if (T * Tk >= 1e-4f) {
+            // no splat of the chunk reaches the stop rule from this T: the
+            // chunk's composite applies as a whole
+            r += T * pk.x;
+            gg += T * pk.y;
+            b += T * pk.z;
+            T *= Tk;
+            done = pk.w < 0.0f;
+        } else {
+            stop = (int32_t)w;
+            done = true;
         }
     }
-    if (g.inside) out[(size_t)g.py * W + g.px] = make_float4(r, gg, b, 1.0f - T);
+    work.stop[pix] = stop;
+    if (stop >= 0) work.state[pix] = make_float4(r, gg, b, T);
+    else if (g.inside) out[(size_t)g.py * W + g.px] = make_float4(r, gg, b, 1.0f - T);
+}
+
+// Fix-up: chunk w composited again, from their true transmittance, for the
+// pixels that meet the stop rule inside it.
+__global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W, int H,
+                                                             const uint2 *__restrict__ ranges,
+                                                             const uint32_t *__restrict__ pval,
+                                                             const float4 *__restrict__ rec,
+                                                             float4 *__restrict__ out, BlendWork work) {
+    __shared__ BlendShared sh;
+    const uint32_t w = blockIdx.x;
+    const int n_cand = work.meta[0];
+    if (w >= (uint32_t)work.meta[1]) return;
+    int lo = 0, hi = n_cand - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (work.cand_chunk0[mid] <= w) lo = mid; else hi = mid - 1;
+    }
+    const int slot = lo;
+    if (work.cand_done[slot]) return;
+    const size_t pix = (size_t)slot * kBlendThreads + threadIdx.x;
+    const bool mine = work.stop[pix] == (int32_t)w;
+    if (__syncthreads_count(mine) == 0) return;
+    const int tile = work.cand_tile[slot];
+    const TileGeom g = tile_geom(tile, tiles_x, W, H);
+    const uint2 rg = ranges[tile];
+    const float4 sb = mine ? work.state[pix] : make_float4(0.f, 0.f, 0.f, 1.f);
+    Pixel px{sb.w, sb.x, sb.y, sb.z, !mine, false};
+    const uint32_t start = rg.x + kBudget + (w - work.cand_chunk0[slot]) * kChunk;
+    composite_range(sh, start, min(rg.y, start + kChunk), pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
+    if (mine && g.inside) out[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, 1.0f - px.T);
 }
 
 // Plan of the split: tiles with more than kBudget pairs get a slot and
@@ -335,8 +352,9 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
     k_blend<<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
     if (n_pairs <= kBudget) return 2;  // no tile can have pairs left after pass 1
     k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);
-    k_blend_merge<<<(unsigned)max_cand, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
-    return 4;
+    k_blend_merge<<<(unsigned)max_cand, kBlendThreads, 0, st>>>(tiles_x, W, H, out, work);
+    k_blend_fix<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+    return 5;
 }
 
 }  // namespace cs

@@ -235,7 +235,8 @@ int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cud
 // first pass (-1 if none); per slot, its tile, its first chunk (one extra
 // entry holds the chunk total), whether pass 1 finished it, and the pass-1
 // pixel state (r, g, b, T; T negated when saturated); per chunk, the chunk's
-// pixel composite (r, g, b, T; T negated when it met the stop rule);
+// pixel composite (r, g, b, T; T negated when it met the stop rule); per
+// slot pixel, the chunk in which it meets the stop rule (-1 if none);
 // meta[0] = slots, meta[1] = chunks.
 struct BlendWork {
     int32_t *cand_slot;
@@ -245,6 +246,7 @@ struct BlendWork {
     float4 *state;
     float4 *part;
     int32_t *meta;
+    int32_t *stop;
 };
 constexpr uint32_t kBlendBudget = 8192;  // pairs composited by pass 1 per tile
 constexpr uint32_t kBlendChunk = 8192;   // pairs per pass-2 chunk

@@ -285,7 +285,7 @@ def test_split_compositing_of_long_tile_lists():
     r, img, ref, errs, st = full_check(sc, label="deep_field_split", max_boundary=0.2)
     rng = r.debug("tile_ranges").astype(np.int64)
     counts = rng[:, 1] - rng[:, 0]
-    assert counts.max() > 3 * 8192, counts  # several pass-2 chunks per tile
+    assert counts.min() > 8192, counts  # every tile has pass-2 chunks
     # some pixels saturate (late in their lists), others never do
     A = ref["rgba"][..., 3]
     assert (A < 0.999).mean() > 0.05 and (A > 0.9998).mean() > 0.5
