@@ -186,7 +186,7 @@ int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_fr
  * front.  CrowdSplat has no counterpart of this call; it renders exactly
  * what cs_render renders, with the per-frame scratch (splat records, sort
  * buffers, pair lists, tile ranges) taken from one static device array of
- * about 10.7 MB that every GPU loading the library holds until the process
+ * about 11.6 MB that every GPU loading the library holds until the process
  * exits.  Limits per frame: 65,536 splats, 262,144 (tile, splat) pairs,
  * 16,384 tiles (e.g. 2048 x 2048); larger frames fail with CS_ERR_CAPACITY
  * and a message naming the limit, leaving rgba_out unwritten.  The

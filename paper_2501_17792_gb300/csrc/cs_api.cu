@@ -845,7 +845,7 @@ constexpr size_t kOffBwDone = kOffBwChunk0 + a256((kStaticSlots + 1) * 4);
 constexpr size_t kOffBwState = kOffBwDone + a256(kStaticSlots * 4);
 constexpr size_t kOffBwPart = kOffBwState + a256(kStaticSlots * 256 * sizeof(float4));
 constexpr size_t kOffBwStop = kOffBwPart + a256(kStaticChunks * 256 * sizeof(float4));
-constexpr size_t kStaticBytes = kOffBwStop + a256(kStaticSlots * 256 * 4);  // about 10.7 MB
+constexpr size_t kStaticBytes = kOffBwStop + a256(kStaticSlots * 256 * 4);  // about 11.6 MB
 
 }  // namespace
 

@@ -249,7 +249,7 @@ struct BlendWork {
     int32_t *stop;
 };
 constexpr uint32_t kBlendBudget = 8192;  // pairs composited by pass 1 per tile
-constexpr uint32_t kBlendChunk = 8192;   // pairs per pass-2 chunk
+constexpr uint32_t kBlendChunk = 1024;   // pairs per pass-2 chunk
 constexpr size_t blend_max_slots(size_t n_tiles, size_t n_pairs) {
     return n_tiles < n_pairs / kBlendBudget + 1 ? n_tiles : n_pairs / kBlendBudget + 1;
 }
