@@ -222,8 +222,8 @@ const char *cs_last_error(const cs_ctx *ctx);
  * the buffer's full size in *size_out (may be NULL).  Synchronises. */
 #define CS_DBG_SKIN_B 1      /* float [I][24][12]: skinning transforms, instance-local */
 #define CS_DBG_VISIBLE 2     /* int32 [V]: visible instance ids in group order         */
-#define CS_DBG_GROUPS 3      /* int32 [G][6]: template, level, first slot, slots,
-                                gaussians per slot, first splat                        */
+#define CS_DBG_GROUPS 3      /* int32 [G][7]: template, level, first slot, slots,
+                                gaussians per slot, first splat, first projection CTA  */
 #define CS_DBG_RECORDS 4     /* float [S][16]: u, v, conic A, B, C, opacity, radius,
                                 depth, r, g, b, 0, reach x, reach y (pixel ranges lo | hi
                                 << 16 as float bits), fcut, log2 opacity              */

@@ -263,7 +263,7 @@ class Renderer:
               "depth_keys": np.uint32, "rects": np.uint16, "depth_order": np.uint32,
               "pair_tiles": np.uint16, "pair_splats": np.uint32, "tile_ranges": np.uint32}[which]
         a = buf.view(dt)
-        shape = {"skin_b": (-1, 24, 3, 4), "groups": (-1, 6), "records": (-1, 16), "rects": (-1, 4),
+        shape = {"skin_b": (-1, 24, 3, 4), "groups": (-1, 7), "records": (-1, 16), "rects": (-1, 4),
                  "tile_ranges": (-1, 2)}.get(which)
         return a.reshape(shape) if shape else a
 

@@ -582,6 +582,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     if (timing) CS_CUDA(cudaEventRecord(ev[1], st));
     // 2. LoD band, instance cull, grouping by (template, level)
     int64_t S = 0;
+    int proj_blocks = 0;
     if (I > 0) {
         launched += launch_cull_group(I, ctx->n_tpl, ctx->tid.p, ctx->root.p, ctx->d_tpl, cp, ctx->lod,
                           ctx->instance_cull, ctx->V.p, ctx->Cloc.p, ctx->vis.p, ctx->groups.p,
@@ -592,6 +593,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         ctx->visible = ctx->h_meta[kMetaVisible];
         ctx->n_groups = ctx->h_meta[kMetaGroups];
         S = ctx->h_meta[kMetaSplats];
+        proj_blocks = ctx->h_meta[kMetaBlocks];
         for (int l = 0; l < kMaxLevels; ++l) ctx->per_level[l] = ctx->h_meta[kMetaLevel0 + l];
         if (S >= 0x7fffffffLL) return fail(ctx, CS_ERR_CAPACITY, "more than 2^31 - 1 splats in a frame");
     } else {
@@ -614,7 +616,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Sa), scan_scratch_words(Sa + 1)), "scratch"));
     TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh};
     if (S > 0)
-        launched += launch_project((int)S, ctx->groups.p, ctx->n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
+        launched += launch_project(proj_blocks, ctx->groups.p, ctx->n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                        ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
                        ctx->rec.p, ctx->key.p, ctx->ids.p, ctx->rect.p, ctx->bins.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[3], st));
@@ -928,7 +930,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     // by cs_set_instances; nothing is allocated here)
     if (I > 0) launched += launch_fk(I, ctx->n_tpl, ctx->tid.p, ctx->pose.p, ctx->d_tpl, ctx->max_depth, ctx->B.p, st);
     int64_t S = 0;
-    int visible = 0, n_groups = 0, per_level[kMaxLevels] = {0, 0, 0, 0};
+    int visible = 0, n_groups = 0, proj_blocks = 0, per_level[kMaxLevels] = {0, 0, 0, 0};
     if (I > 0) {
         launched += launch_cull_group(I, ctx->n_tpl, ctx->tid.p, ctx->root.p, ctx->d_tpl, cp, ctx->lod,
                                       ctx->instance_cull, ctx->V.p, ctx->Cloc.p, ctx->vis.p, ctx->groups.p,
@@ -939,6 +941,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
         visible = ctx->h_meta[kMetaVisible];
         n_groups = ctx->h_meta[kMetaGroups];
         S = ctx->h_meta[kMetaSplats];
+        proj_blocks = ctx->h_meta[kMetaBlocks];
         for (int l = 0; l < kMaxLevels; ++l) per_level[l] = ctx->h_meta[kMetaLevel0 + l];
     }
     if ((size_t)S > kStaticSplats)
@@ -946,7 +949,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
                     (long long)S, kStaticSplats);
     TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh};
     if (S > 0)
-        launched += launch_project((int)S, ctx->groups.p, n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
+        launched += launch_project(proj_blocks, ctx->groups.p, n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                                    ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
                                    rec, key, ids, rect, bins, st);
     if (radix_scratch_words((size_t)std::max<int64_t>(S, 1)) > kStaticScratchWords ||

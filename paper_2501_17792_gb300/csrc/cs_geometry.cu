@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
     __syncthreads();
     if (threadIdx.x == 0) {
         int slot = 0, ng = 0;
-        long long splat = 0;
+        long long splat = 0, blocks = 0;
         int per_level[kMaxLevels] = {0, 0, 0, 0};
         for (int g = 0; g < n_grp; ++g) {
             gslot[g] = slot;
@@ -194,9 +194,11 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
             G.nslots = c;
             G.ng = tpls[t].n_level[l];
             G.splat0 = (int32_t)(splat < 0x7fffffffLL ? splat : 0x7fffffffLL);
+            G.block0 = (int32_t)(blocks < 0x7fffffffLL ? blocks : 0x7fffffffLL);
             groups[ng++] = G;
             slot += c;
             splat += (long long)c * G.ng;
+            blocks += (long long)c * ((G.ng + 255) / 256);
             per_level[l] += c;
         }
         meta[kMetaVisible] = slot;
@@ -204,6 +206,7 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
         // splat count, saturated: the host rejects counts >= 2^31
         meta[kMetaSplats] = (int32_t)(splat < 0x7fffffffLL ? splat : 0x7fffffffLL);
         for (int l = 0; l < kMaxLevels; ++l) meta[kMetaLevel0 + l] = per_level[l];
+        meta[kMetaBlocks] = (int32_t)(blocks < 0x7fffffffLL ? blocks : 0x7fffffffLL);
     }
     __syncthreads();
     // stable placement: one warp per group sweeps the instances in order
@@ -310,29 +313,43 @@ __device__ __forceinline__ void sh_colour(const float4 *__restrict__ sh, int64_t
 
 constexpr int kProjThreads = 256;
 
-__global__ void __launch_bounds__(kProjThreads) k_project(
-    int n_splats, const Group *__restrict__ groups, int n_groups, const int32_t *__restrict__ vis,
+// One CTA per (visible instance, 256 Gaussians of its level): the CTA
+// stages the instance's 24 skinning transforms in shared memory; thread t
+// handles Gaussian chunk * 256 + t.  Splat ids are dense, grouped by
+// (template, level), instance-major within a group.
+__global__ void __launch_bounds__(kProjThreads, 4) k_project(
+    const Group *__restrict__ groups, int n_groups, const int32_t *__restrict__ vis,
     const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ Cloc,
     const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,
     CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
     uint32_t *__restrict__ key, uint32_t *__restrict__ ids, uint2 *__restrict__ rect,
     uint32_t *__restrict__ bin) {
-    __shared__ Group sg[kMaxTemplates * kMaxLevels];
-    for (int g = threadIdx.x; g < n_groups; g += blockDim.x) sg[g] = groups[g];
-    __syncthreads();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_splats) return;
-    // group of this splat: last group with splat0 <= s
-    int lo = 0, hi = n_groups - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (sg[mid].splat0 <= s) lo = mid; else hi = mid - 1;
+    __shared__ float4 sB[kJoints * 3];
+    __shared__ int s_group;
+    if (threadIdx.x == 0) {
+        // group whose CTA range holds this CTA: last group with block0 <= blockIdx.x
+        int lo = 0, hi = n_groups - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (groups[mid].block0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_group = lo;
     }
-    const Group G = sg[lo];
-    const int rel = s - G.splat0;
-    const int slot = G.slot0 + rel / G.ng;
-    const int gg = rel - (rel / G.ng) * G.ng;
-    const int inst = vis[slot];
+    __syncthreads();
+    const Group G = groups[s_group];
+    const int per_inst = (G.ng + kProjThreads - 1) / kProjThreads;
+    const int rb = (int)blockIdx.x - G.block0;
+    const int islot = rb / per_inst;
+    const int chunk = rb - islot * per_inst;
+    const int inst = vis[G.slot0 + islot];
+    {
+        const float4 *Bi = reinterpret_cast<const float4 *>(Bm + (size_t)inst * kJoints * 12);
+        for (int k = threadIdx.x; k < kJoints * 3; k += kProjThreads) sB[k] = __ldg(Bi + k);
+    }
+    __syncthreads();
+    const int gg = chunk * kProjThreads + threadIdx.x;
+    if (gg >= G.ng) return;
+    const int s = G.splat0 + islot * G.ng + gg;
     const TemplateInfo &T = tpls[G.tpl];
     const int gi = T.g_off + gg;
     ids[s] = (uint32_t)s;
@@ -340,7 +357,6 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     // LBS (CrowdSplat Sec. 2): M = sum_k w_k B_{idx_k} (instance local)
     const float4 w = __ldg(ta.skin_w + gi);
     const uint32_t packed = __ldg(ta.skin_i + gi);
-    const float4 *Bi = reinterpret_cast<const float4 *>(Bm + (size_t)inst * kJoints * 12);
     float M[12];
     {
         const float wk[4] = {w.x, w.y, w.z, w.w};
@@ -349,7 +365,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int j = (packed >> (8 * k)) & 0xFF;
-            const float4 b0 = __ldg(Bi + j * 3 + 0), b1 = __ldg(Bi + j * 3 + 1), b2 = __ldg(Bi + j * 3 + 2);
+            const float4 b0 = sB[j * 3 + 0], b1 = sB[j * 3 + 1], b2 = sB[j * 3 + 2];
             M[0] += wk[k] * b0.x; M[1] += wk[k] * b0.y; M[2] += wk[k] * b0.z; M[3] += wk[k] * b0.w;
             M[4] += wk[k] * b1.x; M[5] += wk[k] * b1.y; M[6] += wk[k] * b1.z; M[7] += wk[k] * b1.w;
             M[8] += wk[k] * b2.x; M[9] += wk[k] * b2.y; M[10] += wk[k] * b2.z; M[11] += wk[k] * b2.w;
@@ -498,14 +514,13 @@ __global__ void __launch_bounds__(kProjThreads) k_project(
     bin[s] = live ? bword : 0u;
 }
 
-int launch_project(int n_splats, const Group *groups, int n_groups, const int32_t *vis,
+int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_t *vis,
                     const float *B, const float *V, const float *Cloc, const float *root,
                     const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
                     const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
                     uint32_t *ids, uint2 *rect, uint32_t *bin, cudaStream_t st) {
-    if (n_splats <= 0) return 0;
-    int blocks = (n_splats + kProjThreads - 1) / kProjThreads;
-    k_project<<<blocks, kProjThreads, 0, st>>>(n_splats, groups, n_groups, vis, B, V, Cloc, root, ta,
+    if (n_blocks <= 0) return 0;
+    k_project<<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, vis, B, V, Cloc, root, ta,
                                                 tpls, cam, lod, skin_mode, sh_frame, rec, key, ids,
                                                 rect, bin);
     return 1;

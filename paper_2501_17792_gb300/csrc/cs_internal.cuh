@@ -68,6 +68,7 @@ struct Group {         // visible instances of one (template, level)
     int32_t nslots;
     int32_t ng;        // Gaussians per instance (template size at level)
     int32_t splat0;    // first splat id
+    int32_t block0;    // first projection CTA (each CTA: 256 Gaussians of one instance)
 };
 
 struct CamParams {
@@ -188,7 +189,9 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
 }
 
 // meta words written by the cull kernel and read back by the host
-enum MetaIndex { kMetaVisible = 0, kMetaGroups = 1, kMetaSplats = 2, kMetaLevel0 = 3, kMetaWords = 8 };
+enum MetaIndex {
+    kMetaVisible = 0, kMetaGroups = 1, kMetaSplats = 2, kMetaLevel0 = 3, kMetaBlocks = 7, kMetaWords = 12
+};
 
 // Every launch_* function returns the number of kernels it launched.
 // ---- geometry (cs_geometry.cu) ----
@@ -198,7 +201,7 @@ int launch_cull_group(int n_inst, int n_tpl, const int32_t *tid, const float *ro
                        const TemplateInfo *tpls, const CamParams &cam, const LodParams &lod,
                        int do_cull, float *V, float *Cloc, int32_t *vis, Group *groups,
                        int32_t *meta, cudaStream_t st);
-int launch_project(int n_splats, const Group *groups, int n_groups, const int32_t *vis,
+int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_t *vis,
                     const float *B, const float *V, const float *Cloc, const float *root,
                     const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
                     const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,

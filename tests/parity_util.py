@@ -50,7 +50,7 @@ def splat_ids(r):
     inst = np.full(S, -1, np.int64)
     gau = np.full(S, -1, np.int64)
     lvl = np.full(S, -1, np.int64)
-    for tpl, lv, slot0, nslots, ng, splat0 in groups:
+    for tpl, lv, slot0, nslots, ng, splat0, _block0 in groups:
         s = np.arange(int(nslots) * int(ng))
         inst[splat0 + s] = vis[slot0 + s // ng]
         gau[splat0 + s] = s % ng
