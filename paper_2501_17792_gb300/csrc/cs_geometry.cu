@@ -408,7 +408,9 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(
         const float S0 = ca.x * m2, S1 = ca.y * m2, S2 = ca.z * m2, S3 = ca.w * m2, S4 = cb.x * m2,
                     S5 = cb.y * m2;
         // EWA Jacobian at the mean, x/z and y/z clamped (3DGS)
-        const float iz = 1.0f / tz;
+        // hardware reciprocal and square root (relative error ~1e-7): far
+        // inside the boundary windows the parity tests derive
+        const float iz = __fdividef(1.0f, tz);
         const float txz = fminf(fmaxf(tx * iz, -cam.limx), cam.limx);
         const float tyz = fminf(fmaxf(ty * iz, -cam.limy), cam.limy);
         const float j00 = cam.fx * iz, j02 = -cam.fx * txz * iz;
@@ -429,11 +431,12 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(
         const float det = a * c - b * b;
         live = det > 0.0f;
         if (live) {
-            const float idet = 1.0f / det;
+            const float idet = __fdividef(1.0f, det);
             const float cA = c * idet, cB = -b * idet, cC = a * idet;
             const float mid = 0.5f * (a + c);
-            const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
-            const float r = ceilf(3.0f * sqrtf(lam));
+            const float disc = fmaxf(0.1f, mid * mid - det);
+            const float lam = mid + disc * rsqrtf(disc);
+            const float r = ceilf(3.0f * lam * rsqrtf(lam));
             const float u = cam.fx * tx * iz + cam.cx;
             const float v = cam.fy * ty * iz + cam.cy;
             // pixels with centre inside the support box, clipped to the image

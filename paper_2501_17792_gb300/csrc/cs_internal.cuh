@@ -155,7 +155,8 @@ __device__ __forceinline__ void box_range(float c, float r, int size, int &lo, i
 // of the ellipse f(d) <= fcut (reach = sqrt(fcut * Sigma2D_axis), widened by
 // 1e-4 relative + 0.01 px so FP32 rounding cannot cut a pixel off).
 __device__ __forceinline__ float ellipse_reach(float fcut, float sigma_axis) {
-    return __fadd_rn(__fmul_rn(sqrtf(__fmul_rn(fcut, sigma_axis)), 1.0001f), 0.01f);
+    const float x = fmaxf(__fmul_rn(fcut, sigma_axis), 1e-30f);
+    return __fadd_rn(__fmul_rn(x * rsqrtf(x), 1.0001f), 0.01f);
 }
 
 // Block-wide exclusive scan of one value per thread (blockDim a multiple of
