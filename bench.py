@@ -35,6 +35,17 @@ WORKLOAD = "crowd_14x65536g_sh3_3500inst_1920x1080_lod3_animated"
 PAPER_FPS = 31.0  # RTX4090, resolution not stated: context only, not this workload
 
 
+def aggregate(ms_local: float, steps: int, world: int, dist=None, device=None):
+    """Max of the per-rank timed milliseconds over ranks and the whole-job
+    throughput: all ranks' steps divided by the slowest rank's time."""
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max / 1e3)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -240,13 +251,10 @@ def run_ours(args, sc, rank, world, local_rank):
     ms_total = e0.elapsed_time(e1)
     stage_ms, stage_frames = r.stage_times(average=True)
     clocks = clk.stop() if clk else None
-    t_local = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    ms_max, value = aggregate(ms_total, args.steps, world, dist, dev)
     if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
         dist.barrier()
-    ms_max = float(t_local.item())
     ms_per_step = ms_max / args.steps
-    value = world * args.steps / (ms_max / 1e3)
 
     # end to end through the C ABI with host buffers: pinned poses in, image out
     h_pose = torch.empty((n, 24, 3), dtype=torch.float32).pin_memory()
@@ -272,10 +280,7 @@ def run_ours(args, sc, rank, world, local_rank):
     t0 = time.perf_counter()
     for f in range(args.e2e_steps):
         e2e_step(f + 2)
-    t_e2e = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.e2e_steps / float(t_e2e.item())
+    _, e2e_value = aggregate((time.perf_counter() - t0) * 1e3, args.e2e_steps, world, dist, dev)
     h2d = n * (4 + 48 + 24 * 3 * 4)
     d2h = sc.camera.width * sc.camera.height * 16
 
