@@ -332,6 +332,78 @@ def run_ours(args, sc, rank, world, local_rank):
     r.close()
 
 
+# ---------------------------------------------------------------------------
+# CrowdSplat Table 1 / Table 2 sweep (1280x720, one template size per row)
+# ---------------------------------------------------------------------------
+
+PAPER_TABLE2 = {  # Table 2 FPS on RTX4090, (w/o motion, w/ motion); context only
+    202738: {1: (728, 617), 100: (50, 18.2), 400: (22.2, None)},
+    12661: {1: (1612, 1370), 100: (586, 312), 400: (251, 76), 1000: (125, 34), 5000: (10.3, 6.1)},
+    3176: {1: (1703, 1347), 100: (1240, 804), 400: (673, 298), 1000: (275, 121), 5000: (38.6, 23.2)},
+}
+PAPER_TABLE1 = {  # Table 1 GPU memory MiB on RTX4090, (plain, shared); context only
+    202738: {1: (651, 651), 100: (7929, 7075)},
+    12661: {1: (567, 567), 100: (1005, 953), 400: (2335, 2121), 1000: (5127, 4593), 5000: (21340, 19625)},
+    3176: {1: (557, 557), 100: (675, 639), 400: (993, 937), 1000: (1695, 1541), 5000: (5995, 5329)},
+}
+
+
+def run_sweep(args):
+    """FPS without motion (same poses every frame) and with motion (new poses
+    every frame), and device memory, for one template of each paper size
+    duplicated to the paper's character counts on a 1.2 m grid starting 3 m
+    from the camera, 1280x720, full detail (the paper's rows use a single
+    template size).  Memory: the library always shares template attributes;
+    the unshared figure adds a template copy per extra character."""
+    import torch
+    from paper_2501_17792_gb300 import binding, build
+    from paper_2501_17792_gb300 import scene as S
+    build.build()
+    cam = S.look_camera((0.0, 1.6, 0.0), 10.0, 1280, 720)
+    rows_out = []
+    for n_gauss, cells in PAPER_TABLE2.items():
+        tpl = S.make_template(1000, n_gauss, 3)
+        tbytes = template_bytes(S.Scene([tpl], None, cam, S.single_lod(), ""))
+        for count in cells:
+            cols = min(50, int(math.ceil(math.sqrt(count))))
+            nrows = int(math.ceil(count / cols))
+            inst = S.crowd_instances(1, cols, nrows)
+            tid, root = inst.template_id[:count], inst.root[:count]
+            r = binding.Renderer(device=0)
+            r.upload_templates([tpl])
+            out = torch.empty((720, 1280, 4), dtype=torch.float32, device="cuda")
+            fps = {}
+            for motion in (False, True):
+                poses = [torch.from_numpy(S.random_poses(100 + (f if motion else 0), count)).cuda()
+                         for f in range(args.steps + args.warmup)]
+                dtid = torch.from_numpy(tid).cuda()
+                droot = torch.from_numpy(root.reshape(count, 12)).cuda()
+                for f in range(args.warmup):
+                    r.set_instances(dtid, droot, poses[f])
+                    r.render(cam, out=out)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for f in range(args.warmup, args.warmup + args.steps):
+                    r.set_instances(dtid, droot, poses[f])
+                    r.render(cam, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                fps["motion" if motion else "static"] = args.steps / (e0.elapsed_time(e1) / 1e3)
+            _, st = r.render(cam, out=out, stats=True)
+            mem = r.memory_stats()
+            r.close()
+            shared_mib = (mem["total_bytes"] + out.numel() * 4) / 2 ** 20
+            row = dict(gaussians=n_gauss, characters=count, fps_static=round(fps["static"], 1),
+                       fps_motion=round(fps["motion"], 1), splats=st["splats"], pairs=st["pairs"],
+                       mem_shared_mib=round(shared_mib, 1),
+                       mem_unshared_mib=round(shared_mib + (count - 1) * tbytes / 2 ** 20, 1),
+                       paper_fps=PAPER_TABLE2[n_gauss].get(count), paper_mib=PAPER_TABLE1[n_gauss].get(count))
+            rows_out.append(row)
+            print(json.dumps(row), flush=True)
+    return rows_out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,10 +414,15 @@ def main():
     ap.add_argument("--oracle-stride", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small crowd (debugging)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="paper Table 1/2 sweep at 1280x720 (one JSON line per cell)")
     ap.add_argument("--profile-case", action="store_true",
                     help="quarter crowd (875 instances, 960x540) for full ncu captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.sweep:
+        run_sweep(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
