@@ -55,7 +55,10 @@ class _Scene(C.Structure):
                 ("n_instances", C.c_int32), ("template_id", C.c_void_p), ("root", C.c_void_p),
                 ("pose", C.c_void_p), ("n_levels", C.c_int32), ("thresholds", C.c_void_p),
                 ("fractions", C.c_void_p), ("scale_mult", C.c_void_p),
-                ("skin_mode", C.c_int32), ("sh_frame", C.c_int32), ("cam", _Camera)]
+                ("skin_mode", C.c_int32), ("sh_frame", C.c_int32), ("cam", _Camera),
+                ("sub_n", C.c_void_p), ("sub_off", C.c_void_p), ("sub_idx", C.c_void_p)]
+
+MAX_LEVELS = 4  # LoD levels of the subset table
 
 
 class _Eps(C.Structure):
@@ -77,9 +80,11 @@ def lib():
         L.orc_instance_level.restype = C.c_int
         L.orc_level_count.argtypes = [C.POINTER(_Scene), C.c_int, C.c_int]
         L.orc_level_count.restype = C.c_int
+        L.orc_level_size.argtypes = [C.POINTER(_Scene), C.c_int, C.c_int]
+        L.orc_level_size.restype = C.c_int
         L.orc_project_instance.argtypes = [C.POINTER(_Scene), C.c_int] + [P] * 13
         L.orc_project_instance.restype = C.c_int
-        L.orc_render_lattice.argtypes = [C.POINTER(_Scene), C.POINTER(_Eps)] + [C.c_int] * 6 + [P] * 5
+        L.orc_render_lattice.argtypes = [C.POINTER(_Scene), C.POINTER(_Eps)] + [C.c_int] * 6 + [P] * 6
         L.orc_render_lattice.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
         _lib = L
@@ -96,9 +101,13 @@ def _c(a, dtype):
 
 class OracleScene:
     """Marshals a scene (templates, instances, camera, lod) into the C
-    structures.  Keeps references to every array it hands to C."""
+    structures.  Keeps references to every array it hands to C.
 
-    def __init__(self, scene, *, skin_mode: int = 0, sh_frame: int = 0):
+    ``subsets`` (optional): {(template, level): template-local Gaussian
+    indices} -- the level renders exactly those Gaussians, in that order,
+    instead of its prefix."""
+
+    def __init__(self, scene, *, skin_mode: int = 0, sh_frame: int = 0, subsets=None):
         keep = []
         tpls = (_Template * len(scene.templates))()
         for k, t in enumerate(scene.templates):
@@ -146,6 +155,24 @@ class OracleScene:
         s.skin_mode = int(skin_mode)
         s.sh_frame = int(sh_frame)
         s.cam = c
+        nt = len(scene.templates)
+        self.sub_n = np.full(nt * MAX_LEVELS, -1, np.int32)
+        self.sub_off = np.zeros(nt * MAX_LEVELS, np.int64)
+        idx_parts, off = [], 0
+        for (t, l), idx in sorted((subsets or {}).items()):
+            a = np.asarray(idx, np.int64)
+            if not (0 <= t < nt and 0 <= l < MAX_LEVELS):
+                raise ValueError(f"subset key {(t, l)} out of range")
+            if a.size and (a.min() < 0 or a.max() >= _template_size(scene, t) or np.unique(a).size != a.size):
+                raise ValueError(f"subset {(t, l)}: indices must be distinct and in range")
+            self.sub_n[t * MAX_LEVELS + l] = a.size
+            self.sub_off[t * MAX_LEVELS + l] = off
+            idx_parts.append(a.astype(np.int32))
+            off += a.size
+        self.sub_idx = np.ascontiguousarray(np.concatenate(idx_parts) if idx_parts else np.zeros(1, np.int32))
+        s.sub_n = self.sub_n.ctypes.data
+        s.sub_off = self.sub_off.ctypes.data
+        s.sub_idx = self.sub_idx.ctypes.data
         self._keep = (keep, tpls)
         self.s = s
         self.n_gauss = [int(t.means.shape[0]) for t in scene.templates]
@@ -154,6 +181,10 @@ class OracleScene:
     @property
     def ref(self):
         return C.byref(self.s)
+
+
+def _template_size(scene, t: int) -> int:
+    return int(np.asarray(scene.templates[t].means).shape[0])
 
 
 def default_eps(**kw) -> _Eps:
@@ -218,9 +249,14 @@ def level_count(os_: OracleScene, lvl: int, n: int) -> int:
     return int(lib().orc_level_count(os_.ref, lvl, n))
 
 
+def level_size(os_: OracleScene, template: int, lvl: int) -> int:
+    """Gaussians that level `lvl` of the template renders (subset or prefix)."""
+    return int(lib().orc_level_size(os_.ref, template, lvl))
+
+
 def project_instance(os_: OracleScene, inst: int) -> dict:
-    """Per-Gaussian results of one instance over its LoD prefix (template
-    order): valid, radius, uv, conic, depth, rgb, opacity, mu, cov3, cov2,
+    """Per-Gaussian results of one instance over its LoD level (prefix in
+    template order, or the chosen subset in its order): valid, radius, uv, conic, depth, rgb, opacity, mu, cov3, cov2,
     r_exact, plus level and the skinning transforms B."""
     tp_index = int(os_.template_id[inst])
     n_max = os_.n_gauss[tp_index]
@@ -240,9 +276,11 @@ def project_instance(os_: OracleScene, inst: int) -> dict:
     return res
 
 
-def render(os_: OracleScene, eps: _Eps | None = None, lattice=None) -> dict:
+def render(os_: OracleScene, eps: _Eps | None = None, lattice=None, contrib: bool = False) -> dict:
     """Composite the lattice of pixels (ox, oy, sx, sy, nx, ny); default is
-    the full image.  Returns rgba [ny,nx,4], wsum, flags, impact, ncontrib."""
+    the full image.  Returns rgba [ny,nx,4], wsum, flags, impact, ncontrib,
+    and with ``contrib`` the per-Gaussian sum of compositing weights
+    alpha * T over the lattice (templates concatenated)."""
     if lattice is None:
         lattice = (0, 0, 1, 1, os_.width, os_.height)
     ox, oy, sx, sy, nx, ny = (int(x) for x in lattice)
@@ -252,11 +290,16 @@ def render(os_: OracleScene, eps: _Eps | None = None, lattice=None) -> dict:
     impact = np.zeros((ny, nx))
     nc = np.zeros((ny, nx), np.int32)
     e = eps if eps is not None else default_eps()
+    cb = np.zeros(sum(os_.n_gauss)) if contrib else None
     rc = lib().orc_render_lattice(os_.ref, C.byref(e), ox, oy, sx, sy, nx, ny, _p(rgba),
-                                  _p(wsum), _p(flags), _p(impact), _p(nc))
+                                  _p(wsum), _p(flags), _p(impact), _p(nc),
+                                  _p(cb) if cb is not None else None)
     if rc != 0:
         raise MemoryError("oracle render failed to allocate")
-    return dict(rgba=rgba, wsum=wsum, flags=flags, impact=impact, ncontrib=nc)
+    out = dict(rgba=rgba, wsum=wsum, flags=flags, impact=impact, ncontrib=nc)
+    if cb is not None:
+        out["contrib"] = cb
+    return out
 
 
 def tile_lists(os_: OracleScene, tile: int = 16) -> dict:

@@ -36,6 +36,7 @@
 #endif
 
 #define ORC_NJ 24
+#define ORC_MAXL 4 /* LoD levels a subset table covers per template */
 
 typedef struct {
     int32_t n, sh_degree;
@@ -72,6 +73,13 @@ typedef struct {
     int32_t skin_mode;          /* 0: LBS of means and covariances; 1: means only */
     int32_t sh_frame;           /* 0: view direction in the instance root frame; 1: world */
     orc_camera cam;
+    /* optional chosen Gaussian subsets per (template t, level l), index
+     * t * ORC_MAXL + l: sub_n < 0 keeps the level's prefix, otherwise the
+     * level renders sub_idx[sub_off .. sub_off + sub_n) (template-local
+     * indices, in that order).  sub_n may be NULL (no subsets). */
+    const int32_t *sub_n;
+    const int64_t *sub_off;
+    const int32_t *sub_idx;
 } orc_scene;
 
 /* Windows of the boundary events (see orc_render_lattice). */
@@ -224,6 +232,19 @@ int orc_level_count(const orc_scene *s, int lvl, int n) {
     if (c < 0.0) c = 0.0;
     if (c > n) c = n;
     return (int)c;
+}
+
+/* Size of level `lvl` of template t: its chosen subset's length, else the
+ * prefix of orc_level_count. */
+int orc_level_size(const orc_scene *s, int t, int lvl) {
+    if (s->sub_n && s->sub_n[t * ORC_MAXL + lvl] >= 0) return s->sub_n[t * ORC_MAXL + lvl];
+    return orc_level_count(s, lvl, s->templates[t].n);
+}
+
+/* Template-local index of the k-th Gaussian of level `lvl` of template t. */
+int orc_level_gauss(const orc_scene *s, int t, int lvl, int k) {
+    if (s->sub_n && s->sub_n[t * ORC_MAXL + lvl] >= 0) return s->sub_idx[s->sub_off[t * ORC_MAXL + lvl] + k];
+    return k;
 }
 
 /* ------------------------------------------------------------------ */
@@ -450,8 +471,9 @@ void orc_splat_compute(const orc_scene *s, int inst, const double *B, int lvl, i
 }
 
 /* Per-instance splats for parity checks: all Gaussians of the instance's
- * LoD prefix, in template order.  Arrays have `count` rows (count = level
- * size, returned).  Any output pointer may be NULL. */
+ * LoD level, in level order (the prefix, or the chosen subset's order).
+ * Arrays have `count` rows (count = level size, returned).  Any output
+ * pointer may be NULL. */
 int orc_project_instance(const orc_scene *s, int inst, int32_t *level_out,
                          int32_t *valid, int32_t *radius, double *uv /*[n*2]*/,
                          double *conic /*[n*3]*/, double *depth, double *rgb /*[n*3]*/,
@@ -463,11 +485,12 @@ int orc_project_instance(const orc_scene *s, int inst, int32_t *level_out,
     if (B_out) memcpy(B_out, B, sizeof B);
     int lvl = orc_instance_level(s, inst, NULL, NULL);
     if (level_out) *level_out = lvl;
-    int n = orc_level_count(s, lvl, tp->n);
+    const int t = s->template_id[inst];
+    int n = orc_level_size(s, t, lvl);
     #pragma omp parallel for schedule(static)
     for (int g = 0; g < n; ++g) {
         orc_splat sp;
-        orc_splat_compute(s, inst, B, lvl, g, &sp);
+        orc_splat_compute(s, inst, B, lvl, orc_level_gauss(s, t, lvl, g), &sp);
         if (valid) valid[g] = sp.valid;
         if (radius) radius[g] = sp.r;
         if (uv) { uv[g * 2] = sp.u; uv[g * 2 + 1] = sp.v; }
@@ -489,7 +512,8 @@ int orc_project_instance(const orc_scene *s, int inst, int32_t *level_out,
 
 typedef struct {
     int32_t pix;      /* lattice index                          */
-    int32_t inst, g;
+    int32_t inst, g;  /* g: position in the instance's level     */
+    int64_t gt;       /* Gaussian's index over all templates     */
     int32_t r;
     int32_t near_ev;  /* view depth close to the near plane      */
     int32_t rad_ev;   /* radius close to an integer              */
@@ -533,7 +557,10 @@ static double dmax(double a, double b) { return a > b ? a : b; }
  *   alpha = min(0.99, o e^q);  skip alpha < 1/255;
  *   T' = T (1 - alpha);  stop (without this splat) if T' < 1e-4;
  *   C += c alpha T;  T = T'.
- * Outputs RGB = C (black background), A = 1 - T, wsum = sum alpha T.
+ * Outputs RGB = C (black background), A = 1 - T, wsum = sum alpha T, and
+ * (optional) contrib[gt] += alpha T for each composited Gaussian, gt its
+ * index over all templates (template t's Gaussians follow those of
+ * templates 0 .. t-1).
  *
  * Boundary events: where an FP32 evaluation of the same definition may take
  * the other branch of a discontinuous decision, the pixel is flagged if
@@ -548,14 +575,16 @@ static double dmax(double a, double b) { return a > b ? a : b; }
 int orc_render_lattice(const orc_scene *s, const orc_eps *eps, int ox, int oy, int sx, int sy,
                        int nx, int ny, double *rgba /*[ny*nx*4]*/, double *wsum /*[ny*nx]*/,
                        uint32_t *flags /*[ny*nx]*/, double *impact /*[ny*nx]*/,
-                       int32_t *ncontrib /*[ny*nx]*/) {
+                       int32_t *ncontrib /*[ny*nx]*/, double *contrib /*[total Gaussians] or NULL*/) {
     int nthreads = 1;
 #ifdef _OPENMP
     nthreads = omp_get_max_threads();
 #endif
     orc_vec *vecs = (orc_vec *)calloc((size_t)nthreads, sizeof(orc_vec));
     uint8_t *lod_ev = (uint8_t *)calloc((size_t)(s->n_instances > 0 ? s->n_instances : 1), 1);
-    if (!vecs || !lod_ev) return -1;
+    int64_t *g_off = (int64_t *)calloc((size_t)s->n_templates + 1, sizeof(int64_t));
+    if (!vecs || !lod_ev || !g_off) return -1;
+    for (int t = 0; t < s->n_templates; ++t) g_off[t + 1] = g_off[t] + s->templates[t].n;
     const double margin_px = eps->px;
 
     #pragma omp parallel
@@ -573,10 +602,12 @@ int orc_render_lattice(const orc_scene *s, const orc_eps *eps, int ox, int oy, i
             double nt;
             int lvl = orc_instance_level(s, inst, NULL, &nt);
             if (nt < 1e-4) lod_ev[inst] = 1;
-            int n = orc_level_count(s, lvl, tp->n);
+            const int t = s->template_id[inst];
+            int n = orc_level_size(s, t, lvl);
             for (int g = 0; g < n; ++g) {
                 orc_splat sp;
-                orc_splat_compute(s, inst, B, lvl, g, &sp);
+                const int gl = orc_level_gauss(s, t, lvl, g);
+                orc_splat_compute(s, inst, B, lvl, gl, &sp);
                 int near_ev = fabs(sp.depth - s->cam.near_z) < eps->near_z;
                 /* keep contributors, and near-plane culls close to the plane */
                 if (!sp.on_image || (!sp.valid && !near_ev)) continue;
@@ -597,6 +628,7 @@ int orc_render_lattice(const orc_scene *s, const orc_eps *eps, int ox, int oy, i
                         e.pix = j * nx + i;
                         e.inst = inst;
                         e.g = g;
+                        e.gt = g_off[t] + gl;
                         e.r = sp.r;
                         e.near_ev = near_ev;
                         e.rad_ev = rad_ev;
@@ -695,6 +727,10 @@ int orc_render_lattice(const orc_scene *s, const orc_eps *eps, int ox, int oy, i
             if (Tn < 1e-4) break;
             for (int ch = 0; ch < 3; ++ch) C[ch] += e->rgb[ch] * alpha * T;
             ws += alpha * T;
+            if (contrib) {
+                #pragma omp atomic
+                contrib[e->gt] += alpha * T;
+            }
             have_prev = 1;
             prev_depth = e->depth;
             prev_alpha = alpha;
@@ -715,6 +751,7 @@ int orc_render_lattice(const orc_scene *s, const orc_eps *eps, int ox, int oy, i
     free(all);
     free(start);
     free(lod_ev);
+    free(g_off);
     return 0;
 }
 

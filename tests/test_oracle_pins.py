@@ -674,3 +674,99 @@ def test_tile_lists_agree_with_per_pixel_membership():
         assert set(keys.tolist()) == members[t]
         d = [depth[k] for k in keys.tolist()]
         assert all(d[k] <= d[k + 1] for k in range(len(d) - 1))
+
+
+# ---------------------------------------------------------------------------
+# chosen LoD subsets and per-Gaussian contribution sums
+# ---------------------------------------------------------------------------
+
+def _paper_lod(mults=(1.0, 2.0, 4.0)):
+    return S.LodConfig(thresholds=np.array([10.0, 30.0], np.float32),
+                       fractions=np.array([1.0, 0.25, 0.06], np.float32),
+                       scale_mult=np.array(mults, np.float32))
+
+
+def test_lod_subset_equals_template_of_those_gaussians():
+    """A level restricted to a chosen subset renders exactly like a template
+    made of those Gaussians (in the subset's order) with the level's scale
+    multiplier applied."""
+    base = S.make_template(4321, 512, 1)
+    cam = S.look_camera((0.0, 1.0, 0.0), 0.0, 96, 96, vfov_deg=8.0)
+    root = S.yaw_root(0.7, 0.0, 0.0, 15.0).astype(np.float32)       # band 1 (10..30 m)
+    pose = np.random.default_rng(8).normal(0, 0.3, (1, 24, 3)).astype(np.float32)
+    idx = np.random.default_rng(9).permutation(512)[:90]
+    sc = U.scene_of([base], U.instances(1, root[None], pose), cam, _paper_lod())
+    os_ = oracle.OracleScene(sc, subsets={(0, 1): idx})
+    assert oracle.level_size(os_, 0, 1) == 90
+    assert oracle.level_size(os_, 0, 2) == round(0.06 * 512)
+    img = oracle.render(os_)["rgba"]
+    t2 = S.Template(means=base.means[idx], scales=base.scales[idx] * np.float32(2.0),
+                    quats=base.quats[idx], opacity=base.opacity[idx], sh=base.sh[idx],
+                    skin_idx=base.skin_idx[idx], skin_w=base.skin_w[idx],
+                    rest_joints=base.rest_joints, parents=base.parents, sh_degree=1)
+    img2 = oracle.render(oracle.OracleScene(U.scene_of([t2], U.instances(1, root[None], pose), cam)))["rgba"]
+    assert img[..., 3].max() > 0.3
+    assert np.abs(img - img2).max() < 1e-14
+    p = oracle.project_instance(os_, 0)
+    assert p["count"] == 90 and p["level"] == 1
+    # a subset equal to the prefix changes nothing
+    n1 = round(0.25 * 512)
+    os3 = oracle.OracleScene(sc, subsets={(0, 1): np.arange(n1)})
+    img3 = oracle.render(os3)["rgba"]
+    img4 = oracle.render(oracle.OracleScene(sc))["rgba"]
+    assert np.abs(img3 - img4).max() == 0.0
+
+
+def test_contributions_sum_to_the_alpha_channel():
+    """sum over Gaussians of sum over pixels of alpha T = sum over pixels of
+    (1 - final T); every contribution is non-negative."""
+    sc = U.random_small_scene(21, n_gauss=150, n_inst=4, size=40, sh_degree=1)
+    r = oracle.render(oracle.OracleScene(sc), contrib=True)
+    c = r["contrib"]
+    assert c.shape == (150,)
+    assert c.min() >= 0.0 and (c > 0).sum() > 50
+    assert abs(c.sum() - r["rgba"][..., 3].sum()) < 1e-9 * max(1.0, c.sum())
+
+
+def test_contribution_closed_form_for_two_layers():
+    """Front splat f, back splat b: contrib_f = sum A_f, contrib_b =
+    sum A_b (1 - A_f), with A_x the alpha channel of x rendered alone (no
+    pixel reaches the stop rule or the 0.99 clamp here)."""
+    means = [[0.0, 0.0, 2.0], [0.01, -0.01, 2.6]]
+    scales = [[0.03, 0.02, 0.02], [0.04, 0.03, 0.03]]
+    quats = [[1, 0, 0, 0], [0.9, 0.1, 0.2, 0.1]]
+    op = [0.6, 0.7]
+    sh = np.full((2, 1, 3), 0.2, np.float32)
+    cam = U.identity_camera(48, 48, f=60.0)
+
+    def scene(sel):
+        t = U.template_from(np.asarray(means)[sel], np.asarray(scales)[sel], np.asarray(quats)[sel],
+                            np.asarray(op)[sel], sh[sel])
+        return U.scene_of([t], U.instances(1), cam)
+
+    both = oracle.render(oracle.OracleScene(scene([0, 1])), contrib=True)
+    Af = oracle.render(oracle.OracleScene(scene([0])))["rgba"][..., 3]
+    Ab = oracle.render(oracle.OracleScene(scene([1])))["rgba"][..., 3]
+    assert Af.max() < 0.99 and Ab.max() < 0.99
+    assert abs(both["contrib"][0] - Af.sum()) < 1e-12 * Af.sum()
+    assert abs(both["contrib"][1] - (Ab * (1 - Af)).sum()) < 1e-12 * Ab.sum()
+    assert both["contrib"][1] < Ab.sum() * 0.9          # the front layer hides part of the back one
+
+
+def test_contribution_lands_on_the_template_gaussian():
+    """Two templates; level 0 of template 1 restricted to one Gaussian k:
+    only entry n0 + k of the concatenated array receives weight."""
+    ta = S.make_template(51, 40, 0)
+    tb = S.make_template(52, 30, 0)
+    cam = S.look_camera((0.0, 1.0, 0.0), 0.0, 64, 64, vfov_deg=40.0)
+    roots = np.stack([S.yaw_root(0.0, 0.0, 0.0, 3.0), S.yaw_root(0.5, 0.0, 0.0, 3.0)]).astype(np.float32)
+    inst = U.instances(2, roots, np.zeros((2, 24, 3), np.float32), template_id=[0, 1])
+    sc = U.scene_of([ta, tb], inst, cam)
+    k = 17
+    os_ = oracle.OracleScene(sc, subsets={(0, 0): [], (1, 0): [k]})
+    r = oracle.render(os_, contrib=True)
+    c = r["contrib"]
+    assert c.shape == (70,)
+    nz = np.nonzero(c)[0]
+    assert list(nz) == [40 + k]
+    assert abs(c[40 + k] - r["rgba"][..., 3].sum()) < 1e-12
