@@ -152,6 +152,20 @@ int cs_upload_templates(cs_ctx *ctx, int32_t n_templates, const cs_template_desc
 int cs_set_lod(cs_ctx *ctx, int32_t n_levels, const float *dist_thresh, const float *fraction,
                const float *scale_mult);
 
+/* Choose the Gaussians that LoD level `level` of template `template_id`
+ * renders (CrowdSplat Sec. 2 varies the number of Gaussians per distance
+ * band; the paper fits a separate template per band, this call lets a
+ * ranking pick the band's Gaussians from the full template instead).
+ * idx[n]: HOST array of distinct template-local Gaussian indices, any
+ * order (the order is the splat order inside the level and so breaks depth
+ * ties).  The subset replaces the level's prefix of round(fraction * N)
+ * Gaussians; the level's scale multiplier still applies.  n = 0 clears the
+ * subset (back to the prefix).  Subsets are kept across cs_set_lod and
+ * cleared by cs_upload_templates.  Errors: CS_ERR_ARG (template or level
+ * out of range, n > N, an index >= N or repeated), CS_ERR_STATE (no
+ * templates), CS_ERR_CUDA, CS_ERR_OOM. */
+int cs_set_lod_subset(cs_ctx *ctx, int32_t template_id, int32_t level, int32_t n, const uint32_t *idx);
+
 /* Per-frame instance state (CrowdSplat Sec. 2, stage 2: duplicated
  * characters, each with its template and pose).  template_id[n];
  * root[n*12] row-major 3x4 rigid [R|t] from template-local to world
@@ -173,6 +187,20 @@ int cs_set_instances(cs_ctx *ctx, int32_t n, const int32_t *template_id, const f
  * focal length or near plane, NULL or not 16-byte aligned output), CS_ERR_STATE (no templates or
  * instances), CS_ERR_OOM, CS_ERR_CUDA. */
 int cs_render(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats);
+
+/* cs_render that also measures how much each template Gaussian contributes
+ * to the image: contrib_out[g] (DEVICE float32 array of the total Gaussian
+ * count over all templates, template t's Gaussians at its upload offset) is
+ * ADDED the sum, over every pixel and every instance that rendered g, of g's
+ * compositing weight alpha * T (T = transmittance in front of it).  Summed
+ * over all Gaussians this equals the sum of the frame's alpha channel.
+ * Tile lists are composited in one pass (no split of long lists), so the
+ * frame is slower than cs_render's; the image is the same up to float
+ * rounding order.  Used to build ranked LoD subsets (cs_set_lod_subset);
+ * the paper has no counterpart.  Same arguments and errors as cs_render,
+ * plus CS_ERR_ARG for a NULL or misaligned contrib_out. */
+int cs_render_contrib(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, float *contrib_out,
+                      cs_frame_stats *stats);
 
 /* cs_render into an internal device buffer followed by a device->host copy
  * of the image into rgba_host (HOST memory, pinned for full speed); returns

@@ -70,8 +70,10 @@ SIGNATURES = {
     "cs_destroy": (None, [_P]),
     "cs_upload_templates": (C.c_int, [_P, C.c_int32, C.POINTER(TemplateDesc)]),
     "cs_set_lod": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "cs_set_lod_subset": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P]),
     "cs_set_instances": (C.c_int, [_P, C.c_int32, _P, _P, _P, C.c_int32]),
     "cs_render": (C.c_int, [_P, C.POINTER(Camera), _P, C.POINTER(FrameStats)]),
+    "cs_render_contrib": (C.c_int, [_P, C.POINTER(Camera), _P, _P, C.POINTER(FrameStats)]),
     "cs_render_to_host": (C.c_int, [_P, C.POINTER(Camera), _P, C.POINTER(FrameStats)]),
     "cs_render_static": (C.c_int, [_P, C.POINTER(Camera), _P, C.POINTER(FrameStats)]),
     "cs_get_stage_times": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]),
@@ -197,6 +199,13 @@ class Renderer:
         self._check(self.L.cs_set_lod(self.h, n, thr.ctypes.data if thr.size else None,
                                       frac.ctypes.data, mult.ctypes.data))
 
+    def set_lod_subset(self, template_id: int, level: int, idx):
+        """Gaussians (template-local indices) that `level` of the template
+        renders; an empty array restores the level's prefix."""
+        a = _host(np.asarray(idx), np.uint32)
+        self._check(self.L.cs_set_lod_subset(self.h, int(template_id), int(level), int(a.shape[0]),
+                                             a.ctypes.data if a.size else None))
+
     def set_instances(self, template_id, root, pose):
         """Host arrays (numpy, or CPU tensors) or CUDA tensors on this device."""
         torch = self.torch
@@ -225,6 +234,23 @@ class Renderer:
                                   device=f"cuda:{self.device}")
         st = FrameStats()
         self._check(self.L.cs_render(self.h, C.byref(cam), out.data_ptr(), C.byref(st) if stats else None))
+        return (out, st.as_dict()) if stats else out
+
+    def render_contrib(self, camera, contrib, out=None, stats: bool = False):
+        """Render and ADD each template Gaussian's summed compositing weight
+        to `contrib` (CUDA float32 tensor, one entry per uploaded Gaussian,
+        templates concatenated in upload order)."""
+        torch = self.torch
+        cam = camera_struct(camera)
+        if out is None:
+            with torch.cuda.stream(self.stream):
+                out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32,
+                                  device=f"cuda:{self.device}")
+        if not (contrib.is_cuda and contrib.dtype == torch.float32 and contrib.is_contiguous()):
+            raise ValueError("contrib must be a contiguous float32 CUDA tensor")
+        st = FrameStats()
+        self._check(self.L.cs_render_contrib(self.h, C.byref(cam), out.data_ptr(), contrib.data_ptr(),
+                                             C.byref(st) if stats else None))
         return (out, st.as_dict()) if stats else out
 
     def render_to_host(self, camera, out: np.ndarray | None = None, stats: bool = False):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -39,6 +40,11 @@ struct cs_ctx {
     int n_tpl = 0;
     std::vector<TemplateInfo> tpl_host;
     std::vector<std::vector<float>> reach_g, smax_g;  // per Gaussian, for LoD bounds
+    // chosen Gaussian subsets per (template, level); empty: the level renders a prefix
+    std::vector<std::array<std::vector<uint32_t>, kMaxLevels>> lod_sub;
+    std::vector<uint32_t> lod_idx_host;  // all subsets, concatenated
+    uint32_t *d_lod_idx = nullptr;
+    size_t lod_idx_cap = 0;
     TemplateInfo *d_tpl = nullptr;
     float4 *d_mean_op = nullptr, *d_cov_a = nullptr, *d_skin_w = nullptr, *d_sh = nullptr;
     float2 *d_cov_b = nullptr;
@@ -65,6 +71,7 @@ struct cs_ctx {
     DevBuf<uint2> rect, ranges;
     DevBuf<uint16_t> ptile, ptile2;
     DevBuf<float4> img;  // for cs_render_to_host
+    DevBuf<float> contrib_s;  // per-splat compositing weight sums (cs_render_contrib)
     // split compositing of long tile lists
     DevBuf<int32_t> bw_slot, bw_tile, bw_meta, bw_stop;
     DevBuf<uint32_t> bw_chunk0, bw_done;
@@ -157,6 +164,11 @@ void free_templates(cs_ctx *c) {
     cudaFree(c->d_skin_w);
     cudaFree(c->d_skin_i);
     cudaFree(c->d_sh);
+    cudaFree(c->d_lod_idx);
+    c->d_lod_idx = nullptr;
+    c->lod_idx_cap = 0;
+    c->lod_sub.clear();
+    c->lod_idx_host.clear();
     c->d_tpl = nullptr;
     c->d_mean_op = c->d_cov_a = c->d_skin_w = c->d_sh = nullptr;
     c->d_cov_b = nullptr;
@@ -165,17 +177,30 @@ void free_templates(cs_ctx *c) {
     c->n_gauss_total = c->sh_planes_total = 0;
 }
 
-// Level sizes and instance-cull bounds of every template for the current LoD.
+// Level sizes, subset offsets and instance-cull bounds of every template for
+// the current LoD.  A level with a chosen subset renders exactly that subset;
+// otherwise it renders the first round(fraction * n) Gaussians.
 void refresh_lod_bounds(cs_ctx *c) {
+    c->lod_idx_host.clear();
     for (int t = 0; t < c->n_tpl; ++t) {
         TemplateInfo &T = c->tpl_host[t];
         for (int l = 0; l < kMaxLevels; ++l) {
             int lvl = l < c->lod.n_levels ? l : c->lod.n_levels - 1;
-            double cnt = std::floor((double)c->lod_frac[lvl] * (double)T.n + 0.5);
-            int n = (int)std::min<double>(std::max<double>(cnt, 0.0), (double)T.n);
+            const std::vector<uint32_t> &sub = c->lod_sub[t][lvl];
+            int n;
+            if (!sub.empty()) {
+                n = (int)sub.size();
+                T.lod_idx_off[l] = (int32_t)c->lod_idx_host.size();
+                c->lod_idx_host.insert(c->lod_idx_host.end(), sub.begin(), sub.end());
+            } else {
+                double cnt = std::floor((double)c->lod_frac[lvl] * (double)T.n + 0.5);
+                n = (int)std::min<double>(std::max<double>(cnt, 0.0), (double)T.n);
+                T.lod_idx_off[l] = -1;
+            }
             T.n_level[l] = n;
             float reach = 0.f, smax = 0.f;
-            for (int g = 0; g < n; ++g) {
+            for (int k = 0; k < n; ++k) {
+                const int g = sub.empty() ? k : (int)sub[k];
                 reach = std::max(reach, c->reach_g[t][g]);
                 smax = std::max(smax, c->smax_g[t][g]);
             }
@@ -186,6 +211,18 @@ void refresh_lod_bounds(cs_ctx *c) {
 }
 
 int push_templates(cs_ctx *ctx) {
+    const size_t ni = ctx->lod_idx_host.size();
+    if (ni > ctx->lod_idx_cap) {
+        CS_CUDA(cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->d_lod_idx);
+        ctx->d_lod_idx = nullptr;
+        ctx->lod_idx_cap = 0;
+        CS_CUDA(cudaMalloc(&ctx->d_lod_idx, ni * sizeof(uint32_t)));
+        ctx->lod_idx_cap = ni;
+    }
+    if (ni > 0)
+        CS_CUDA(cudaMemcpyAsync(ctx->d_lod_idx, ctx->lod_idx_host.data(), ni * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, ctx->stream));
     CS_CUDA(cudaMemcpyAsync(ctx->d_tpl, ctx->tpl_host.data(), sizeof(TemplateInfo) * ctx->n_tpl,
                             cudaMemcpyHostToDevice, ctx->stream));
     CS_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -311,7 +348,7 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->rec); release(ctx->key); release(ctx->ids); release(ctx->key2); release(ctx->ids2);
     release(ctx->bins); release(ctx->bins_sorted); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
     release(ctx->scratch); release(ctx->rect); release(ctx->ranges); release(ctx->ptile);
-    release(ctx->ptile2); release(ctx->img);
+    release(ctx->ptile2); release(ctx->img); release(ctx->contrib_s);
     release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_chunk0);
     release(ctx->bw_done); release(ctx->bw_state); release(ctx->bw_part);
     if (ctx->d_meta) cudaFree(ctx->d_meta);
@@ -462,6 +499,7 @@ int cs_upload_templates(cs_ctx *ctx, int32_t n_templates, const cs_template_desc
     CS_CUDA(cudaMemcpy(ctx->d_sh, sh.data(), sizeof(float4) * planes_total, cudaMemcpyHostToDevice));
     ctx->n_tpl = n_templates;
     ctx->tpl_host = info;
+    ctx->lod_sub.assign(n_templates, {});
     ctx->reach_g = std::move(reach);
     ctx->smax_g = std::move(smax);
     ctx->n_gauss_total = g_total;
@@ -507,6 +545,29 @@ int cs_set_lod(cs_ctx *ctx, int32_t n_levels, const float *dist_thresh, const fl
     return push_templates(ctx);
 }
 
+int cs_set_lod_subset(cs_ctx *ctx, int32_t template_id, int32_t level, int32_t n, const uint32_t *idx) {
+    if (!ctx) return CS_ERR_ARG;
+    if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "cs_set_lod_subset before cs_upload_templates");
+    if (template_id < 0 || template_id >= ctx->n_tpl)
+        return fail(ctx, CS_ERR_ARG, "template_id %d out of range", template_id);
+    if (level < 0 || level >= CS_MAX_LEVELS) return fail(ctx, CS_ERR_ARG, "level must be 0..%d", CS_MAX_LEVELS - 1);
+    const int ng = ctx->tpl_host[template_id].n;
+    if (n < 0 || n > ng) return fail(ctx, CS_ERR_ARG, "n = %d outside 0..%d", n, ng);
+    if (n > 0 && !idx) return fail(ctx, CS_ERR_ARG, "NULL index array");
+    std::vector<uint32_t> sub(idx, idx + n);
+    std::vector<char> seen(ng, 0);
+    for (int k = 0; k < n; ++k) {
+        if (sub[k] >= (uint32_t)ng)
+            return fail(ctx, CS_ERR_ARG, "idx[%d] = %u outside the template's %d Gaussians", k, sub[k], ng);
+        if (seen[sub[k]]) return fail(ctx, CS_ERR_ARG, "idx[%d] = %u repeats an earlier index", k, sub[k]);
+        seen[sub[k]] = 1;
+    }
+    CS_CUDA(cudaSetDevice(ctx->device));
+    ctx->lod_sub[template_id][level] = std::move(sub);
+    refresh_lod_bounds(ctx);
+    return push_templates(ctx);
+}
+
 int cs_set_instances(cs_ctx *ctx, int32_t n, const int32_t *template_id, const float *root,
                      const float *joint_pose, int32_t on_device) {
     if (!ctx) return CS_ERR_ARG;
@@ -539,7 +600,8 @@ int cs_set_instances(cs_ctx *ctx, int32_t n, const int32_t *template_id, const f
     return CS_OK;
 }
 
-static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_stats *stats) {
+static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_stats *stats,
+                       float *contrib_tmpl = nullptr) {
     if (!cam || !out) return fail(ctx, CS_ERR_ARG, "NULL camera or output");
     if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(ctx, CS_ERR_ARG, "rgba_out must be 16-byte aligned");
     if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "no templates uploaded");
@@ -614,7 +676,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->bins_sorted, Sa, "bin words in depth order"));
     CS_TRY(ensure(ctx, ctx->pair_off, Sa + 1, "pair offsets"));
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Sa), scan_scratch_words(Sa + 1)), "scratch"));
-    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh};
+    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh,
+                      ctx->d_lod_idx};
     if (S > 0)
         launched += launch_project(proj_blocks, ctx->groups.p, ctx->n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                        ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
@@ -671,9 +734,17 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         CS_TRY(ensure(ctx, ctx->bw_stop, ms * 256, "blend stop chunks"));
     }
     BlendWork bw{ctx->bw_slot.p, ctx->bw_tile.p, ctx->bw_chunk0.p, ctx->bw_done.p, ctx->bw_state.p, ctx->bw_part.p,
-                 ctx->bw_meta.p, ctx->bw_stop.p};
+                 ctx->bw_meta.p, ctx->bw_stop.p, nullptr};
+    if (contrib_tmpl) {
+        CS_TRY(ensure(ctx, ctx->contrib_s, Sa, "splat contributions"));
+        CS_CUDA(cudaMemsetAsync(ctx->contrib_s.p, 0, Sa * sizeof(float), st));
+        bw.contrib = ctx->contrib_s.p;
+    }
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ctx->ranges.p, pval, ctx->rec.p, out,
                              bw, (uint32_t)P, st);
+    if (contrib_tmpl)
+        launched += launch_contrib_to_template((int)S, ctx->groups.p, ctx->n_groups, ctx->d_tpl, ctx->d_lod_idx,
+                                               ctx->contrib_s.p, contrib_tmpl, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[8], st));
     CS_CUDA(cudaGetLastError());
     ctx->timed = timing;
@@ -696,6 +767,14 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
 int cs_render(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats) {
     if (!ctx) return CS_ERR_ARG;
     return render_impl(ctx, cam, reinterpret_cast<float4 *>(rgba_out), stats);
+}
+
+int cs_render_contrib(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, float *contrib_out,
+                      cs_frame_stats *stats) {
+    if (!ctx) return CS_ERR_ARG;
+    if (!contrib_out) return fail(ctx, CS_ERR_ARG, "NULL contribution array");
+    if (reinterpret_cast<uintptr_t>(contrib_out) & 3u) return fail(ctx, CS_ERR_ARG, "contrib_out must be 4-byte aligned");
+    return render_impl(ctx, cam, reinterpret_cast<float4 *>(rgba_out), stats, contrib_out);
 }
 
 int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_frame_stats *stats) {
@@ -758,7 +837,8 @@ int cs_get_stage_times(cs_ctx *ctx, float *ms, int32_t n, int32_t average, int64
 int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
     if (!ctx || !out) return CS_ERR_ARG;
     int64_t tb = (int64_t)ctx->n_gauss_total * (sizeof(float4) * 3 + sizeof(float2) + sizeof(uint32_t)) +
-                 (int64_t)ctx->sh_planes_total * sizeof(float4) + (int64_t)ctx->n_tpl * sizeof(TemplateInfo);
+                 (int64_t)ctx->sh_planes_total * sizeof(float4) + (int64_t)ctx->n_tpl * sizeof(TemplateInfo) +
+                 (int64_t)ctx->lod_idx_cap * sizeof(uint32_t);
     int64_t ib = bytes_of(ctx->tid) + bytes_of(ctx->vis) + bytes_of(ctx->root) + bytes_of(ctx->pose) +
                  bytes_of(ctx->B) + bytes_of(ctx->V) + bytes_of(ctx->Cloc) + bytes_of(ctx->groups);
     int64_t fb = bytes_of(ctx->rec) + bytes_of(ctx->key) + bytes_of(ctx->ids) + bytes_of(ctx->key2) +
@@ -766,7 +846,7 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
                  bytes_of(ctx->pval2) + bytes_of(ctx->scratch) + bytes_of(ctx->rect) + bytes_of(ctx->ranges) +
                  bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img) + bytes_of(ctx->bw_slot) +
                  bytes_of(ctx->bw_tile) + bytes_of(ctx->bw_meta) + bytes_of(ctx->bw_chunk0) + bytes_of(ctx->bw_done) +
-                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop);
+                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop) + bytes_of(ctx->contrib_s);
     out->template_bytes = tb;
     out->instance_bytes = ib;
     out->frame_bytes = fb;
@@ -947,7 +1027,8 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     if ((size_t)S > kStaticSplats)
         return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: %lld splats exceed the static limit of %zu",
                     (long long)S, kStaticSplats);
-    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh};
+    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh,
+                      ctx->d_lod_idx};
     if (S > 0)
         launched += launch_project(proj_blocks, ctx->groups.p, n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                                    ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,

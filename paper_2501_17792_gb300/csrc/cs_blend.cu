@@ -50,6 +50,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 struct StagedRecord {
     float4 a, b, c, q;  // {u, v, A, B}, {C, o, r, depth}, {r, g, b, -}, {reach x, reach y, fcut, log2 o}
+    uint32_t s;         // splat id
     bool have;
 };
 
@@ -57,7 +58,8 @@ __device__ __forceinline__ void load_record(StagedRecord &r, const uint32_t *__r
                                             const float4 *__restrict__ rec, uint32_t idx, uint32_t end) {
     r.have = idx < end;
     if (r.have) {
-        const float4 *p = rec + (size_t)__ldg(pval + idx) * kRecVec;
+        r.s = __ldg(pval + idx);
+        const float4 *p = rec + (size_t)r.s * kRecVec;
         r.a = __ldg(p + 0);
         r.b = __ldg(p + 1);
         r.c = __ldg(p + 2);
@@ -71,6 +73,7 @@ struct BlendShared {
     float4 s0[2][kBlendThreads];
     float4 s1[2][kBlendThreads];
     float4 s2[2][kBlendThreads];
+    uint32_t sid[2][kBlendThreads];
     uint8_t mask[2][kBlendThreads];
 };
 
@@ -85,7 +88,8 @@ struct Pixel {
 __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start, uint32_t end,
                                                 const uint32_t *__restrict__ pval,
                                                 const float4 *__restrict__ rec, int tx0, int ty0,
-                                                float fpx, float fpy, Pixel &px) {
+                                                float fpx, float fpy, Pixel &px,
+                                                float *__restrict__ contrib = nullptr) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t wbit = 1u << warp;
     auto stage = [&](const StagedRecord &r, int h) {
@@ -102,6 +106,7 @@ __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start,
             sh.s0[h][tid] = make_float4(r.a.x, r.a.y, -0.5f * kLog2e * r.a.z, -kLog2e * r.a.w);
             sh.s1[h][tid] = make_float4(-0.5f * kLog2e * r.b.x, r.q.w, r.b.z, 0.0f);
             sh.s2[h][tid] = r.c;
+            sh.sid[h][tid] = r.s;
         }
         sh.mask[h][tid] = (uint8_t)m;
     };
@@ -139,6 +144,7 @@ __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start,
                 }
                 const float4 col = sh.s2[h][j];
                 const float wgt = alpha * px.T;
+                if (contrib) atomicAdd(contrib + sh.sid[h][j], wgt);
                 px.r += col.x * wgt;
                 px.g += col.y * wgt;
                 px.b += col.z * wgt;
@@ -187,8 +193,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int
     const TileGeom g = tile_geom(tile, tiles_x, W, H);
     const uint2 rg = ranges[tile];
     Pixel px{1.0f, 0.0f, 0.0f, 0.0f, !g.inside, false};
-    const uint32_t end1 = rg.y - rg.x > kBudget ? rg.x + kBudget : rg.y;
-    composite_range(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
+    const uint32_t end1 = rg.y - rg.x > kBudget && !work.contrib ? rg.x + kBudget : rg.y;
+    composite_range(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib);
     if (end1 < rg.y) {
         // pairs remain: record the pixel state for pass 2 and the merge
         const int slot = work.cand_slot[tile];
@@ -316,7 +322,7 @@ __global__ void __launch_bounds__(1024) k_blend_plan(int n_tiles, const uint2 *_
         const int t = base + threadIdx.x;
         uint32_t n = 0;
         if (t < n_tiles) n = ranges[t].y - ranges[t].x;
-        const uint32_t cand = n > kBudget ? 1u : 0u;
+        const uint32_t cand = n > kBudget && !work.contrib ? 1u : 0u;
         const uint32_t nk = cand ? (n - kBudget + kChunk - 1) / kChunk : 0u;
         const uint32_t ec = block_exclusive_scan(cand, &tot_c);
         const uint32_t ek = block_exclusive_scan(nk, &tot_k);
@@ -350,7 +356,8 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
     const size_t max_chunks = blend_max_chunks((size_t)n, n_pairs);
     k_blend_plan<<<1, 1024, 0, st>>>(n, ranges, work);
     k_blend<<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
-    if (n_pairs <= kBudget) return 2;  // no tile can have pairs left after pass 1
+    // no tile has pairs left after pass 1 (or statistics: one exact pass)
+    if (n_pairs <= kBudget || work.contrib) return 2;
     k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);
     k_blend_merge<<<(unsigned)max_cand, kBlendThreads, 0, st>>>(tiles_x, W, H, out, work);
     k_blend_fix<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);

@@ -351,7 +351,10 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(
     if (gg >= G.ng) return;
     const int s = G.splat0 + islot * G.ng + gg;
     const TemplateInfo &T = tpls[G.tpl];
-    const int gi = T.g_off + gg;
+    // the level's Gaussians: a prefix of the template, or a chosen subset
+    const int sub = T.lod_idx_off[G.lvl];
+    const int gsrc = sub >= 0 ? (int)__ldg(ta.lod_idx + sub + gg) : gg;
+    const int gi = T.g_off + gsrc;
     ids[s] = (uint32_t)s;
 
     // LBS (CrowdSplat Sec. 2): M = sum_k w_k B_{idx_k} (instance local)
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(
                 const float inv = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
                 ddx *= inv; ddy *= inv; ddz *= inv;
                 float rgb[3];
-                const int64_t base = T.sh_off + gg;
+                const int64_t base = T.sh_off + gsrc;
                 switch (T.sh_deg) {
                     case 0: sh_colour<0>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
                     case 1: sh_colour<1>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
@@ -526,6 +529,44 @@ int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_
     k_project<<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, vis, B, V, Cloc, root, ta,
                                                 tpls, cam, lod, skin_mode, sh_frame, rec, key, ids,
                                                 rect, bin);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// contribution statistics: per-splat sums -> per template Gaussian
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_contrib_to_template(int n_splats, const Group *__restrict__ groups,
+                                                             int n_groups, const TemplateInfo *__restrict__ tpls,
+                                                             const uint32_t *__restrict__ lod_idx,
+                                                             const float *__restrict__ cs_,
+                                                             float *__restrict__ ct) {
+    __shared__ Group sg[kMaxTemplates * kMaxLevels];
+    for (int g = threadIdx.x; g < n_groups; g += blockDim.x) sg[g] = groups[g];
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_splats) return;
+    const float c = cs_[s];
+    if (c == 0.0f) return;
+    int lo = 0, hi = n_groups - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sg[mid].splat0 <= s) lo = mid; else hi = mid - 1;
+    }
+    const Group &G = sg[lo];
+    const int gg = (s - G.splat0) % G.ng;
+    const TemplateInfo &T = tpls[G.tpl];
+    const int sub = T.lod_idx_off[G.lvl];
+    const int gsrc = sub >= 0 ? (int)lod_idx[sub + gg] : gg;
+    atomicAdd(ct + T.g_off + gsrc, c);
+}
+
+int launch_contrib_to_template(int n_splats, const Group *groups, int n_groups, const TemplateInfo *tpls,
+                               const uint32_t *lod_idx, const float *contrib_splat, float *contrib_tmpl,
+                               cudaStream_t st) {
+    if (n_splats <= 0) return 0;
+    k_contrib_to_template<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, groups, n_groups, tpls, lod_idx,
+                                                                  contrib_splat, contrib_tmpl);
     return 1;
 }
 

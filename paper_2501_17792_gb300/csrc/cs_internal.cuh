@@ -60,6 +60,7 @@ struct TemplateInfo {
     int8_t parent[kJoints];
     int8_t depth[kJoints];         // depth in the kinematic tree (root 0)
     int32_t max_depth;
+    int32_t lod_idx_off[kMaxLevels];  // level's Gaussian subset in lod_idx, -1: the first n_level
 };
 
 struct Group {         // visible instances of one (template, level)
@@ -96,6 +97,7 @@ struct TemplateArrays {
     const float4 *skin_w;
     const uint32_t *skin_i;
     const float4 *sh;
+    const uint32_t *lod_idx;  // template-local Gaussian indices of subset levels
 };
 
 // ---------------------------------------------------------------------------
@@ -195,6 +197,11 @@ enum MetaIndex {
 };
 
 // Every launch_* function returns the number of kernels it launched.
+// Per template Gaussian, add the per-splat sums of contrib (splat ids as
+// grouped by the cull kernel; subset levels map through lod_idx).
+int launch_contrib_to_template(int n_splats, const Group *groups, int n_groups, const TemplateInfo *tpls,
+                               const uint32_t *lod_idx, const float *contrib_splat, float *contrib_tmpl,
+                               cudaStream_t st);
 // ---- geometry (cs_geometry.cu) ----
 int launch_fk(int n_inst, int n_tpl, const int32_t *tid, const float *pose, const TemplateInfo *tpls,
               int max_depth, float *B, cudaStream_t st);
@@ -251,6 +258,9 @@ struct BlendWork {
     float4 *part;
     int32_t *meta;
     int32_t *stop;
+    // when set: per splat, sum over pixels of its compositing weight
+    // alpha * T (added to); lists are then composited in one pass
+    float *contrib;
 };
 constexpr uint32_t kBlendBudget = 8192;  // pairs composited by pass 1 per tile
 constexpr uint32_t kBlendChunk = 1024;   // pairs per pass-2 chunk

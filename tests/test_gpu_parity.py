@@ -48,10 +48,12 @@ def render(r, sc, stats=False):
     return out.cpu().numpy()
 
 
-def full_check(sc, *, skin_mode=0, sh_frame=0, label="", max_boundary=0.08, **kw):
+def full_check(sc, *, skin_mode=0, sh_frame=0, label="", max_boundary=0.08, subsets=None, **kw):
     r = make(sc, skin_mode=skin_mode, sh_frame=sh_frame, **kw)
+    for (t, l), idx in (subsets or {}).items():
+        r.set_lod_subset(t, l, idx)
     img, st = render(r, sc, stats=True)
-    os_ = oracle.OracleScene(sc, skin_mode=skin_mode, sh_frame=sh_frame)
+    os_ = oracle.OracleScene(sc, skin_mode=skin_mode, sh_frame=sh_frame, subsets=subsets)
     errs = PU.compare_splats(r, sc, os_)
     eps = PU.eps_from(errs)
     ref = oracle.render(os_, eps)
