@@ -1,8 +1,9 @@
 """Thin Python binding of libcrowdsplat.so (argument marshalling only).
 
-Every function of ``include/crowdsplat.h`` is reachable under the same name
-through :func:`lib`; :class:`Renderer` wraps a context with PyTorch device
-memory and streams.  All computation runs in the library's CUDA kernels:
+Every function of ``include/crowdsplat.h`` and ``include/crowdsplat_lod.h``
+is reachable under the same name through :func:`lib`; :class:`Renderer`
+wraps a render context and :class:`Mlp` the LoD ranking network, with
+PyTorch device memory and streams.  All computation runs in the library's CUDA kernels:
 there is no CPU path, and :func:`load` raises if the library is missing.
 """
 from __future__ import annotations
@@ -81,7 +82,20 @@ SIGNATURES = {
     "cs_last_error": (C.c_char_p, [_P]),
     "cs_debug_read": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "cs_version": (C.c_char_p, []),
+    # ranked LoD (include/crowdsplat_lod.h)
+    "cs_lod_features": (C.c_int, [_P, _P]),
+    "cs_lod_rank": (C.c_int, [_P, _P, _P]),
+    "cs_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, _P, C.c_uint64]),
+    "cs_mlp_destroy": (None, [_P]),
+    "cs_mlp_last_error": (C.c_char_p, [_P]),
+    "cs_mlp_get_params": (C.c_int, [_P, _P]),
+    "cs_mlp_set_params": (C.c_int, [_P, _P]),
+    "cs_mlp_forward": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
+    "cs_mlp_train_step": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_float, C.POINTER(C.c_float)]),
+    "cs_mlp_get_grad": (C.c_int, [_P, _P]),
 }
+
+LOD_FEATURES, MLP_PARAMS = 32, 48 * 64 + 64 + 64 * 64 + 64 + 64 + 1
 
 
 def load(path: str | None = None):
@@ -190,6 +204,8 @@ class Renderer:
             (d.means, d.scales, d.quats, d.opacity, d.sh, d.skin_idx, d.skin_w, d.rest_joints,
              d.parents) = (a.ctypes.data for a in arrs)
         self._check(self.L.cs_upload_templates(self.h, len(templates), descs))
+        self.template_sizes = [int(np.asarray(t.means).shape[0]) for t in templates]
+        self.n_gauss_total = sum(self.template_sizes)
 
     def set_lod(self, lod):
         thr = _host(lod.thresholds, np.float32)
@@ -278,6 +294,27 @@ class Renderer:
         return dict(template_bytes=m.template_bytes, instance_bytes=m.instance_bytes,
                     frame_bytes=m.frame_bytes, total_bytes=m.total_bytes)
 
+    def lod_features(self):
+        """[n_total, 32] float32 CUDA tensor of per-Gaussian ranking features."""
+        torch = self.torch
+        n = self.n_gauss_total
+        with torch.cuda.stream(self.stream):
+            f = torch.empty((n, LOD_FEATURES), dtype=torch.float32, device=f"cuda:{self.device}")
+        self._check(self.L.cs_lod_features(self.h, f.data_ptr()))
+        return f
+
+    def lod_rank(self, score):
+        """Per-template orders (uint32 as int32 CUDA tensor [n_total]) of the
+        Gaussians by descending score (float32 CUDA tensor [n_total])."""
+        torch = self.torch
+        s = score.to(torch.float32).contiguous()
+        with torch.cuda.stream(self.stream):
+            o = torch.empty(s.shape[0], dtype=torch.int32, device=f"cuda:{self.device}")
+        if s.shape[0] != self.n_gauss_total:
+            raise ValueError(f"score has {s.shape[0]} entries, templates hold {self.n_gauss_total}")
+        self._check(self.L.cs_lod_rank(self.h, s.data_ptr(), o.data_ptr()))
+        return o
+
     def debug(self, which: str) -> np.ndarray:
         code = DBG[which]
         size = C.c_size_t()
@@ -292,6 +329,80 @@ class Renderer:
         shape = {"skin_b": (-1, 24, 3, 4), "groups": (-1, 7), "records": (-1, 16), "rects": (-1, 4),
                  "tile_ranges": (-1, 2)}.get(which)
         return a.reshape(shape) if shape else a
+
+
+class Mlp:
+    """The LoD ranking MLP (48 -> 64 -> 64 -> 1, BF16 tensor-core kernels)
+    on one CUDA device; inputs and outputs are CUDA tensors."""
+
+    def __init__(self, device: int = 0, stream=None, seed: int = 0):
+        import torch
+        self.torch = torch
+        self.L = load()
+        self.device = int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        rc = self.L.cs_mlp_create(C.byref(h), self.device, C.c_void_p(int(self.stream.cuda_stream)),
+                                  C.c_uint64(int(seed)))
+        if rc != CS_OK:
+            raise CrowdSplatError(rc, "cs_mlp_create failed")
+        self.h = h
+
+    def _check(self, rc: int):
+        if rc != CS_OK:
+            raise CrowdSplatError(rc, self.L.cs_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.cs_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        self._check(self.L.cs_mlp_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, p):
+        a = _host(np.asarray(p), np.float32)
+        if a.shape != (MLP_PARAMS,):
+            raise ValueError(f"need {MLP_PARAMS} parameters")
+        self._check(self.L.cs_mlp_set_params(self.h, a.ctypes.data))
+
+    def grad(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        self._check(self.L.cs_mlp_get_grad(self.h, out.ctypes.data))
+        return out
+
+    def _dev(self, t, dtype):
+        torch = self.torch
+        return t.to(device=f"cuda:{self.device}", dtype=dtype).contiguous()
+
+    def forward(self, feat, band, out=None):
+        torch = self.torch
+        f = self._dev(feat, torch.float32)
+        b = self._dev(band, torch.int32)
+        n = int(f.shape[0])
+        if out is None:
+            with torch.cuda.stream(self.stream):
+                out = torch.empty(n, dtype=torch.float32, device=f"cuda:{self.device}")
+        self._check(self.L.cs_mlp_forward(self.h, n, f.data_ptr(), b.data_ptr(), out.data_ptr()))
+        return out
+
+    def train_step(self, feat, band, target, lr: float, want_loss: bool = True):
+        torch = self.torch
+        f = self._dev(feat, torch.float32)
+        b = self._dev(band, torch.int32)
+        t = self._dev(target, torch.float32)
+        loss = C.c_float()
+        self._check(self.L.cs_mlp_train_step(self.h, int(f.shape[0]), f.data_ptr(), b.data_ptr(), t.data_ptr(),
+                                             float(lr), C.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None
 
 
 def render_scene(scene, *, device: int = 0, **kw):

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/crowdsplat.h"
+#include "../../include/crowdsplat_lod.h"
 #include "cs_internal.cuh"
 
 using namespace cs;
@@ -395,6 +396,7 @@ int cs_upload_templates(cs_ctx *ctx, int32_t n_templates, const cs_template_desc
             T.parent[j] = (int8_t)par;
             T.depth[j] = (int8_t)(par < 0 ? 0 : T.depth[par] + 1);
             max_depth = std::max(max_depth, (int)T.depth[j]);
+            T.max_depth = std::max(T.max_depth, (int32_t)T.depth[j]);
             for (int e = 0; e < 3; ++e) T.rest[j * 3 + e] = d.rest_joints[j * 3 + e];
         }
         g_total += (size_t)d.n_gauss;
@@ -775,6 +777,47 @@ int cs_render_contrib(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, float 
     if (!contrib_out) return fail(ctx, CS_ERR_ARG, "NULL contribution array");
     if (reinterpret_cast<uintptr_t>(contrib_out) & 3u) return fail(ctx, CS_ERR_ARG, "contrib_out must be 4-byte aligned");
     return render_impl(ctx, cam, reinterpret_cast<float4 *>(rgba_out), stats, contrib_out);
+}
+
+int cs_lod_features(cs_ctx *ctx, float *feat_out) {
+    if (!ctx) return CS_ERR_ARG;
+    if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "no templates uploaded");
+    if (!feat_out || (reinterpret_cast<uintptr_t>(feat_out) & 15u))
+        return fail(ctx, CS_ERR_ARG, "feat_out must be a 16-byte aligned device pointer");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh,
+                      ctx->d_lod_idx};
+    launch_lod_features((int)ctx->n_gauss_total, ctx->n_tpl, ctx->d_tpl, ta, feat_out, ctx->stream);
+    CS_CUDA(cudaGetLastError());
+    return CS_OK;
+}
+
+int cs_lod_rank(cs_ctx *ctx, const float *score, uint32_t *order_out) {
+    if (!ctx) return CS_ERR_ARG;
+    if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "no templates uploaded");
+    if (!score || !order_out || (reinterpret_cast<uintptr_t>(score) & 3u) ||
+        (reinterpret_cast<uintptr_t>(order_out) & 3u))
+        return fail(ctx, CS_ERR_ARG, "NULL or misaligned score / order_out");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    const size_t n = ctx->n_gauss_total;
+    // temporary sort buffers: an offline call, so plain allocations
+    // every array starts on a 16-byte boundary
+    const size_t w32 = (n + 3) & ~size_t(3), w16 = ((n + 1) / 2 + 3) & ~size_t(3);
+    const size_t words = 4 * w32 + 2 * w16 + radix_scratch_words(n) + 4;
+    uint32_t *buf = nullptr;
+    if (cudaMalloc(&buf, words * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, CS_ERR_OOM, "cs_lod_rank: %zu bytes of sort buffers", words * sizeof(uint32_t));
+    }
+    uint32_t *k0 = buf, *v0 = k0 + w32, *k1 = v0 + w32, *v1 = k1 + w32;
+    uint16_t *t0 = reinterpret_cast<uint16_t *>(v1 + w32), *t1 = reinterpret_cast<uint16_t *>(v1 + w32 + w16);
+    uint32_t *scratch = v1 + w32 + 2 * w16;
+    lod_rank((int)n, ctx->n_tpl, ctx->d_tpl, score, order_out, k0, v0, k1, v1, t0, t1, scratch, ctx->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(ctx, CS_ERR_CUDA, "cs_lod_rank: %s", cudaGetErrorString(e));
+    return CS_OK;
 }
 
 int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_frame_stats *stats) {

@@ -199,6 +199,13 @@ enum MetaIndex {
 // Every launch_* function returns the number of kernels it launched.
 // Per template Gaussian, add the per-splat sums of contrib (splat ids as
 // grouped by the cull kernel; subset levels map through lod_idx).
+// ranked LoD (offline): per-Gaussian features and per-template ranking
+constexpr int kLodFeatures = 32;
+int launch_lod_features(int n_total, int n_tpl, const TemplateInfo *tpls, const TemplateArrays &ta, float *feat,
+                        cudaStream_t st);
+int lod_rank(int n_total, int n_tpl, const TemplateInfo *tpls, const float *score, uint32_t *order,
+             uint32_t *key0, uint32_t *val0, uint32_t *key1, uint32_t *val1, uint16_t *tk0, uint16_t *tk1,
+             uint32_t *scratch, cudaStream_t st);
 int launch_contrib_to_template(int n_splats, const Group *groups, int n_groups, const TemplateInfo *tpls,
                                const uint32_t *lod_idx, const float *contrib_splat, float *contrib_tmpl,
                                cudaStream_t st);

@@ -1,5 +1,5 @@
 """CPU checks of the C ABI: the library builds for sm_103a, loads, and exports
-every function include/crowdsplat.h declares; host-only calls behave."""
+every function the headers under include/ declare; host-only calls behave."""
 import ctypes as C
 import os
 import re
@@ -7,13 +7,15 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "crowdsplat.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("crowdsplat.h", "crowdsplat_lod.h")]
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(cs_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(cs_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -27,8 +29,10 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ("cs_create", "cs_destroy", "cs_upload_templates", "cs_set_lod", "cs_set_instances",
                  "cs_render", "cs_render_to_host", "cs_get_stage_times", "cs_memory_stats",
-                 "cs_last_error", "cs_debug_read", "cs_version"):
+                 "cs_last_error", "cs_debug_read", "cs_version", "cs_set_lod_subset", "cs_render_contrib",
+                 "cs_lod_features", "cs_lod_rank", "cs_mlp_create", "cs_mlp_forward", "cs_mlp_train_step"):
         assert must in names
+    assert sorted(os.listdir(os.path.join(ROOT, "include"))) == sorted(os.path.basename(h) for h in HEADERS)
 
 
 def test_library_exports_every_declared_symbol(lib):
