@@ -404,6 +404,183 @@ def run_sweep(args):
     return rows_out
 
 
+def _fps(r, cam, tid, root, poses, out, warmup, steps):
+    """Frames per second of animated frames (new device-resident poses per
+    frame), CUDA events on the default stream."""
+    import torch
+    for f in range(warmup):
+        r.set_instances(tid, root, poses[f % len(poses)])
+        r.render(cam, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for f in range(steps):
+        r.set_instances(tid, root, poses[(warmup + f) % len(poses)])
+        r.render(cam, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    return steps / (e0.elapsed_time(e1) / 1e3)
+
+
+def run_learned_lod(args):
+    """Ranked (learned) LoD against the distance LoD with prefix subsets, at
+    10,000 instances and 3840x2160: PSNR against the full-detail frame at the
+    same Gaussian budget, and FPS of the learned ranking at the smallest
+    budget that matches the distance LoD's PSNR."""
+    import numpy as np
+    import torch
+    from paper_2501_17792_gb300 import binding, build
+    from paper_2501_17792_gb300 import lod as LOD
+    from paper_2501_17792_gb300 import scene as S
+    build.build()
+    small = args.small
+    W, H = (960, 540) if small else (3840, 2160)
+    cols, rows = (30, 30) if small else (100, 100)
+    n_tpl, n_g = (4, 16384) if small else (14, 65536)
+    views = 8 if small else 34
+    tpls = [S.make_template(1000 + t, n_g, 3) for t in range(n_tpl)]
+    cam = S.look_camera((0.0, 1.6, 0.0), 10.0, W, H)
+    r = binding.Renderer(device=0)
+    r.upload_templates(tpls)
+    sizes = r.template_sizes
+    # 1. training data: contributions of every Gaussian per distance band
+    t0 = time.time()
+    feat = r.lod_features()
+    contrib = LOD.collect_contributions(r, n_tpl, cam, views_per_band=views, instances_per_view=100, seed=5)
+    t_collect = time.time() - t0
+    targets = r.lod_targets(contrib)
+    # 2. the ranking MLP
+    t0 = time.time()
+    mlp = binding.Mlp(device=0, seed=1)
+    hist = LOD.train_ranker(mlp, feat, targets, steps=args.lod_steps, log_every=max(1, args.lod_steps // 5))
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    scores = LOD.band_scores(mlp, feat, 3)
+    # rank correlation of predicted and measured order, per band (Spearman, host)
+    def spearman(a, b):
+        ra = np.argsort(np.argsort(a)).astype(np.float64)
+        rb = np.argsort(np.argsort(b)).astype(np.float64)
+        return float(np.corrcoef(ra, rb)[0, 1])
+    tg = targets.cpu().numpy()
+    sc_np = scores.cpu().numpy()
+    rho = [round(spearman(sc_np[b], tg[b]), 4) for b in range(3)]
+
+    base = S.paper_lod()
+    f = np.asarray(base.fractions, np.float64)
+
+    def lod_cfg(scale=1.0, expo=0.5):
+        fr = np.array([1.0, f[1] * scale, f[2] * scale])
+        return S.LodConfig(thresholds=base.thresholds, fractions=fr.astype(np.float32),
+                           scale_mult=(fr ** -expo).astype(np.float32)), fr
+
+    def frame_images(inst, poses_dev, configs):
+        """Images of frame 0 for each (name, lod, subsets-or-None)."""
+        tid = torch.from_numpy(inst.template_id).cuda()
+        root = torch.from_numpy(inst.root.reshape(-1, 12)).cuda()
+        out = {}
+        for name, lod, subs in configs:
+            LOD.clear_subsets(r, n_tpl)
+            r.set_lod(lod)
+            if subs is not None:
+                LOD.apply_subsets(r, subs)
+            r.set_instances(tid, root, poses_dev[0])
+            img, st = r.render(cam, stats=True)
+            out[name] = (img, st)
+        return out
+
+    # 3. scale-multiplier exponent, tuned on a training crowd (other layout
+    # and poses) for both methods
+    tr_inst = S.crowd_instances(n_tpl, cols, rows, layout_seed=8, pose_seed=300)
+    tr_poses = [torch.from_numpy(tr_inst.pose).cuda()]
+    expos = (0.0, 0.25, 0.5)
+    cfgs = [("full", S.single_lod(), None)]
+    for e in expos:
+        lod, fr = lod_cfg(1.0, e)
+        cfgs.append((f"plain_{e}", lod, None))
+        cfgs.append((f"learned_{e}", lod, LOD.ranked_subsets(r, scores, fr, sizes, levels=(1, 2))))
+    imgs = frame_images(tr_inst, tr_poses, cfgs)
+    ref = imgs["full"][0]
+    tune = {k: LOD.psnr(v[0], ref) for k, v in imgs.items() if k != "full"}
+    e_plain = max(expos, key=lambda e: tune[f"plain_{e}"])
+    e_learn = max(expos, key=lambda e: tune[f"learned_{e}"])
+    del imgs, ref
+
+    # 4. evaluation crowd: PSNR vs full detail, budgets, FPS
+    inst = S.crowd_instances(n_tpl, cols, rows, layout_seed=7, pose_seed=100)
+    n = inst.n
+    poses = [torch.from_numpy(S.random_poses(100 + k, n)).cuda() for k in range(args.warmup + args.steps)]
+    tid = torch.from_numpy(inst.template_id).cuda()
+    root = torch.from_numpy(inst.root.reshape(n, 12)).cuda()
+    lod_plain, _ = lod_cfg(1.0, 0.5)
+    lod_plain_t, _ = lod_cfg(1.0, e_plain)
+    scales = (1.0, 0.7, 0.5, 0.35, 0.25, 0.18, 0.12, 0.08, 0.05, 0.03, 0.02)
+    cfgs = [("full", S.single_lod(), None), ("plain", lod_plain, None), ("plain_tuned", lod_plain_t, None)]
+    direct = LOD.ranked_subsets(r, contrib, lod_cfg(1.0)[1], sizes, levels=(1, 2))
+    cfgs.append(("direct", lod_cfg(1.0, e_learn)[0], direct))
+    learned_subs = {}
+    for s_ in scales:
+        lod, fr = lod_cfg(s_, e_learn)
+        learned_subs[s_] = (lod, LOD.ranked_subsets(r, scores, fr, sizes, levels=(1, 2)))
+        cfgs.append((f"learned_{s_}", lod, learned_subs[s_][1]))
+    imgs = frame_images(inst, poses, cfgs)
+    ref = imgs["full"][0]
+    res = {k: dict(psnr=round(LOD.psnr(v[0], ref), 3), splats=int(v[1]["splats"]), pairs=int(v[1]["pairs"]))
+           for k, v in imgs.items() if k != "full"}
+    full_splats = int(imgs["full"][1]["splats"])
+    del imgs, ref
+    def equal_budget(target_psnr):
+        eq = [s_ for s_ in scales if res[f"learned_{s_}"]["psnr"] >= target_psnr]
+        return min(eq) if eq else None
+
+    s_eq = equal_budget(res["plain"]["psnr"])
+    s_eq_t = equal_budget(res["plain_tuned"]["psnr"])
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+
+    def fps_of(lod, subs):
+        LOD.clear_subsets(r, n_tpl)
+        r.set_lod(lod)
+        if subs is not None:
+            LOD.apply_subsets(r, subs)
+        return _fps(r, cam, tid, root, poses, out, args.warmup, args.steps)
+
+    fps_full = fps_of(S.single_lod(), None)
+    fps_plain = fps_of(lod_plain, None)
+    fps_plain_t = fps_of(lod_plain_t, None)
+    fps_same = fps_of(*learned_subs[1.0])
+    fps_eq = fps_of(*learned_subs[s_eq]) if s_eq is not None else None
+    fps_eq_t = fps_of(*learned_subs[s_eq_t]) if s_eq_t is not None else None
+    line = {
+        "metric": "learned vs distance LoD: FPS at equal PSNR vs full detail",
+        "value": round(fps_eq, 2) if fps_eq else None, "unit": "frames/s",
+        "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "dtype": "f32 render, bf16 MLP", "data": "synthetic",
+        "config": {"workload": f"crowd_{n_tpl}x{n_g}g_sh3_{n}inst_{W}x{H}_lod3_animated",
+                   "bands_m": [10, 30], "fractions": [1.0, 0.25, 0.06]},
+        "distance_lod": {"fps": round(fps_plain, 2), "psnr_db": res["plain"]["psnr"],
+                         "splats": res["plain"]["splats"], "scale_mult_exponent": 0.5,
+                         "psnr_db_tuned_exponent": res["plain_tuned"]["psnr"], "tuned_exponent": e_plain},
+        "learned_lod_same_budget": {"fps": round(fps_same, 2), "psnr_db": res["learned_1.0"]["psnr"],
+                                    "splats": res["learned_1.0"]["splats"], "scale_mult_exponent": e_learn},
+        "learned_lod_equal_psnr": {"budget_scale": s_eq, "psnr_db": res[f"learned_{s_eq}"]["psnr"] if s_eq else None,
+                                   "splats": res[f"learned_{s_eq}"]["splats"] if s_eq else None},
+        "speedup_at_equal_psnr": round(fps_eq / fps_plain, 3) if fps_eq else None,
+        "vs_tuned_distance_lod": {"fps": round(fps_plain_t, 2), "psnr_db": res["plain_tuned"]["psnr"],
+                                  "splats": res["plain_tuned"]["splats"], "learned_budget_scale": s_eq_t,
+                                  "learned_fps": round(fps_eq_t, 2) if fps_eq_t else None,
+                                  "speedup": round(fps_eq_t / fps_plain_t, 3) if fps_eq_t else None},
+        "direct_contribution_ranking_psnr_db": res["direct"]["psnr"],
+        "learned_psnr_by_budget": {str(s_): res[f"learned_{s_}"]["psnr"] for s_ in scales},
+        "learned_splats_by_budget": {str(s_): res[f"learned_{s_}"]["splats"] for s_ in scales},
+        "full_detail": {"fps": round(fps_full, 2), "splats": full_splats},
+        "training": {"instance_views": 3 * views * 100, "rows": int(targets.numel()), "steps": args.lod_steps,
+                     "loss": [(int(a), round(b, 4)) for a, b in hist], "spearman_by_band": rho,
+                     "collect_s": round(t_collect, 2), "train_s": round(t_train, 2)},
+        "tuning_psnr_db": {k: round(v, 3) for k, v in tune.items()},
+    }
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,12 +593,18 @@ def main():
     ap.add_argument("--small", action="store_true", help="small crowd (debugging)")
     ap.add_argument("--sweep", action="store_true",
                     help="paper Table 1/2 sweep at 1280x720 (one JSON line per cell)")
+    ap.add_argument("--learned-lod", action="store_true",
+                    help="learned vs distance LoD at 10,000 instances, 3840x2160 (one JSON line)")
+    ap.add_argument("--lod-steps", type=int, default=1500, help="MLP training steps for --learned-lod")
     ap.add_argument("--profile-case", action="store_true",
                     help="quarter crowd (875 instances, 960x540) for full ncu captures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.sweep:
         run_sweep(args)
+        return
+    if args.learned_lod:
+        run_learned_lod(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

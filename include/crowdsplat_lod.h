@@ -66,6 +66,16 @@ extern "C" {
  * templates), CS_ERR_CUDA. */
 int cs_lod_features(cs_ctx *ctx, float *feat_out);
 
+/* Regression targets of the ranking MLP from contribution sums
+ * (cs_render_contrib): contrib DEVICE float32 [n_bands][n_total] (row b =
+ * the sums over views of distance band b), target_out DEVICE float32
+ * [n_bands][n_total] = ln(c / m + floor), m the mean of c over the
+ * Gaussian's template within that band (sum in double).  floor > 0 keeps
+ * Gaussians that never contributed finite.  Errors: CS_ERR_ARG (n_bands
+ * outside 1..CS_MAX_LEVELS, floor <= 0, NULL or misaligned arrays),
+ * CS_ERR_STATE, CS_ERR_CUDA. */
+int cs_lod_targets(cs_ctx *ctx, int32_t n_bands, const float *contrib, float floor_, float *target_out);
+
 /* Rank every template's Gaussians by score, highest first.
  * score: DEVICE float32 [n_total] (finite); order_out: DEVICE uint32
  * [n_total]: for template t, order_out[g_off(t) + k] is the template-local

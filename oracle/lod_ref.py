@@ -198,6 +198,20 @@ def features(t) -> np.ndarray:
     return f
 
 
+def targets(contrib, sizes, floor: float = 1e-3) -> np.ndarray:
+    """ln(c / m + floor) per (band, Gaussian), m the mean of c over the
+    Gaussian's template in that band.  contrib [n_bands, n_total]."""
+    c = np.asarray(contrib, np.float32).astype(np.float64)
+    out = np.empty_like(c)
+    off = 0
+    for n in sizes:
+        seg = c[:, off:off + n]
+        m = np.maximum(seg.mean(1, keepdims=True), 1e-30)
+        out[:, off:off + n] = np.log(seg / m + floor)
+        off += n
+    return out
+
+
 def rank(scores, sizes) -> np.ndarray:
     """Concatenated per-template orders: for each template (sizes in upload
     order), its local indices by descending score, ties by lower index."""

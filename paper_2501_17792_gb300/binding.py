@@ -85,6 +85,7 @@ SIGNATURES = {
     # ranked LoD (include/crowdsplat_lod.h)
     "cs_lod_features": (C.c_int, [_P, _P]),
     "cs_lod_rank": (C.c_int, [_P, _P, _P]),
+    "cs_lod_targets": (C.c_int, [_P, C.c_int32, _P, C.c_float, _P]),
     "cs_mlp_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, _P, C.c_uint64]),
     "cs_mlp_destroy": (None, [_P]),
     "cs_mlp_last_error": (C.c_char_p, [_P]),
@@ -302,6 +303,18 @@ class Renderer:
             f = torch.empty((n, LOD_FEATURES), dtype=torch.float32, device=f"cuda:{self.device}")
         self._check(self.L.cs_lod_features(self.h, f.data_ptr()))
         return f
+
+    def lod_targets(self, contrib, floor: float = 1e-3):
+        """ln(c / template mean + floor) per (band, Gaussian); contrib is a
+        CUDA float32 tensor [n_bands, n_total]."""
+        torch = self.torch
+        c = contrib.to(torch.float32).contiguous()
+        if c.dim() != 2 or c.shape[1] != self.n_gauss_total:
+            raise ValueError("contrib must be [n_bands, n_total]")
+        with torch.cuda.stream(self.stream):
+            t = torch.empty_like(c)
+        self._check(self.L.cs_lod_targets(self.h, int(c.shape[0]), c.data_ptr(), float(floor), t.data_ptr()))
+        return t
 
     def lod_rank(self, score):
         """Per-template orders (uint32 as int32 CUDA tensor [n_total]) of the

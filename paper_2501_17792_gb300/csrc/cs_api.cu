@@ -792,6 +792,21 @@ int cs_lod_features(cs_ctx *ctx, float *feat_out) {
     return CS_OK;
 }
 
+int cs_lod_targets(cs_ctx *ctx, int32_t n_bands, const float *contrib, float floor_, float *target_out) {
+    if (!ctx) return CS_ERR_ARG;
+    if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "no templates uploaded");
+    if (n_bands < 1 || n_bands > CS_MAX_LEVELS) return fail(ctx, CS_ERR_ARG, "n_bands must be 1..%d", CS_MAX_LEVELS);
+    if (!(floor_ > 0.0f) || !std::isfinite(floor_)) return fail(ctx, CS_ERR_ARG, "floor must be > 0");
+    if (!contrib || !target_out || (reinterpret_cast<uintptr_t>(contrib) & 3u) ||
+        (reinterpret_cast<uintptr_t>(target_out) & 3u))
+        return fail(ctx, CS_ERR_ARG, "NULL or misaligned contrib / target_out");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    launch_lod_targets((int)ctx->n_gauss_total, ctx->n_tpl, n_bands, ctx->d_tpl, contrib, floor_, target_out,
+                       ctx->stream);
+    CS_CUDA(cudaGetLastError());
+    return CS_OK;
+}
+
 int cs_lod_rank(cs_ctx *ctx, const float *score, uint32_t *order_out) {
     if (!ctx) return CS_ERR_ARG;
     if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "no templates uploaded");

@@ -203,6 +203,8 @@ enum MetaIndex {
 constexpr int kLodFeatures = 32;
 int launch_lod_features(int n_total, int n_tpl, const TemplateInfo *tpls, const TemplateArrays &ta, float *feat,
                         cudaStream_t st);
+int launch_lod_targets(int n_total, int n_tpl, int n_bands, const TemplateInfo *tpls, const float *contrib,
+                       float floor_, float *target, cudaStream_t st);
 int lod_rank(int n_total, int n_tpl, const TemplateInfo *tpls, const float *score, uint32_t *order,
              uint32_t *key0, uint32_t *val0, uint32_t *key1, uint32_t *val1, uint16_t *tk0, uint16_t *tk1,
              uint32_t *scratch, cudaStream_t st);

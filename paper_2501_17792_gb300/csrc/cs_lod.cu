@@ -167,7 +167,37 @@ __global__ void k_rank_local(int n, int n_tpl, const TemplateInfo *__restrict__ 
     order[i] = (uint32_t)(g - s_off[template_of(s_off, n_tpl, g)]);
 }
 
+// Regression targets: one CTA per (band, template) sums the template's
+// contributions (fixed order: strided per thread, then a tree), then writes
+// ln(c / mean + floor) for each of its Gaussians.
+__global__ void __launch_bounds__(256) k_lod_targets(int n_total, const TemplateInfo *__restrict__ tpls,
+                                                     const float *__restrict__ contrib, float floor_,
+                                                     float *__restrict__ target) {
+    __shared__ double red[256];
+    const int t = blockIdx.x, b = blockIdx.y;
+    const int g0 = tpls[t].g_off, n = tpls[t].n;
+    const float *c = contrib + (size_t)b * n_total + g0;
+    float *o = target + (size_t)b * n_total + g0;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += (double)c[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double mean = fmax(red[0] / (double)n, 1e-30);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) o[i] = (float)log((double)c[i] / mean + (double)floor_);
+}
+
 }  // namespace
+
+int launch_lod_targets(int n_total, int n_tpl, int n_bands, const TemplateInfo *tpls, const float *contrib,
+                       float floor_, float *target, cudaStream_t st) {
+    if (n_total <= 0 || n_bands <= 0) return 0;
+    k_lod_targets<<<dim3(n_tpl, n_bands), 256, 0, st>>>(n_total, tpls, contrib, floor_, target);
+    return 1;
+}
 
 int launch_lod_features(int n_total, int n_tpl, const TemplateInfo *tpls, const TemplateArrays &ta, float *feat,
                         cudaStream_t st) {

@@ -380,6 +380,24 @@ def crowd_instances(n_templates: int, cols: int, rows: int, *, spacing: float = 
                      pose=random_poses(pose_seed, n))
 
 
+def band_instances(n_templates: int, n: int, d_lo: float, d_hi: float, seed: int, *,
+                   camera_position=(0.0, 1.6, 0.0), half_angle_deg: float = 40.0) -> Instances:
+    """n instances on the ground whose root lies at a distance U(d_lo, d_hi)
+    from the camera centre, at an azimuth U(-half_angle, half_angle) about
+    the camera's +z heading, with yaw U(0, 2 pi), template uniform and poses
+    N(0, 0.3 rad).  Views of one LoD distance band."""
+    rng = np.random.default_rng(seed)
+    cx, cy, cz = camera_position
+    d = rng.uniform(d_lo, d_hi, n)
+    dh = np.sqrt(np.maximum(d * d - cy * cy, 0.0))
+    az = np.radians(rng.uniform(-half_angle_deg, half_angle_deg, n))
+    yaw = rng.uniform(0.0, 2.0 * math.pi, n)
+    tid = rng.integers(0, n_templates, n).astype(np.int32)
+    roots = np.stack([yaw_root(yaw[k], cx + dh[k] * math.sin(az[k]), 0.0, cz + dh[k] * math.cos(az[k]))
+                      for k in range(n)]).astype(np.float32)
+    return Instances(template_id=tid, root=roots, pose=random_poses(seed + 1, n))
+
+
 def crowd(n_templates: int = 14, n_gauss: int = 65536, sh_degree: int = 3,
           cols: int = 50, rows: int = 70, width: int = 1920, height: int = 1080,
           frame: int = 0, lod: LodConfig | None = None) -> Scene:

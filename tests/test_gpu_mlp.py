@@ -87,6 +87,21 @@ def test_rank_matches_reference():
     assert np.array_equal(o, ref)
 
 
+def test_targets_match_reference():
+    sizes = [3000, 517, 4096]
+    tpls = [S.make_template(700 + t, n, 0) for t, n in enumerate(sizes)]
+    sc = S.Scene(tpls, S.Instances(np.zeros(1, np.int32), np.tile(np.eye(3, 4, dtype=np.float32), (1, 1, 1)),
+                                   np.zeros((1, 24, 3), np.float32)),
+                 S.look_camera((0, 1, 0), 0, 32, 32), S.single_lod(), "targets")
+    r = make(sc)
+    rng = np.random.default_rng(4)
+    c = (rng.exponential(1.0, (3, sum(sizes))) * (rng.random((3, sum(sizes))) < 0.7)).astype(np.float32)
+    c[2, :3000] = 0.0
+    t = r.lod_targets(_cuda(c)).cpu().numpy().astype(np.float64)
+    ref = R.targets(c, sizes)
+    assert np.abs(t - ref).max() < 1e-5
+
+
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 40000])
 def test_mlp_forward_matches_reference(n):
     m = _mlp()

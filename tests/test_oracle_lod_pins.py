@@ -173,3 +173,12 @@ def test_rank_orders_by_descending_score_with_index_ties():
     o = R.rank(s, [4, 3])
     assert list(o[:4]) == [1, 0, 2, 3]
     assert list(o[4:]) == [0, 1, 2]
+
+
+def test_targets_closed_form():
+    c = np.array([[1.0, 3.0, 0.0, 2.0, 2.0], [0.0, 0.0, 0.0, 5.0, 1.0]], np.float32)
+    t = R.targets(c, [3, 2], floor=1e-3)
+    assert np.allclose(t[0, :3], np.log(np.array([0.75, 2.25, 0.0]) + 1e-3))
+    assert np.allclose(t[0, 3:], np.log(1.0 + 1e-3))
+    assert np.allclose(t[1, :3], np.log(1e-3))                    # a template that never contributed
+    assert np.allclose(t[1, 3:], np.log(np.array([5 / 3, 1 / 3]) + 1e-3))
