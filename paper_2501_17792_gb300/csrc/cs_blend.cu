@@ -84,7 +84,9 @@ struct Pixel {
 };
 
 // Composite pairs [start, end) of a tile into the calling thread's pixel.
-// Every thread of the CTA must call it with the same range.
+// Every thread of the CTA must call it with the same range.  kStats: also
+// add each composited weight alpha * T to contrib[splat].
+template <bool kStats = false>
 __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start, uint32_t end,
                                                 const uint32_t *__restrict__ pval,
                                                 const float4 *__restrict__ rec, int tx0, int ty0,
@@ -106,7 +108,7 @@ __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start,
             sh.s0[h][tid] = make_float4(r.a.x, r.a.y, -0.5f * kLog2e * r.a.z, -kLog2e * r.a.w);
             sh.s1[h][tid] = make_float4(-0.5f * kLog2e * r.b.x, r.q.w, r.b.z, 0.0f);
             sh.s2[h][tid] = r.c;
-            sh.sid[h][tid] = r.s;
+            if (kStats) sh.sid[h][tid] = r.s;
         }
         sh.mask[h][tid] = (uint8_t)m;
     };
@@ -144,7 +146,7 @@ __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start,
                 }
                 const float4 col = sh.s2[h][j];
                 const float wgt = alpha * px.T;
-                if (contrib) atomicAdd(contrib + sh.sid[h][j], wgt);
+                if (kStats) atomicAdd(contrib + sh.sid[h][j], wgt);
                 px.r += col.x * wgt;
                 px.g += col.y * wgt;
                 px.b += col.z * wgt;
@@ -182,7 +184,9 @@ __device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int 
     return g;
 }
 
-// Pass 1: the first kBudget pairs of every tile.
+// Pass 1: the first kBudget pairs of every tile (kStats: every pair, with
+// per-splat weight sums).
+template <bool kStats>
 __global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int H,
                                                          const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ pval,
@@ -193,8 +197,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int
     const TileGeom g = tile_geom(tile, tiles_x, W, H);
     const uint2 rg = ranges[tile];
     Pixel px{1.0f, 0.0f, 0.0f, 0.0f, !g.inside, false};
-    const uint32_t end1 = rg.y - rg.x > kBudget && !work.contrib ? rg.x + kBudget : rg.y;
-    composite_range(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib);
+    const uint32_t end1 = rg.y - rg.x > kBudget && !kStats ? rg.x + kBudget : rg.y;
+    composite_range<kStats>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib);
     if (end1 < rg.y) {
         // pairs remain: record the pixel state for pass 2 and the merge
         const int slot = work.cand_slot[tile];
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(1024) k_blend_plan(int n_tiles, const uint2 *_
         const int t = base + threadIdx.x;
         uint32_t n = 0;
         if (t < n_tiles) n = ranges[t].y - ranges[t].x;
-        const uint32_t cand = n > kBudget && !work.contrib ? 1u : 0u;
+        const uint32_t cand = n > kBudget ? 1u : 0u;
         const uint32_t nk = cand ? (n - kBudget + kChunk - 1) / kChunk : 0u;
         const uint32_t ec = block_exclusive_scan(cand, &tot_c);
         const uint32_t ek = block_exclusive_scan(nk, &tot_k);
@@ -354,10 +358,15 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
     if (n <= 0) return 0;
     const size_t max_cand = blend_max_slots((size_t)n, n_pairs);
     const size_t max_chunks = blend_max_chunks((size_t)n, n_pairs);
+    if (work.contrib) {
+        // statistics: every list composited in one pass
+        k_blend<true><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+        return 1;
+    }
     k_blend_plan<<<1, 1024, 0, st>>>(n, ranges, work);
-    k_blend<<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
-    // no tile has pairs left after pass 1 (or statistics: one exact pass)
-    if (n_pairs <= kBudget || work.contrib) return 2;
+    k_blend<false><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+    // no tile has pairs left after pass 1
+    if (n_pairs <= kBudget) return 2;
     k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);
     k_blend_merge<<<(unsigned)max_cand, kBlendThreads, 0, st>>>(tiles_x, W, H, out, work);
     k_blend_fix<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
