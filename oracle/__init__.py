@@ -41,7 +41,8 @@ class _Template(C.Structure):
     _fields_ = [("n", C.c_int32), ("sh_degree", C.c_int32),
                 ("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity", C.c_void_p), ("sh", C.c_void_p), ("skin_idx", C.c_void_p),
-                ("skin_w", C.c_void_p), ("rest_joints", C.c_void_p), ("parents", C.c_void_p)]
+                ("skin_w", C.c_void_p), ("rest_joints", C.c_void_p), ("parents", C.c_void_p),
+                ("cov", C.c_void_p)]
 
 
 class _Camera(C.Structure):
@@ -119,6 +120,9 @@ class OracleScene:
             keep.append(arrs)
             tpls[k].n = int(arrs["means"].shape[0])
             tpls[k].sh_degree = int(t.sh_degree)
+            cov = getattr(t, "cov", None)
+            if cov is not None:  # canonical covariance given directly [n, 6]
+                arrs["cov"] = _c(np.asarray(cov).reshape(-1, 6), np.float32)
             for name, a in arrs.items():
                 setattr(tpls[k], name, a.ctypes.data)
         inst = scene.instances

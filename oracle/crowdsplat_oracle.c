@@ -49,6 +49,9 @@ typedef struct {
     const float *skin_w;      /* [n*4]                                   */
     const float *rest_joints; /* [24*3]                                  */
     const int32_t *parents;   /* [24], parents[0] = -1                   */
+    const float *cov;         /* optional [n*6] xx,xy,xz,yy,yz,zz: the canonical
+                                 covariance given directly (replaces
+                                 scales and quats; NULL: from them)      */
 } orc_template;
 
 typedef struct {
@@ -324,23 +327,33 @@ void orc_splat_compute(const orc_scene *s, int inst, const double *B, int lvl, i
     double mu[3] = {tp->means[(size_t)g * 3 + 0], tp->means[(size_t)g * 3 + 1], tp->means[(size_t)g * 3 + 2]};
     for (int r = 0; r < 3; ++r)
         o->mu[r] = M[r * 4 + 0] * mu[0] + M[r * 4 + 1] * mu[1] + M[r * 4 + 2] * mu[2] + M[r * 4 + 3];
-    /* canonical covariance Sigma = R(q) S S^T R(q)^T, S = diag(m_l * s) */
-    double q[4] = {tp->quats[(size_t)g * 4 + 0], tp->quats[(size_t)g * 4 + 1],
-                   tp->quats[(size_t)g * 4 + 2], tp->quats[(size_t)g * 4 + 3]};
-    double Rq[9];
-    orc_quat_to_rot(q, Rq);
+    /* canonical covariance Sigma = R(q) S S^T R(q)^T, S = diag(m_l * s),
+     * or m_l^2 times the covariance given directly */
     double m = s->scale_mult[lvl];
-    double S[3] = {m * tp->scales[(size_t)g * 3 + 0], m * tp->scales[(size_t)g * 3 + 1],
-                   m * tp->scales[(size_t)g * 3 + 2]};
-    double RS[9], Sig[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) RS[i * 3 + j] = Rq[i * 3 + j] * S[j];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double acc = 0.0;
-            for (int k = 0; k < 3; ++k) acc += RS[i * 3 + k] * RS[j * 3 + k];
-            Sig[i * 3 + j] = acc;
-        }
+    double Sig[9];
+    if (tp->cov) {
+        const float *c = tp->cov + (size_t)g * 6;
+        const double m2 = m * m;
+        Sig[0] = m2 * c[0]; Sig[1] = m2 * c[1]; Sig[2] = m2 * c[2];
+        Sig[3] = m2 * c[1]; Sig[4] = m2 * c[3]; Sig[5] = m2 * c[4];
+        Sig[6] = m2 * c[2]; Sig[7] = m2 * c[4]; Sig[8] = m2 * c[5];
+    } else {
+        double q[4] = {tp->quats[(size_t)g * 4 + 0], tp->quats[(size_t)g * 4 + 1],
+                       tp->quats[(size_t)g * 4 + 2], tp->quats[(size_t)g * 4 + 3]};
+        double Rq[9];
+        orc_quat_to_rot(q, Rq);
+        double S[3] = {m * tp->scales[(size_t)g * 3 + 0], m * tp->scales[(size_t)g * 3 + 1],
+                       m * tp->scales[(size_t)g * 3 + 2]};
+        double RS[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) RS[i * 3 + j] = Rq[i * 3 + j] * S[j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += RS[i * 3 + k] * RS[j * 3 + k];
+                Sig[i * 3 + j] = acc;
+            }
+    }
     double Sp[9];
     if (s->skin_mode == 0) {
         /* Sigma' = A Sigma A^T with A the 3x3 part of M */

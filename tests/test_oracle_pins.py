@@ -770,3 +770,36 @@ def test_contribution_lands_on_the_template_gaussian():
     nz = np.nonzero(c)[0]
     assert list(nz) == [40 + k]
     assert abs(c[40 + k] - r["rgba"][..., 3].sum()) < 1e-12
+
+
+def test_direct_covariance_matches_scales_and_rotation():
+    """A covariance given directly renders like the scales and quaternion
+    it comes from: exactly for an axis-aligned Gaussian with dyadic scales,
+    to float32 rounding of the covariance otherwise."""
+    import dataclasses
+    base = S.make_template(91, 300, 1)
+    cam = S.look_camera((0.0, 1.0, -2.5), 0.0, 64, 64, vfov_deg=50.0)
+    root = S.yaw_root(math.pi, 0.0, 0.0, 0.0).astype(np.float32)[None]
+    pose = np.random.default_rng(3).normal(0, 0.3, (1, 24, 3)).astype(np.float32)
+    lod = S.LodConfig(thresholds=np.zeros(0, np.float32), fractions=np.ones(1, np.float32),
+                      scale_mult=np.array([1.5], np.float32))
+    q = base.quats.astype(np.float64)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    Rq = np.stack([oracle.quat_to_rot(x) for x in q])
+    s2 = base.scales.astype(np.float64) ** 2
+    C = np.einsum("nik,nk,njk->nij", Rq, s2, Rq)
+    t2 = dataclasses.replace(base)
+    t2.cov = np.stack([C[:, 0, 0], C[:, 0, 1], C[:, 0, 2], C[:, 1, 1], C[:, 1, 2], C[:, 2, 2]], 1).astype(np.float32)
+    a = oracle.render(oracle.OracleScene(U.scene_of([base], U.instances(1, root, pose), cam, lod)))["rgba"]
+    b = oracle.render(oracle.OracleScene(U.scene_of([t2], U.instances(1, root, pose), cam, lod)))["rgba"]
+    assert a[..., 3].max() > 0.5
+    assert np.abs(a - b).max() < 1e-4
+    # axis-aligned, dyadic scales: the covariance is exact in float32
+    t3 = U.template_from([[0.0, 1.0, 0.0]], [[0.03125, 0.0625, 0.015625]], [[1, 0, 0, 0]], [0.8],
+                         np.full((1, 1, 3), 0.4, np.float32))
+    t4 = dataclasses.replace(t3)
+    t4.cov = np.array([[0.03125 ** 2, 0, 0, 0.0625 ** 2, 0, 0.015625 ** 2]], np.float32)
+    c = oracle.render(oracle.OracleScene(U.scene_of([t3], U.instances(1, root, pose), cam, lod)))["rgba"]
+    d = oracle.render(oracle.OracleScene(U.scene_of([t4], U.instances(1, root, pose), cam, lod)))["rgba"]
+    assert c[..., 3].max() > 0.3
+    assert np.abs(c - d).max() < 1e-14
