@@ -144,11 +144,15 @@ def workload_name(sc):
             f"{sc.camera.width}x{sc.camera.height}_lod{len(sc.lod.fractions)}_animated")
 
 
-def template_bytes(sc):
+def template_bytes(sc, storage="fp32"):
+    """Device bytes of the uploaded templates (the library's layout)."""
     tot = 0
     for t in sc.templates:
         k = (t.sh_degree + 1) ** 2
-        tot += t.means.shape[0] * (16 + 16 + 8 + 16 + 4 + ((k * 3 + 3) // 4) * 16)
+        if storage == "bf16":
+            tot += t.means.shape[0] * (16 + 16 + ((k * 3 + 7) // 8) * 16)
+        else:
+            tot += t.means.shape[0] * (16 + 16 + 8 + 16 + 4 + ((k * 3 + 3) // 4) * 16)
     return tot
 
 
@@ -216,7 +220,8 @@ def run_ours(args, sc, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    r = binding.Renderer(device=local_rank, stream=stream, stage_timing=True)
+    storage = binding.CS_STORE_BF16 if args.storage == "bf16" else binding.CS_STORE_FP32
+    r = binding.Renderer(device=local_rank, stream=stream, stage_timing=True, template_storage=storage)
     r.upload_templates(sc.templates)
     r.set_lod(sc.lod)
     n = sc.instances.n
@@ -293,7 +298,7 @@ def run_ours(args, sc, rank, world, local_rank):
         return
     pk = peaks()
     pixels = sc.camera.width * sc.camera.height
-    sb = stage_bytes(st0, n, template_bytes(sc), pixels)
+    sb = stage_bytes(st0, n, template_bytes(sc, args.storage), pixels)
     stages = {}
     for name, ms in stage_ms.items():
         gbs = sb[name] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
@@ -309,12 +314,14 @@ def run_ours(args, sc, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.storage == "fp32" else "f32 compute, bf16/fp16 template storage", "data": "synthetic",
         "config": {"workload": workload_name(sc), "templates": len(sc.templates), "gaussians_per_template": int(sc.templates[0].n),
                    "sh_degree": int(sc.templates[0].sh_degree), "instances": n, "width": sc.camera.width,
                    "height": sc.camera.height, "lod": {"thresholds_m": [10, 30], "fractions": [1, 0.25, 0.06]},
                    "l2": "inputs larger than L2 (templates 231 MB, splat records > 1 GB per frame)",
-                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "template_storage": args.storage},
         "frame": {"visible_instances": st0["instances_visible"], "per_level": st0["instances_per_level"][:3],
                   "splats": st0["splats"], "pairs": st0["pairs"],
                   "gaussians_per_s": st0["splats"] * value},
@@ -600,6 +607,8 @@ def main():
     ap.add_argument("--small", action="store_true", help="small crowd (debugging)")
     ap.add_argument("--sweep", action="store_true",
                     help="paper Table 1/2 sweep at 1280x720 (one JSON line per cell)")
+    ap.add_argument("--storage", choices=["fp32", "bf16"], default="fp32",
+                    help="template storage precision (bf16: BF16 attributes, FP16 SH, tensor-core skinning)")
     ap.add_argument("--learned-lod", action="store_true",
                     help="learned vs distance LoD at 10,000 instances, 3840x2160 (one JSON line)")
     ap.add_argument("--lod-steps", type=int, default=1500, help="MLP training steps for --learned-lod")

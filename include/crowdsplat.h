@@ -62,6 +62,15 @@ extern "C" {
 #define CS_SH_ROOT_FRAME 0  /* direction expressed in the instance's root frame */
 #define CS_SH_WORLD_FRAME 1 /* direction in world coordinates                   */
 
+/* template storage precision (the precision variant of the path) */
+#define CS_STORE_FP32 0 /* FP32 attributes: 252 B per Gaussian at SH degree 3        */
+#define CS_STORE_BF16 1 /* BF16 mean (as an offset from one of its skinning joints),
+                           opacity, covariance and skinning weights, FP16 SH
+                           coefficients: 128 B per Gaussian at SH degree 3; the
+                           skinning blend runs as a split-BF16 tensor-core product
+                           with FP32 accumulation, renormalised by the sum of the
+                           rounded weights; projection and compositing stay FP32 */
+
 typedef struct cs_ctx cs_ctx; /* opaque, library-owned */
 
 typedef struct {
@@ -72,6 +81,7 @@ typedef struct {
     int32_t instance_cull; /* 1: drop instances whose every splat misses the image
                               (conservative bound; never changes the image); 0: off */
     int32_t stage_timing;  /* 1: record CUDA events per stage (cs_get_stage_times)     */
+    int32_t template_storage; /* CS_STORE_FP32 or CS_STORE_BF16 (applies to uploads)  */
 } cs_create_params;
 
 /* One avatar template, all pointers HOST memory, read during the call.

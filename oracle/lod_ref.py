@@ -139,7 +139,8 @@ Y00 = 0.28209479177387814  # 1 / (2 sqrt(pi))
 def features(t) -> np.ndarray:
     """The 32 ranking features of every Gaussian of template t (attributes
     as uploaded: scales, quaternions, opacity, SH, skinning, rest joints,
-    parents), [n, 32] in FP64."""
+    parents; or, when the template carries ``cov`` [n, 6], its canonical
+    covariance instead of scales and quaternions), [n, 32] in FP64."""
     s = np.asarray(t.scales, np.float32).astype(np.float64)
     qt = np.asarray(t.quats, np.float32).astype(np.float64)
     o = np.asarray(t.opacity, np.float32).astype(np.float64)
@@ -151,8 +152,15 @@ def features(t) -> np.ndarray:
     parents = np.asarray(t.parents)
     n = s.shape[0]
     f = np.zeros((n, N_FEAT))
-    # principal standard deviations: the scales, largest first
-    ss = -np.sort(-s, axis=1)
+    cov6 = getattr(t, "cov", None)
+    if cov6 is not None:
+        # covariance given directly: principal deviations from its eigenvalues
+        c = np.asarray(cov6, np.float32).astype(np.float64).reshape(n, 6)
+        Cg = np.stack([c[:, 0], c[:, 1], c[:, 2], c[:, 1], c[:, 3], c[:, 4], c[:, 2], c[:, 4], c[:, 5]], 1).reshape(n, 3, 3)
+        ss = np.sqrt(np.maximum(np.linalg.eigvalsh(Cg)[:, ::-1], 1e-20))
+    else:
+        # principal standard deviations: the scales, largest first
+        ss = -np.sort(-s, axis=1)
     ls = np.log(ss / 0.01)
     f[:, 0:3] = ls
     f[:, 3] = ls.mean(1)
@@ -181,13 +189,17 @@ def features(t) -> np.ndarray:
         depth[j] = depth[parents[j]] + 1
     f[:, 24] = depth[j0] / depth.max() if depth.max() > 0 else 0.0
     f[:, 25] = 10.0 * np.linalg.norm(mu - rest[j0], axis=1)
-    # covariance R diag(s^2) R^T from the normalised quaternion
-    qn = qt / np.linalg.norm(qt, axis=1, keepdims=True)
-    qw, qx, qy, qz = qn.T
-    R = np.stack([1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
-                  2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
-                  2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)], 1).reshape(n, 3, 3)
-    cov = np.einsum("nik,nk,njk->nij", R, s * s, R)
+    # covariance R diag(s^2) R^T from the normalised quaternion (or as given)
+    if cov6 is not None:
+        cov = Cg
+    else:
+        qn = qt / np.linalg.norm(qt, axis=1, keepdims=True)
+        qw, qx, qy, qz = qn.T
+        R = np.stack([1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
+                      2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                      2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)],
+                     1).reshape(n, 3, 3)
+        cov = np.einsum("nik,nk,njk->nij", R, s * s, R)
     tr = np.trace(cov, axis1=1, axis2=2)
     f[:, 26] = cov[:, 0, 0] / tr
     f[:, 27] = cov[:, 1, 1] / tr

@@ -20,6 +20,7 @@ LIB_PATH = _build.LIB
 CS_OK, CS_ERR_ARG, CS_ERR_CUDA, CS_ERR_OOM, CS_ERR_CAPACITY, CS_ERR_TIMEOUT, CS_ERR_STATE = range(7)
 CS_SKIN_FULL, CS_SKIN_MEANS_ONLY = 0, 1
 CS_SH_ROOT_FRAME, CS_SH_WORLD_FRAME = 0, 1
+CS_STORE_FP32, CS_STORE_BF16 = 0, 1
 DBG = dict(skin_b=1, visible=2, groups=3, records=4, depth_keys=5, rects=6, depth_order=7,
            pair_tiles=8, pair_splats=9, tile_ranges=10)
 STAGES = ("fk", "cull_lod", "skin_project", "depth_sort", "pair_emit", "tile_sort", "tile_ranges",
@@ -28,7 +29,8 @@ STAGES = ("fk", "cull_lod", "skin_project", "depth_sort", "pair_emit", "tile_sor
 
 class CreateParams(C.Structure):
     _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("skin_mode", C.c_int32),
-                ("sh_frame", C.c_int32), ("instance_cull", C.c_int32), ("stage_timing", C.c_int32)]
+                ("sh_frame", C.c_int32), ("instance_cull", C.c_int32), ("stage_timing", C.c_int32),
+                ("template_storage", C.c_int32)]
 
 
 class TemplateDesc(C.Structure):
@@ -154,7 +156,7 @@ class Renderer:
 
     def __init__(self, device: int = 0, stream=None, skin_mode: int = CS_SKIN_FULL,
                  sh_frame: int = CS_SH_ROOT_FRAME, instance_cull: bool = True,
-                 stage_timing: bool = False):
+                 stage_timing: bool = False, template_storage: int = CS_STORE_FP32):
         import torch
         self.torch = torch
         self.L = load()
@@ -165,7 +167,7 @@ class Renderer:
         p = CreateParams(device=self.device, stream=C.c_void_p(int(stream.cuda_stream)),
                          skin_mode=int(skin_mode), sh_frame=int(sh_frame),
                          instance_cull=1 if instance_cull else 0,
-                         stage_timing=1 if stage_timing else 0)
+                         stage_timing=1 if stage_timing else 0, template_storage=int(template_storage))
         h = C.c_void_p()
         rc = self.L.cs_create(C.byref(h), C.byref(p))
         if rc != CS_OK:

@@ -1,6 +1,8 @@
 // cs_api.cu -- the C ABI of libcrowdsplat.so (declared in include/crowdsplat.h):
 // context and device-memory management, template upload, LoD and
 // per-frame instance state, and the ordering of one frame's kernels.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +37,7 @@ struct cs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int skin_mode = 0, sh_frame = 0, instance_cull = 1, stage_timing = 0;
+    int storage = CS_STORE_FP32;  // template storage precision
     std::string err;
 
     // templates
@@ -50,6 +53,7 @@ struct cs_ctx {
     float4 *d_mean_op = nullptr, *d_cov_a = nullptr, *d_skin_w = nullptr, *d_sh = nullptr;
     float2 *d_cov_b = nullptr;
     uint32_t *d_skin_i = nullptr;
+    uint4 *d_qa = nullptr, *d_qb = nullptr, *d_sh16 = nullptr;  // BF16 storage
     size_t n_gauss_total = 0, sh_planes_total = 0;
     int max_depth = 0;
 
@@ -165,6 +169,10 @@ void free_templates(cs_ctx *c) {
     cudaFree(c->d_skin_w);
     cudaFree(c->d_skin_i);
     cudaFree(c->d_sh);
+    cudaFree(c->d_qa);
+    cudaFree(c->d_qb);
+    cudaFree(c->d_sh16);
+    c->d_qa = c->d_qb = c->d_sh16 = nullptr;
     cudaFree(c->d_lod_idx);
     c->d_lod_idx = nullptr;
     c->lod_idx_cap = 0;
@@ -210,6 +218,32 @@ void refresh_lod_bounds(cs_ctx *c) {
         }
     }
 }
+
+TemplateArrays template_arrays(const cs_ctx *c) {
+    TemplateArrays ta{};
+    ta.mean_op = c->d_mean_op;
+    ta.cov_a = c->d_cov_a;
+    ta.cov_b = c->d_cov_b;
+    ta.skin_w = c->d_skin_w;
+    ta.skin_i = c->d_skin_i;
+    ta.sh = c->d_sh;
+    ta.lod_idx = c->d_lod_idx;
+    ta.qa = c->d_qa;
+    ta.qb = c->d_qb;
+    ta.sh16 = c->d_sh16;
+    ta.storage = c->storage;
+    return ta;
+}
+
+// Round to BF16 / FP16 (nearest, ties to even) and return the bits.
+uint32_t bf16_bits(float v) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+float bf16_value(uint32_t bits) {
+    uint32_t u = bits << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+uint32_t f16_bits(float v) { return (uint32_t)__half_as_ushort(__float2half_rn(v)); }
 
 int push_templates(cs_ctx *ctx) {
     const size_t ni = ctx->lod_idx_host.size();
@@ -318,6 +352,11 @@ int cs_create(cs_ctx **out, const cs_create_params *p) {
     ctx->sh_frame = p->sh_frame;
     ctx->instance_cull = p->instance_cull ? 1 : 0;
     ctx->stage_timing = p->stage_timing ? 1 : 0;
+    if (p->template_storage != CS_STORE_FP32 && p->template_storage != CS_STORE_BF16) {
+        delete ctx;
+        return CS_ERR_ARG;
+    }
+    ctx->storage = p->template_storage;
     ctx->lod.n_levels = 1;
     for (int l = 0; l < kMaxLevels; ++l) ctx->lod.mult[l] = 1.0f;
     int rc = CS_OK;
@@ -483,10 +522,110 @@ int cs_upload_templates(cs_ctx *ctx, int32_t n_templates, const cs_template_desc
             }
         }
     }
+    // BF16 storage: quantise the staged attributes (CS_STORE_BF16 in the header)
+    std::vector<uint4> qa, qb, sh16;
+    size_t planes16_total = 0;
+    if (ctx->storage == CS_STORE_BF16) {
+        qa.resize(g_total);
+        qb.resize(g_total);
+        for (int t = 0; t < n_templates; ++t) {
+            TemplateInfo &T = info[t];
+            const int K = (T.sh_deg + 1) * (T.sh_deg + 1);
+            T.sh_planes = (K * 3 + 7) / 8;
+            T.sh_off = (int64_t)planes16_total;
+            planes16_total += (size_t)T.sh_planes * (size_t)T.n;
+        }
+        sh16.assign(planes16_total, make_uint4(0u, 0u, 0u, 0u));
+        for (int t = 0; t < n_templates; ++t) {
+            const cs_template_desc &d = tp[t];
+            TemplateInfo &T = info[t];
+            const int K = (d.sh_degree + 1) * (d.sh_degree + 1);
+            double chain[kJoints];
+            for (int j = 0; j < kJoints; ++j) {
+                const int p = T.parent[j];
+                if (p < 0) { chain[j] = 0.0; continue; }
+                const double dx = T.rest[j * 3] - T.rest[p * 3], dy = T.rest[j * 3 + 1] - T.rest[p * 3 + 1],
+                             dz = T.rest[j * 3 + 2] - T.rest[p * 3 + 2];
+                chain[j] = chain[p] + std::sqrt(dx * dx + dy * dy + dz * dz);
+            }
+            const double pel = std::sqrt((double)T.rest[0] * T.rest[0] + (double)T.rest[1] * T.rest[1] +
+                                         (double)T.rest[2] * T.rest[2]);
+            for (int g = 0; g < d.n_gauss; ++g) {
+                const size_t gi = (size_t)T.g_off + g;
+                const double m[3] = {d.means[g * 3], d.means[g * 3 + 1], d.means[g * 3 + 2]};
+                int js[4];
+                float ws[4];
+                for (int k = 0; k < 4; ++k) {
+                    js[k] = d.skin_idx[g * 4 + k];
+                    ws[k] = d.skin_w[g * 4 + k];
+                }
+                // anchor: the skinning joint nearest to the mean goes to slot 0
+                int best = 0;
+                double bd = INFINITY;
+                for (int k = 0; k < 4; ++k) {
+                    const int j = js[k];
+                    const double dx = m[0] - T.rest[j * 3], dy = m[1] - T.rest[j * 3 + 1], dz = m[2] - T.rest[j * 3 + 2];
+                    const double dd = dx * dx + dy * dy + dz * dz;
+                    if (dd < bd) { bd = dd; best = k; }
+                }
+                std::swap(js[0], js[best]);
+                std::swap(ws[0], ws[best]);
+                const int a = js[0];
+                uint32_t db[3];
+                float mq[3];  // the mean the kernels reconstruct (FP32 add)
+                for (int e = 0; e < 3; ++e) {
+                    db[e] = bf16_bits((float)(m[e] - (double)T.rest[a * 3 + e]));
+                    mq[e] = T.rest[a * 3 + e] + bf16_value(db[e]);
+                }
+                const float4 ca = cov_a[gi];
+                const float2 cb = cov_b[gi];
+                const uint32_t ob = bf16_bits(d.opacity[g]);
+                uint32_t wb[4];
+                double wsum = 0.0, r = 0.0;
+                uint32_t packed = 0;
+                for (int k = 0; k < 4; ++k) {
+                    wb[k] = bf16_bits(ws[k]);
+                    const double wq = bf16_value(wb[k]);
+                    wsum += wq;
+                    packed |= (uint32_t)js[k] << (8 * k);
+                    const int j = js[k];
+                    const double dx = mq[0] - T.rest[j * 3], dy = mq[1] - T.rest[j * 3 + 1], dz = mq[2] - T.rest[j * 3 + 2];
+                    if (wq > 0.0) r = std::max(r, std::sqrt(dx * dx + dy * dy + dz * dz) + chain[j]);
+                }
+                qa[gi] = make_uint4(db[0] | (db[1] << 16), db[2] | (ob << 16), bf16_bits(ca.x) | (bf16_bits(ca.y) << 16),
+                                    bf16_bits(ca.z) | (bf16_bits(ca.w) << 16));
+                qb[gi] = make_uint4(bf16_bits(cb.x) | (bf16_bits(cb.y) << 16), wb[0] | (wb[1] << 16),
+                                    wb[2] | (wb[3] << 16), packed);
+                // cull bounds from the quantised values; the split-BF16 blend
+                // and the rounded covariance add small margins
+                reach[t][g] = (float)((r + std::fabs(wsum - 1.0) * (pel + r)) * wsum + 1e-4);
+                smax[t][g] = (float)(smax[t][g] * 1.01 * std::max(1.0, wsum));
+                const float *shg = d.sh + (size_t)g * K * 3;
+                for (int pl = 0; pl < T.sh_planes; ++pl) {
+                    uint32_t h[8];
+                    for (int e = 0; e < 8; ++e) {
+                        const int f = pl * 8 + e;
+                        h[e] = f16_bits(f < K * 3 ? shg[f] : 0.0f);
+                    }
+                    sh16[(size_t)T.sh_off + (size_t)pl * T.n + g] =
+                        make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+                }
+            }
+        }
+    }
     // device copies
     CS_CUDA(cudaStreamSynchronize(ctx->stream));
     free_templates(ctx);
     CS_CUDA(cudaMalloc(&ctx->d_tpl, sizeof(TemplateInfo) * n_templates));
+    if (ctx->storage == CS_STORE_BF16) {
+        CS_CUDA(cudaMalloc(&ctx->d_qa, sizeof(uint4) * g_total));
+        CS_CUDA(cudaMalloc(&ctx->d_qb, sizeof(uint4) * g_total));
+        CS_CUDA(cudaMalloc(&ctx->d_sh16, sizeof(uint4) * std::max<size_t>(planes16_total, 1)));
+        CS_CUDA(cudaMemcpy(ctx->d_qa, qa.data(), sizeof(uint4) * g_total, cudaMemcpyHostToDevice));
+        CS_CUDA(cudaMemcpy(ctx->d_qb, qb.data(), sizeof(uint4) * g_total, cudaMemcpyHostToDevice));
+        CS_CUDA(cudaMemcpy(ctx->d_sh16, sh16.data(), sizeof(uint4) * planes16_total, cudaMemcpyHostToDevice));
+        planes_total = planes16_total;
+    } else {
     CS_CUDA(cudaMalloc(&ctx->d_mean_op, sizeof(float4) * g_total));
     CS_CUDA(cudaMalloc(&ctx->d_cov_a, sizeof(float4) * g_total));
     CS_CUDA(cudaMalloc(&ctx->d_cov_b, sizeof(float2) * g_total));
@@ -499,6 +638,7 @@ int cs_upload_templates(cs_ctx *ctx, int32_t n_templates, const cs_template_desc
     CS_CUDA(cudaMemcpy(ctx->d_skin_w, skin_w.data(), sizeof(float4) * g_total, cudaMemcpyHostToDevice));
     CS_CUDA(cudaMemcpy(ctx->d_skin_i, skin_i.data(), sizeof(uint32_t) * g_total, cudaMemcpyHostToDevice));
     CS_CUDA(cudaMemcpy(ctx->d_sh, sh.data(), sizeof(float4) * planes_total, cudaMemcpyHostToDevice));
+    }
     ctx->n_tpl = n_templates;
     ctx->tpl_host = info;
     ctx->lod_sub.assign(n_templates, {});
@@ -678,8 +818,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->bins_sorted, Sa, "bin words in depth order"));
     CS_TRY(ensure(ctx, ctx->pair_off, Sa + 1, "pair offsets"));
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Sa), scan_scratch_words(Sa + 1)), "scratch"));
-    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh,
-                      ctx->d_lod_idx};
+    const TemplateArrays ta = template_arrays(ctx);
     if (S > 0)
         launched += launch_project(proj_blocks, ctx->groups.p, ctx->n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                        ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
@@ -785,8 +924,7 @@ int cs_lod_features(cs_ctx *ctx, float *feat_out) {
     if (!feat_out || (reinterpret_cast<uintptr_t>(feat_out) & 15u))
         return fail(ctx, CS_ERR_ARG, "feat_out must be a 16-byte aligned device pointer");
     CS_CUDA(cudaSetDevice(ctx->device));
-    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh,
-                      ctx->d_lod_idx};
+    const TemplateArrays ta = template_arrays(ctx);
     launch_lod_features((int)ctx->n_gauss_total, ctx->n_tpl, ctx->d_tpl, ta, feat_out, ctx->stream);
     CS_CUDA(cudaGetLastError());
     return CS_OK;
@@ -894,8 +1032,10 @@ int cs_get_stage_times(cs_ctx *ctx, float *ms, int32_t n, int32_t average, int64
 
 int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
     if (!ctx || !out) return CS_ERR_ARG;
-    int64_t tb = (int64_t)ctx->n_gauss_total * (sizeof(float4) * 3 + sizeof(float2) + sizeof(uint32_t)) +
-                 (int64_t)ctx->sh_planes_total * sizeof(float4) + (int64_t)ctx->n_tpl * sizeof(TemplateInfo) +
+    const int64_t per_g = ctx->storage == CS_STORE_BF16 ? (int64_t)(2 * sizeof(uint4))
+                                                       : (int64_t)(sizeof(float4) * 3 + sizeof(float2) + sizeof(uint32_t));
+    int64_t tb = (int64_t)ctx->n_gauss_total * per_g + (int64_t)ctx->sh_planes_total * 16 +
+                 (int64_t)ctx->n_tpl * sizeof(TemplateInfo) +
                  (int64_t)ctx->lod_idx_cap * sizeof(uint32_t);
     int64_t ib = bytes_of(ctx->tid) + bytes_of(ctx->vis) + bytes_of(ctx->root) + bytes_of(ctx->pose) +
                  bytes_of(ctx->B) + bytes_of(ctx->V) + bytes_of(ctx->Cloc) + bytes_of(ctx->groups);
@@ -1085,8 +1225,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     if ((size_t)S > kStaticSplats)
         return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: %lld splats exceed the static limit of %zu",
                     (long long)S, kStaticSplats);
-    TemplateArrays ta{ctx->d_mean_op, ctx->d_cov_a, ctx->d_cov_b, ctx->d_skin_w, ctx->d_skin_i, ctx->d_sh,
-                      ctx->d_lod_idx};
+    const TemplateArrays ta = template_arrays(ctx);
     if (S > 0)
         launched += launch_project(proj_blocks, ctx->groups.p, n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                                    ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,

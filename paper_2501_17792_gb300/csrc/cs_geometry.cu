@@ -311,12 +311,162 @@ __device__ __forceinline__ void sh_colour(const float4 *__restrict__ sh, int64_t
     rgb[2] = fmaxf(b + 0.5f, 0.0f);
 }
 
+// The same with FP16 coefficient planes of 8 (BF16 template storage).
+template <int DEG>
+__device__ __forceinline__ void sh_colour16(const uint4 *__restrict__ sh, int64_t base, int n,
+                                            float dx, float dy, float dz, float rgb[3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int P = (K * 3 + 7) / 8;
+    float Y[16];
+    sh_basis(DEG, dx, dy, dz, Y);
+    float c[P * 8];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const uint4 v = __ldg(sh + base + (int64_t)p * n);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[e]));
+            c[p * 8 + 2 * e] = f.x;
+            c[p * 8 + 2 * e + 1] = f.y;
+        }
+    }
+    float r = 0.f, g = 0.f, b = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        r += Y[k] * c[k * 3 + 0];
+        g += Y[k] * c[k * 3 + 1];
+        b += Y[k] * c[k * 3 + 2];
+    }
+    rgb[0] = fmaxf(r + 0.5f, 0.0f);
+    rgb[1] = fmaxf(g + 0.5f, 0.0f);
+    rgb[2] = fmaxf(b + 0.5f, 0.0f);
+}
+
 constexpr int kProjThreads = 256;
+
+// ---------------------------------------------------------------------------
+// LBS blend on the tensor cores (BF16 template storage).  For the CTA's 256
+// Gaussians of one instance, M[256 x 12] = W[256 x 32] Bt^T, W the dense
+// skinning weights (joints 24..31 zero) and Bt[12 x 32] the instance's 24
+// skinning transforms (row e = matrix entry e of every joint).  The weights
+// are BF16 as stored, so W is exact in BF16; the transforms are split into
+// BF16 hi + lo parts (split-BF16: W Bt_hi^T + W Bt_lo^T; the third product
+// of bf16x3, W_lo Bt_hi^T, vanishes because W_lo = 0), accumulated in FP32
+// by mma.sync m16n8k16, then divided by the sum of the four weights.  Fragment layout of mma.m16n8k16 with lane =
+// 4 g + q: A regs {A[g][2q..], A[g+8][2q..], A[g][2q+8..], A[g+8][2q+8..]},
+// B regs {B[2q..][g], B[2q+8..][g]}, C {C[g][2q], C[g][2q+1], C[g+8][2q],
+// C[g+8][2q+1]}.  Every thread of the CTA must call it.
+// ---------------------------------------------------------------------------
+constexpr int kTcLd = 40;  // bf16 row stride of W and Bt (80 B: conflict-free fragment loads)
+constexpr int kTcMld = 13; // float row stride of the result
+constexpr int kSkinTcBytes = (kProjThreads * kTcLd + 2 * 16 * kTcLd) * 2;  // 23,040 B
+static_assert(kProjThreads * kTcMld * 4 <= kProjThreads * kTcLd * 2, "result aliases W");
+
+__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ void skin_blend_tc(const float4 *__restrict__ sB, const float w_in[4], uint32_t joints, bool valid,
+                              unsigned char *__restrict__ smem, float M[12]) {
+    __nv_bfloat16 *sW = reinterpret_cast<__nv_bfloat16 *>(smem);
+    __nv_bfloat16 *sBh = sW + kProjThreads * kTcLd;
+    __nv_bfloat16 *sBl = sBh + 16 * kTcLd;
+    float *sM = reinterpret_cast<float *>(smem);
+    const int t = threadIdx.x;
+    // this thread's row of W: zeros, then its weights (a repeated joint adds up)
+    {
+        uint4 *row = reinterpret_cast<uint4 *>(sW + t * kTcLd);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) row[i] = make_uint4(0u, 0u, 0u, 0u);
+        float wk[4] = {w_in[0], w_in[1], w_in[2], w_in[3]};
+        int jk[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) jk[k] = (joints >> (8 * k)) & 0xFF;
+#pragma unroll
+        for (int k = 1; k < 4; ++k)
+#pragma unroll
+            for (int k2 = 0; k2 < k; ++k2)
+                if (jk[k] >= 0 && jk[k2] == jk[k]) {
+                    wk[k2] += wk[k];
+                    jk[k] = -1;
+                }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (valid && jk[k] >= 0 && jk[k] < kJoints) sW[t * kTcLd + jk[k]] = __float2bfloat16_rn(wk[k]);
+    }
+    // Bt hi and lo: entry e of joint j, zero beyond 12 entries and 24 joints
+    for (int i = t; i < 16 * 32; i += kProjThreads) {
+        const int e = i >> 5, j = i & 31;
+        float v = 0.0f;
+        if (e < 12 && j < kJoints) {
+            const float4 b = sB[j * 3 + (e >> 2)];
+            const int c = e & 3;
+            v = c == 0 ? b.x : (c == 1 ? b.y : (c == 2 ? b.z : b.w));
+        }
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        sBh[e * kTcLd + j] = hi;
+        sBl[e * kTcLd + j] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+    __syncthreads();
+    const int warp = t >> 5, lane = t & 31, g = lane >> 2, q = lane & 3;
+    float acc[2][2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const int r0 = 32 * warp + 16 * mt;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            const __nv_bfloat16 *ap = sW + (r0 + g) * kTcLd + 16 * kk + 2 * q;
+            const uint32_t a[4] = {lds32(ap), lds32(ap + 8 * kTcLd), lds32(ap + 8), lds32(ap + 8 * kTcLd + 8)};
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                const int bo = (8 * nt + g) * kTcLd + 16 * kk + 2 * q;
+                mma_bf16_16816(acc[mt][nt], a, lds32(sBh + bo), lds32(sBh + bo + 8));
+                mma_bf16_16816(acc[mt][nt], a, lds32(sBl + bo), lds32(sBl + bo + 8));
+            }
+        }
+    }
+    __syncthreads();  // W and Bt consumed: the result overwrites W
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int r = 32 * warp + 16 * mt + g, c = 8 * nt + 2 * q;
+            if (c < 12) {
+                sM[r * kTcMld + c] = acc[mt][nt][0];
+                sM[(r + 8) * kTcMld + c] = acc[mt][nt][2];
+            }
+            if (c + 1 < 12) {
+                sM[r * kTcMld + c + 1] = acc[mt][nt][1];
+                sM[(r + 8) * kTcMld + c + 1] = acc[mt][nt][3];
+            }
+        }
+    __syncthreads();
+    // BF16 weights need not sum to 1: normalise the blend, so that the root
+    // transform applied afterwards stays rigid
+    const float wsum = w_in[0] + w_in[1] + w_in[2] + w_in[3];
+    const float iw = wsum > 0.0f ? 1.0f / wsum : 0.0f;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) M[e] = sM[t * kTcMld + e] * iw;
+}
 
 // One CTA per (visible instance, 256 Gaussians of its level): the CTA
 // stages the instance's 24 skinning transforms in shared memory; thread t
 // handles Gaussian chunk * 256 + t.  Splat ids are dense, grouped by
 // (template, level), instance-major within a group.
+template <int kStore>
 __global__ void __launch_bounds__(kProjThreads, 4) k_project(
     const Group *__restrict__ groups, int n_groups, const int32_t *__restrict__ vis,
     const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ Cloc,
@@ -326,6 +476,7 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(
     uint32_t *__restrict__ bin) {
     __shared__ float4 sB[kJoints * 3];
     __shared__ int s_group;
+    __shared__ __align__(16) unsigned char s_tc[kStore == kStoreBf16 ? kSkinTcBytes : 16];
     if (threadIdx.x == 0) {
         // group whose CTA range holds this CTA: last group with block0 <= blockIdx.x
         int lo = 0, hi = n_groups - 1;
@@ -348,20 +499,38 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(
     }
     __syncthreads();
     const int gg = chunk * kProjThreads + threadIdx.x;
-    if (gg >= G.ng) return;
+    const bool valid = gg < G.ng;
+    // the tensor-core blend needs every thread of the CTA
+    if (kStore == kStoreFp32 && !valid) return;
     const int s = G.splat0 + islot * G.ng + gg;
     const TemplateInfo &T = tpls[G.tpl];
     // the level's Gaussians: a prefix of the template, or a chosen subset
-    const int sub = T.lod_idx_off[G.lvl];
-    const int gsrc = sub >= 0 ? (int)__ldg(ta.lod_idx + sub + gg) : gg;
-    const int gi = T.g_off + gsrc;
-    ids[s] = (uint32_t)s;
+    int gsrc = 0, gi = 0;
+    if (valid) {
+        const int sub = T.lod_idx_off[G.lvl];
+        gsrc = sub >= 0 ? (int)__ldg(ta.lod_idx + sub + gg) : gg;
+        gi = T.g_off + gsrc;
+        ids[s] = (uint32_t)s;
+    }
 
     // LBS (CrowdSplat Sec. 2): M = sum_k w_k B_{idx_k} (instance local)
-    const float4 w = __ldg(ta.skin_w + gi);
-    const uint32_t packed = __ldg(ta.skin_i + gi);
     float M[12];
-    {
+    float4 mo;        // mean (template local), opacity
+    float cv[6];      // canonical covariance xx, xy, xz, yy, yz, zz (BF16 storage)
+    if constexpr (kStore == kStoreBf16) {
+        const uint4 qa = valid ? __ldg(ta.qa + gi) : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 qb = valid ? __ldg(ta.qb + gi) : make_uint4(0u, 0u, 0u, 0u);
+        const float wq[4] = {bf16_lo(qb.y), bf16_hi(qb.y), bf16_lo(qb.z), bf16_hi(qb.z)};
+        skin_blend_tc(sB, wq, qb.w, valid, s_tc, M);
+        if (!valid) return;
+        const int j0 = qb.w & 0xFF;
+        mo = make_float4(T.rest[j0 * 3] + bf16_lo(qa.x), T.rest[j0 * 3 + 1] + bf16_hi(qa.x),
+                         T.rest[j0 * 3 + 2] + bf16_lo(qa.y), bf16_hi(qa.y));
+        cv[0] = bf16_lo(qa.z); cv[1] = bf16_hi(qa.z); cv[2] = bf16_lo(qa.w); cv[3] = bf16_hi(qa.w);
+        cv[4] = bf16_lo(qb.x); cv[5] = bf16_hi(qb.x);
+    } else {
+        const float4 w = __ldg(ta.skin_w + gi);
+        const uint32_t packed = __ldg(ta.skin_i + gi);
         const float wk[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int e = 0; e < 12; ++e) M[e] = 0.0f;
@@ -373,8 +542,8 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(
             M[4] += wk[k] * b1.x; M[5] += wk[k] * b1.y; M[6] += wk[k] * b1.z; M[7] += wk[k] * b1.w;
             M[8] += wk[k] * b2.x; M[9] += wk[k] * b2.y; M[10] += wk[k] * b2.z; M[11] += wk[k] * b2.w;
         }
+        mo = __ldg(ta.mean_op + gi);
     }
-    const float4 mo = __ldg(ta.mean_op + gi);
     const float lx = M[0] * mo.x + M[1] * mo.y + M[2] * mo.z + M[3];
     const float ly = M[4] * mo.x + M[5] * mo.y + M[6] * mo.z + M[7];
     const float lz = M[8] * mo.x + M[9] * mo.y + M[10] * mo.z + M[11];
@@ -404,8 +573,15 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(
             W[3] = v1.x; W[4] = v1.y; W[5] = v1.z;
             W[6] = v2.x; W[7] = v2.y; W[8] = v2.z;
         }
-        const float4 ca = __ldg(ta.cov_a + gi);
-        const float2 cb = __ldg(ta.cov_b + gi);
+        float4 ca;
+        float2 cb;
+        if constexpr (kStore == kStoreBf16) {
+            ca = make_float4(cv[0], cv[1], cv[2], cv[3]);
+            cb = make_float2(cv[4], cv[5]);
+        } else {
+            ca = __ldg(ta.cov_a + gi);
+            cb = __ldg(ta.cov_b + gi);
+        }
         const float m = lod.mult[G.lvl];
         const float m2 = m * m;
         const float S0 = ca.x * m2, S1 = ca.y * m2, S2 = ca.z * m2, S3 = ca.w * m2, S4 = cb.x * m2,
@@ -499,11 +675,20 @@ __global__ void __launch_bounds__(kProjThreads, 4) k_project(
                 ddx *= inv; ddy *= inv; ddz *= inv;
                 float rgb[3];
                 const int64_t base = T.sh_off + gsrc;
-                switch (T.sh_deg) {
-                    case 0: sh_colour<0>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
-                    case 1: sh_colour<1>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
-                    case 2: sh_colour<2>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
-                    default: sh_colour<3>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                if constexpr (kStore == kStoreBf16) {
+                    switch (T.sh_deg) {
+                        case 0: sh_colour16<0>(ta.sh16, base, T.n, ddx, ddy, ddz, rgb); break;
+                        case 1: sh_colour16<1>(ta.sh16, base, T.n, ddx, ddy, ddz, rgb); break;
+                        case 2: sh_colour16<2>(ta.sh16, base, T.n, ddx, ddy, ddz, rgb); break;
+                        default: sh_colour16<3>(ta.sh16, base, T.n, ddx, ddy, ddz, rgb); break;
+                    }
+                } else {
+                    switch (T.sh_deg) {
+                        case 0: sh_colour<0>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                        case 1: sh_colour<1>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                        case 2: sh_colour<2>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                        default: sh_colour<3>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                    }
                 }
                 float4 *ro = rec + (size_t)s * kRecVec;
                 ro[0] = make_float4(u, v, cA, cB);
@@ -526,9 +711,12 @@ int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_
                     const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
                     uint32_t *ids, uint2 *rect, uint32_t *bin, cudaStream_t st) {
     if (n_blocks <= 0) return 0;
-    k_project<<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, vis, B, V, Cloc, root, ta,
-                                                tpls, cam, lod, skin_mode, sh_frame, rec, key, ids,
-                                                rect, bin);
+    if (ta.storage == kStoreBf16)
+        k_project<kStoreBf16><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, vis, B, V, Cloc, root, ta, tpls,
+                                                                cam, lod, skin_mode, sh_frame, rec, key, ids, rect, bin);
+    else
+        k_project<kStoreFp32><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, vis, B, V, Cloc, root, ta, tpls,
+                                                                cam, lod, skin_mode, sh_frame, rec, key, ids, rect, bin);
     return 1;
 }
 

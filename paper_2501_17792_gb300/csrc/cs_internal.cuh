@@ -11,6 +11,8 @@
 //   sh          float4 planes: plane p of Gaussian k of template t at
 //               sh[t.sh_off + p * t.n + k]; plane p holds the flat SH
 //               coefficients 4p..4p+3 of that Gaussian (flat = k*3 + channel)
+// With BF16 storage (TemplateArrays::storage) the same attributes sit in
+// two 16-byte words per Gaussian (qa, qb) and FP16 SH planes of 8.
 // Per instance: B[i][24][12] instance-local skinning transforms (root not
 // applied), V[i][12] = camera o root (3x4), C[i][4] = camera centre in the
 // instance root frame.
@@ -26,6 +28,8 @@
 // window's tile origin and a 9-bit mask, x0 | y0 << 8 | mask << 16; larger
 // ones store kBinLarge | count and are re-tested from their record.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,7 +56,7 @@ struct TemplateInfo {
     int32_t n;          // Gaussians
     int32_t sh_deg;     // 0..3
     int32_t sh_planes;  // float4 planes per Gaussian
-    int64_t sh_off;     // float4 offset of plane 0
+    int64_t sh_off;     // offset of SH plane 0 (float4 planes, or uint4 FP16 planes with BF16 storage)
     int32_t n_level[kMaxLevels];   // Gaussians rendered at each level
     float reach[kMaxLevels];       // bound of |posed local mean - pelvis rest| per level
     float sigma_max[kMaxLevels];   // largest scale x level multiplier per level
@@ -90,15 +94,31 @@ struct LodParams {
     float mult[kMaxLevels];
 };
 
+constexpr int kStoreFp32 = 0, kStoreBf16 = 1;  // CS_STORE_FP32 / CS_STORE_BF16
+
 struct TemplateArrays {
+    // FP32 storage (CS_STORE_FP32)
     const float4 *mean_op;
     const float4 *cov_a;
     const float2 *cov_b;
     const float4 *skin_w;
     const uint32_t *skin_i;
-    const float4 *sh;
+    const float4 *sh;         // planes of 4 coefficients, TemplateInfo sh_off / sh_planes
     const uint32_t *lod_idx;  // template-local Gaussian indices of subset levels
+    // BF16 storage (CS_STORE_BF16): two 16-byte words per Gaussian
+    //   qa = bf16 {dx, dy, dz, opacity, cxx, cxy, cxz, cyy}, (dx, dy, dz) the
+    //        mean minus the rest position of the Gaussian's first skinning joint
+    //   qb = bf16 {cyz, czz, w0, w1, w2, w3}, then the four joint ids (bytes)
+    // and FP16 SH planes of 8 coefficients (sh_off / sh_planes count these)
+    const uint4 *qa;
+    const uint4 *qb;
+    const uint4 *sh16;
+    int storage;  // CS_STORE_FP32 or CS_STORE_BF16
 };
+
+// BF16 halves of a 32-bit word, widened exactly to FP32
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
 
 // ---------------------------------------------------------------------------
 // Exact (conservative) splat-rectangle test shared by binning and blending.

@@ -49,6 +49,7 @@ __device__ void sym3_eigenvalues(double a00, double a01, double a02, double a11,
     ev[2] = e3;
 }
 
+template <int kStore>
 __global__ void __launch_bounds__(256) k_lod_features(int n_total, int n_tpl, const TemplateInfo *__restrict__ tpls,
                                                       TemplateArrays ta, float *__restrict__ feat) {
     __shared__ int32_t s_off[kMaxTemplates];
@@ -60,9 +61,26 @@ __global__ void __launch_bounds__(256) k_lod_features(int n_total, int n_tpl, co
     const TemplateInfo &T = tpls[t];
     const int gl = g - T.g_off;
     float f[kLodFeatures];
-    const float4 mo = ta.mean_op[g];
-    const float4 ca = ta.cov_a[g];   // xx, xy, xz, yy
-    const float2 cb = ta.cov_b[g];   // yz, zz
+    // attributes as stored (BF16 storage: widened to FP32)
+    float4 mo, ca, w;  // mean + opacity; covariance xx, xy, xz, yy; skinning weights
+    float2 cb;         // covariance yz, zz
+    uint32_t si;       // joint ids
+    if constexpr (kStore == kStoreBf16) {
+        const uint4 qa = ta.qa[g], qb = ta.qb[g];
+        const int j0 = qb.w & 0xFF;
+        mo = make_float4(T.rest[j0 * 3] + bf16_lo(qa.x), T.rest[j0 * 3 + 1] + bf16_hi(qa.x),
+                         T.rest[j0 * 3 + 2] + bf16_lo(qa.y), bf16_hi(qa.y));
+        ca = make_float4(bf16_lo(qa.z), bf16_hi(qa.z), bf16_lo(qa.w), bf16_hi(qa.w));
+        cb = make_float2(bf16_lo(qb.x), bf16_hi(qb.x));
+        w = make_float4(bf16_lo(qb.y), bf16_hi(qb.y), bf16_lo(qb.z), bf16_hi(qb.z));
+        si = qb.w;
+    } else {
+        mo = ta.mean_op[g];
+        ca = ta.cov_a[g];
+        cb = ta.cov_b[g];
+        w = ta.skin_w[g];
+        si = ta.skin_i[g];
+    }
     double ev[3];
     sym3_eigenvalues(ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, ev);
     double ls[3];
@@ -79,9 +97,16 @@ __global__ void __launch_bounds__(256) k_lod_features(int n_total, int n_tpl, co
     // colour: SH planes hold coefficient k, channel c at flat index 3k + c
     auto coeff = [&](int k, int c) -> double {
         const int fi = 3 * k + c;
-        const float4 pl = ta.sh[T.sh_off + (int64_t)(fi >> 2) * T.n + gl];
-        const int e = fi & 3;
-        return e == 0 ? pl.x : e == 1 ? pl.y : e == 2 ? pl.z : pl.w;
+        if constexpr (kStore == kStoreBf16) {
+            const uint4 pl = ta.sh16[T.sh_off + (int64_t)(fi >> 3) * T.n + gl];
+            const int e = fi & 7;
+            const uint32_t wd = (e >> 1) == 0 ? pl.x : (e >> 1) == 1 ? pl.y : (e >> 1) == 2 ? pl.z : pl.w;
+            return (double)__half2float(__ushort_as_half((unsigned short)(e & 1 ? wd >> 16 : wd & 0xFFFFu)));
+        } else {
+            const float4 pl = ta.sh[T.sh_off + (int64_t)(fi >> 2) * T.n + gl];
+            const int e = fi & 3;
+            return e == 0 ? pl.x : e == 1 ? pl.y : e == 2 ? pl.z : pl.w;
+        }
     };
     double dc[3];
     for (int c = 0; c < 3; ++c) dc[c] = fmax(0.0, 0.28209479177387814 * coeff(0, c) + 0.5);
@@ -105,8 +130,6 @@ __global__ void __launch_bounds__(256) k_lod_features(int n_total, int n_tpl, co
     f[17] = mo.z;
     const double rx = mo.x - T.rest[0], rz = mo.z - T.rest[2];
     f[18] = (float)sqrt(rx * rx + rz * rz);
-    const float4 w = ta.skin_w[g];
-    const uint32_t si = ta.skin_i[g];
     float wv[4] = {w.x, w.y, w.z, w.w};
     int jv[4] = {(int)(si & 0xFF), (int)((si >> 8) & 0xFF), (int)((si >> 16) & 0xFF), (int)(si >> 24)};
     // sort the four weights, largest first (ties keep their slot order)
@@ -202,7 +225,10 @@ int launch_lod_targets(int n_total, int n_tpl, int n_bands, const TemplateInfo *
 int launch_lod_features(int n_total, int n_tpl, const TemplateInfo *tpls, const TemplateArrays &ta, float *feat,
                         cudaStream_t st) {
     if (n_total <= 0) return 0;
-    k_lod_features<<<(n_total + 255) / 256, 256, 0, st>>>(n_total, n_tpl, tpls, ta, feat);
+    if (ta.storage == kStoreBf16)
+        k_lod_features<kStoreBf16><<<(n_total + 255) / 256, 256, 0, st>>>(n_total, n_tpl, tpls, ta, feat);
+    else
+        k_lod_features<kStoreFp32><<<(n_total + 255) / 256, 256, 0, st>>>(n_total, n_tpl, tpls, ta, feat);
     return 1;
 }
 

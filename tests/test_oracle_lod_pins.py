@@ -182,3 +182,17 @@ def test_targets_closed_form():
     assert np.allclose(t[0, 3:], np.log(1.0 + 1e-3))
     assert np.allclose(t[1, :3], np.log(1e-3))                    # a template that never contributed
     assert np.allclose(t[1, 3:], np.log(np.array([5 / 3, 1 / 3]) + 1e-3))
+
+
+def test_features_from_a_direct_covariance_match_scales():
+    import dataclasses
+    t = S.make_template(78, 500, 1)
+    q = t.quats.astype(np.float64)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    import oracle as O
+    Rq = np.stack([O.quat_to_rot(x) for x in q])
+    C = np.einsum("nik,nk,njk->nij", Rq, t.scales.astype(np.float64) ** 2, Rq)
+    t2 = dataclasses.replace(t)
+    t2.cov = np.stack([C[:, 0, 0], C[:, 0, 1], C[:, 0, 2], C[:, 1, 1], C[:, 1, 2], C[:, 2, 2]], 1).astype(np.float32)
+    a, b = R.features(t), R.features(t2)
+    assert np.abs(a - b).max() < 1e-4
