@@ -1,7 +1,8 @@
 """Thin Python binding of libcrowdsplat.so (argument marshalling only).
 
-Every function of ``include/crowdsplat.h`` and ``include/crowdsplat_lod.h``
-is reachable under the same name through :func:`lib`; :class:`Renderer`
+Every function of ``include/crowdsplat.h``, ``include/crowdsplat_lod.h`` and
+``include/crowdsplat_grad.h`` is reachable under the same name through
+:func:`lib`; :class:`Renderer`
 wraps a render context and :class:`Mlp` the LoD ranking network, with
 PyTorch device memory and streams.  All computation runs in the library's CUDA kernels:
 there is no CPU path, and :func:`load` raises if the library is missing.
@@ -59,6 +60,11 @@ class FrameStats(C.Structure):
                     tiles_y=self.tiles_y, kernel_launches=self.kernel_launches)
 
 
+class Grads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity", C.c_void_p), ("sh", C.c_void_p), ("pose", C.c_void_p)]
+
+
 class MemoryStats(C.Structure):
     _fields_ = [("template_bytes", C.c_int64), ("instance_bytes", C.c_int64),
                 ("frame_bytes", C.c_int64), ("total_bytes", C.c_int64)]
@@ -96,6 +102,9 @@ SIGNATURES = {
     "cs_mlp_forward": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "cs_mlp_train_step": (C.c_int, [_P, C.c_int64, _P, _P, _P, C.c_float, C.POINTER(C.c_float)]),
     "cs_mlp_get_grad": (C.c_int, [_P, _P]),
+    # gradients (include/crowdsplat_grad.h)
+    "cs_render_train": (C.c_int, [_P, C.POINTER(Camera), _P, C.POINTER(FrameStats)]),
+    "cs_backward": (C.c_int, [_P, _P, C.POINTER(Grads)]),
 }
 
 LOD_FEATURES, MLP_PARAMS = 32, 48 * 64 + 64 + 64 * 64 + 64 + 64 + 1
@@ -271,6 +280,40 @@ class Renderer:
         self._check(self.L.cs_render_contrib(self.h, C.byref(cam), out.data_ptr(), contrib.data_ptr(),
                                              C.byref(st) if stats else None))
         return (out, st.as_dict()) if stats else out
+
+    def render_train(self, camera, out=None, stats: bool = False):
+        """Render and keep the state :meth:`backward` needs."""
+        torch = self.torch
+        cam = camera_struct(camera)
+        if out is None:
+            with torch.cuda.stream(self.stream):
+                out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32,
+                                  device=f"cuda:{self.device}")
+        st = FrameStats()
+        self._check(self.L.cs_render_train(self.h, C.byref(cam), out.data_ptr(), C.byref(st) if stats else None))
+        self._train_shape = (cam.height, cam.width)
+        return (out, st.as_dict()) if stats else out
+
+    def backward(self, dl_drgba, n_instances: int, grads: dict | None = None) -> dict:
+        """Gradients of the last :meth:`render_train` frame for dL/d(RGBA)
+        [H, W, 4] (CUDA float32).  Returns (and adds into, when given) CUDA
+        tensors means [N,3], scales [N,3], quats [N,4], opacity [N],
+        sh [N,16,3] and pose [I,24,3]."""
+        torch = self.torch
+        dev = f"cuda:{self.device}"
+        g = dl_drgba.to(device=dev, dtype=torch.float32).contiguous()
+        n = self.n_gauss_total
+        if grads is None:
+            with torch.cuda.stream(self.stream):
+                grads = dict(means=torch.zeros((n, 3), device=dev), scales=torch.zeros((n, 3), device=dev),
+                             quats=torch.zeros((n, 4), device=dev), opacity=torch.zeros(n, device=dev),
+                             sh=torch.zeros((n, 16, 3), device=dev),
+                             pose=torch.zeros((int(n_instances), 24, 3), device=dev))
+        cg = Grads(*(grads[k].data_ptr() if grads.get(k) is not None else None
+                     for k in ("means", "scales", "quats", "opacity", "sh", "pose")))
+        self._check(self.L.cs_backward(self.h, g.data_ptr(), C.byref(cg)))
+        self._keep_grad = g
+        return grads
 
     def render_to_host(self, camera, out: np.ndarray | None = None, stats: bool = False):
         cam = camera_struct(camera)

@@ -17,6 +17,7 @@
 
 #include "../../include/crowdsplat.h"
 #include "../../include/crowdsplat_lod.h"
+#include "../../include/crowdsplat_grad.h"
 #include "cs_internal.cuh"
 
 using namespace cs;
@@ -54,6 +55,7 @@ struct cs_ctx {
     float2 *d_cov_b = nullptr;
     uint32_t *d_skin_i = nullptr;
     uint4 *d_qa = nullptr, *d_qb = nullptr, *d_sh16 = nullptr;  // BF16 storage
+    float4 *d_scale = nullptr, *d_quat = nullptr;              // FP32 storage, for the backward
     size_t n_gauss_total = 0, sh_planes_total = 0;
     int max_depth = 0;
 
@@ -77,6 +79,13 @@ struct cs_ctx {
     DevBuf<uint16_t> ptile, ptile2;
     DevBuf<float4> img;  // for cs_render_to_host
     DevBuf<float> contrib_s;  // per-splat compositing weight sums (cs_render_contrib)
+    // training frame (cs_render_train / cs_backward)
+    DevBuf<uint32_t> px_end;
+    DevBuf<float> px_T, g_cov, g_B, g_dummy;
+    DevBuf<float4> dsplat;
+    bool train_valid = false;
+    CamParams train_cp{};
+    int train_proj_blocks = 0;
     // split compositing of long tile lists
     DevBuf<int32_t> bw_slot, bw_tile, bw_meta, bw_stop;
     DevBuf<uint32_t> bw_chunk0, bw_done;
@@ -169,6 +178,10 @@ void free_templates(cs_ctx *c) {
     cudaFree(c->d_skin_w);
     cudaFree(c->d_skin_i);
     cudaFree(c->d_sh);
+    cudaFree(c->d_scale);
+    cudaFree(c->d_quat);
+    c->d_scale = c->d_quat = nullptr;
+    c->train_valid = false;
     cudaFree(c->d_qa);
     cudaFree(c->d_qb);
     cudaFree(c->d_sh16);
@@ -232,6 +245,8 @@ TemplateArrays template_arrays(const cs_ctx *c) {
     ta.qb = c->d_qb;
     ta.sh16 = c->d_sh16;
     ta.storage = c->storage;
+    ta.scale = c->d_scale;
+    ta.quat = c->d_quat;
     return ta;
 }
 
@@ -389,6 +404,8 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->bins); release(ctx->bins_sorted); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
     release(ctx->scratch); release(ctx->rect); release(ctx->ranges); release(ctx->ptile);
     release(ctx->ptile2); release(ctx->img); release(ctx->contrib_s);
+    release(ctx->px_end); release(ctx->px_T); release(ctx->dsplat); release(ctx->g_cov); release(ctx->g_B);
+    release(ctx->g_dummy);
     release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_chunk0);
     release(ctx->bw_done); release(ctx->bw_state); release(ctx->bw_part);
     if (ctx->d_meta) cudaFree(ctx->d_meta);
@@ -626,6 +643,20 @@ int cs_upload_templates(cs_ctx *ctx, int32_t n_templates, const cs_template_desc
         CS_CUDA(cudaMemcpy(ctx->d_sh16, sh16.data(), sizeof(uint4) * planes16_total, cudaMemcpyHostToDevice));
         planes_total = planes16_total;
     } else {
+    {
+        std::vector<float4> sc(g_total), qt(g_total);
+        for (int t = 0; t < n_templates; ++t)
+            for (int g = 0; g < tp[t].n_gauss; ++g) {
+                const size_t gi = (size_t)info[t].g_off + g;
+                const float *s3 = tp[t].scales + (size_t)g * 3, *q4 = tp[t].quats + (size_t)g * 4;
+                sc[gi] = make_float4(s3[0], s3[1], s3[2], 0.0f);
+                qt[gi] = make_float4(q4[0], q4[1], q4[2], q4[3]);
+            }
+        CS_CUDA(cudaMalloc(&ctx->d_scale, sizeof(float4) * g_total));
+        CS_CUDA(cudaMalloc(&ctx->d_quat, sizeof(float4) * g_total));
+        CS_CUDA(cudaMemcpy(ctx->d_scale, sc.data(), sizeof(float4) * g_total, cudaMemcpyHostToDevice));
+        CS_CUDA(cudaMemcpy(ctx->d_quat, qt.data(), sizeof(float4) * g_total, cudaMemcpyHostToDevice));
+    }
     CS_CUDA(cudaMalloc(&ctx->d_mean_op, sizeof(float4) * g_total));
     CS_CUDA(cudaMalloc(&ctx->d_cov_a, sizeof(float4) * g_total));
     CS_CUDA(cudaMalloc(&ctx->d_cov_b, sizeof(float2) * g_total));
@@ -683,6 +714,7 @@ int cs_set_lod(cs_ctx *ctx, int32_t n_levels, const float *dist_thresh, const fl
         if (l < kMaxLevels - 1) ctx->lod.thresh[l] = l < n_levels - 1 ? dist_thresh[l] : INFINITY;
     }
     CS_CUDA(cudaSetDevice(ctx->device));
+    ctx->train_valid = false;
     refresh_lod_bounds(ctx);
     return push_templates(ctx);
 }
@@ -706,6 +738,7 @@ int cs_set_lod_subset(cs_ctx *ctx, int32_t template_id, int32_t level, int32_t n
     }
     CS_CUDA(cudaSetDevice(ctx->device));
     ctx->lod_sub[template_id][level] = std::move(sub);
+    ctx->train_valid = false;
     refresh_lod_bounds(ctx);
     return push_templates(ctx);
 }
@@ -739,11 +772,13 @@ int cs_set_instances(cs_ctx *ctx, int32_t n, const int32_t *template_id, const f
         CS_CUDA(cudaMemcpyAsync(ctx->pose.p, joint_pose, sizeof(float) * kJoints * 3 * n, kind, ctx->stream));
     }
     ctx->n_inst = n;
+    ctx->train_valid = false;
     return CS_OK;
 }
 
 static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_stats *stats,
-                       float *contrib_tmpl = nullptr) {
+                       float *contrib_tmpl = nullptr, bool train = false) {
+    ctx->train_valid = false;  // the frame buffers are about to be rewritten
     if (!cam || !out) return fail(ctx, CS_ERR_ARG, "NULL camera or output");
     if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(ctx, CS_ERR_ARG, "rgba_out must be 16-byte aligned");
     if (ctx->n_tpl == 0) return fail(ctx, CS_ERR_STATE, "no templates uploaded");
@@ -881,6 +916,13 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         CS_CUDA(cudaMemsetAsync(ctx->contrib_s.p, 0, Sa * sizeof(float), st));
         bw.contrib = ctx->contrib_s.p;
     }
+    if (train) {
+        const size_t npix = (size_t)cam->width * cam->height;
+        CS_TRY(ensure(ctx, ctx->px_end, npix, "per-pixel list ends"));
+        CS_TRY(ensure(ctx, ctx->px_T, npix, "per-pixel transmittance"));
+        bw.px_end = ctx->px_end.p;
+        bw.px_T = ctx->px_T.p;
+    }
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ctx->ranges.p, pval, ctx->rec.p, out,
                              bw, (uint32_t)P, st);
     if (contrib_tmpl)
@@ -891,6 +933,11 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     ctx->timed = timing;
     ctx->ev_pending[ctx->ev_cur] = timing;
     ctx->launches = launched;
+    if (train) {
+        ctx->train_valid = true;
+        ctx->train_cp = cp;
+        ctx->train_proj_blocks = proj_blocks;
+    }
     if (stats) {
         stats->instances = I;
         stats->instances_visible = ctx->visible;
@@ -973,6 +1020,78 @@ int cs_lod_rank(cs_ctx *ctx, const float *score, uint32_t *order_out) {
     return CS_OK;
 }
 
+int cs_render_train(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats) {
+    if (!ctx) return CS_ERR_ARG;
+    if (ctx->storage != CS_STORE_FP32) return fail(ctx, CS_ERR_STATE, "gradients need FP32 template storage");
+    return render_impl(ctx, cam, reinterpret_cast<float4 *>(rgba_out), stats, nullptr, true);
+}
+
+int cs_backward(cs_ctx *ctx, const float *dl_drgba, const cs_grads *grads) {
+    if (!ctx) return CS_ERR_ARG;
+    if (!dl_drgba || !grads || (reinterpret_cast<uintptr_t>(dl_drgba) & 15u))
+        return fail(ctx, CS_ERR_ARG, "NULL or misaligned dl_drgba / grads");
+    if (!ctx->train_valid) return fail(ctx, CS_ERR_STATE, "no training frame (cs_render_train) since the last change");
+    CS_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const CamParams &cp = ctx->train_cp;
+    const size_t S = (size_t)std::max<int64_t>(ctx->S, 1), G = std::max<size_t>(ctx->n_gauss_total, 1);
+    const size_t I = (size_t)std::max(ctx->n_inst, 1);
+    CS_TRY(ensure(ctx, ctx->dsplat, S * 3, "splat gradients"));
+    CS_TRY(ensure(ctx, ctx->g_cov, G * 6, "covariance gradients"));
+    CS_TRY(ensure(ctx, ctx->g_B, I * kJoints * 12, "skinning-transform gradients"));
+    // destinations the caller does not want go to one scratch buffer
+    CS_TRY(ensure(ctx, ctx->g_dummy, std::max(G * 48, I * kJoints * 3), "gradient scratch"));
+    CS_CUDA(cudaMemsetAsync(ctx->dsplat.p, 0, S * 3 * sizeof(float4), st));
+    CS_CUDA(cudaMemsetAsync(ctx->g_cov.p, 0, G * 6 * sizeof(float), st));
+    CS_CUDA(cudaMemsetAsync(ctx->g_B.p, 0, I * kJoints * 12 * sizeof(float), st));
+    BackwardArgs a{};
+    a.tiles_x = cp.tiles_x;
+    a.tiles_y = cp.tiles_y;
+    a.W = cp.W;
+    a.H = cp.H;
+    a.n_pairs = (uint32_t)ctx->P;
+    a.ranges = ctx->ranges.p;
+    a.pval = ctx->pair_buf ? ctx->pval2.p : ctx->pval.p;
+    a.rec = ctx->rec.p;
+    a.px_end = ctx->px_end.p;
+    a.px_T = ctx->px_T.p;
+    a.dl_drgba = reinterpret_cast<const float4 *>(dl_drgba);
+    a.dsplat = ctx->dsplat.p;
+    a.proj_blocks = ctx->S > 0 ? ctx->train_proj_blocks : 0;
+    a.groups = ctx->groups.p;
+    a.n_groups = ctx->n_groups;
+    a.vis = ctx->vis.p;
+    a.B = ctx->B.p;
+    a.V = ctx->V.p;
+    a.Cloc = ctx->Cloc.p;
+    a.root = ctx->root.p;
+    a.ta = template_arrays(ctx);
+    a.tpls = ctx->d_tpl;
+    a.cam = cp;
+    a.lod = ctx->lod;
+    a.skin_mode = ctx->skin_mode;
+    a.sh_frame = ctx->sh_frame;
+    float *dummy = ctx->g_dummy.p;
+    a.g_mean = grads->means ? grads->means : dummy;
+    a.g_cov = ctx->g_cov.p;
+    a.g_opacity = grads->opacity ? grads->opacity : dummy;
+    a.g_sh = grads->sh ? grads->sh : dummy;
+    a.g_B = ctx->g_B.p;
+    a.n_inst = ctx->n_inst;
+    a.n_tpl = ctx->n_tpl;
+    a.tid = ctx->tid.p;
+    a.pose = ctx->pose.p;
+    a.g_pose = grads->pose ? grads->pose : dummy;
+    a.n_gauss = (int)ctx->n_gauss_total;
+    a.scale = ctx->d_scale;
+    a.quat = ctx->d_quat;
+    a.g_scale = grads->scales ? grads->scales : dummy;
+    a.g_quat = grads->quats ? grads->quats : dummy;
+    launch_backward(a, st);
+    CS_CUDA(cudaGetLastError());
+    return CS_OK;
+}
+
 int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_frame_stats *stats) {
     if (!ctx) return CS_ERR_ARG;
     if (!cam || !rgba_host) return fail(ctx, CS_ERR_ARG, "NULL camera or output");
@@ -1044,7 +1163,9 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
                  bytes_of(ctx->pval2) + bytes_of(ctx->scratch) + bytes_of(ctx->rect) + bytes_of(ctx->ranges) +
                  bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img) + bytes_of(ctx->bw_slot) +
                  bytes_of(ctx->bw_tile) + bytes_of(ctx->bw_meta) + bytes_of(ctx->bw_chunk0) + bytes_of(ctx->bw_done) +
-                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop) + bytes_of(ctx->contrib_s);
+                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop) + bytes_of(ctx->contrib_s) +
+                 bytes_of(ctx->px_end) + bytes_of(ctx->px_T) + bytes_of(ctx->dsplat) + bytes_of(ctx->g_cov) +
+                 bytes_of(ctx->g_B) + bytes_of(ctx->g_dummy);
     out->template_bytes = tb;
     out->instance_bytes = ib;
     out->frame_bytes = fb;

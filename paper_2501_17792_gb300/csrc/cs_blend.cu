@@ -36,7 +36,7 @@
 namespace cs {
 
 constexpr int kBlendThreads = kTile * kTile;
-constexpr int kBlockW = 8, kBlockH = 4;  // pixels per warp
+constexpr int kBlockW = kBlendBlockW, kBlockH = kBlendBlockH;  // pixels per warp
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr uint32_t kBudget = kBlendBudget;  // pairs of pass 1 per tile
 constexpr uint32_t kChunk = kBlendChunk;    // pairs per pass-2 chunk
@@ -79,14 +79,16 @@ struct BlendShared {
 
 struct Pixel {
     float T, r, g, b;
+    uint32_t last;  // one past the last composited pair (training forward)
     bool done;     // saturated, outside the image, or not composited here
     bool stopped;  // met the stop rule in this call
 };
 
 // Composite pairs [start, end) of a tile into the calling thread's pixel.
-// Every thread of the CTA must call it with the same range.  kStats: also
-// add each composited weight alpha * T to contrib[splat].
-template <bool kStats = false>
+// Every thread of the CTA must call it with the same range.  kMode 1
+// (statistics): also add each composited weight alpha * T to
+// contrib[splat]; kMode 2 (training): also track the last composited pair.
+template <int kMode = 0>
 __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start, uint32_t end,
                                                 const uint32_t *__restrict__ pval,
                                                 const float4 *__restrict__ rec, int tx0, int ty0,
@@ -108,7 +110,7 @@ __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start,
             sh.s0[h][tid] = make_float4(r.a.x, r.a.y, -0.5f * kLog2e * r.a.z, -kLog2e * r.a.w);
             sh.s1[h][tid] = make_float4(-0.5f * kLog2e * r.b.x, r.q.w, r.b.z, 0.0f);
             sh.s2[h][tid] = r.c;
-            if (kStats) sh.sid[h][tid] = r.s;
+            if (kMode == 1) sh.sid[h][tid] = r.s;
         }
         sh.mask[h][tid] = (uint8_t)m;
     };
@@ -146,7 +148,8 @@ __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start,
                 }
                 const float4 col = sh.s2[h][j];
                 const float wgt = alpha * px.T;
-                if (kStats) atomicAdd(contrib + sh.sid[h][j], wgt);
+                if (kMode == 1) atomicAdd(contrib + sh.sid[h][j], wgt);
+                if (kMode == 2) px.last = base + (uint32_t)j + 1u;
                 px.r += col.x * wgt;
                 px.g += col.y * wgt;
                 px.b += col.z * wgt;
@@ -184,9 +187,9 @@ __device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int 
     return g;
 }
 
-// Pass 1: the first kBudget pairs of every tile (kStats: every pair, with
-// per-splat weight sums).
-template <bool kStats>
+// Pass 1: the first kBudget pairs of every tile (kMode 1 statistics, 2
+// training: every pair in one pass).
+template <int kMode>
 __global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int H,
                                                          const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ pval,
@@ -196,9 +199,13 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int
     const int tile = blockIdx.x;
     const TileGeom g = tile_geom(tile, tiles_x, W, H);
     const uint2 rg = ranges[tile];
-    Pixel px{1.0f, 0.0f, 0.0f, 0.0f, !g.inside, false};
-    const uint32_t end1 = rg.y - rg.x > kBudget && !kStats ? rg.x + kBudget : rg.y;
-    composite_range<kStats>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib);
+    Pixel px{1.0f, 0.0f, 0.0f, 0.0f, rg.x, !g.inside, false};
+    const uint32_t end1 = rg.y - rg.x > kBudget && kMode == 0 ? rg.x + kBudget : rg.y;
+    composite_range<kMode>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib);
+    if (kMode == 2 && g.inside) {
+        work.px_end[(size_t)g.py * W + g.px] = px.last;
+        work.px_T[(size_t)g.py * W + g.px] = px.T;
+    }
     if (end1 < rg.y) {
         // pairs remain: record the pixel state for pass 2 and the merge
         const int slot = work.cand_slot[tile];
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_chunks(int tiles_x, int
     const uint32_t start = rg.x + kBudget + c * kChunk;
     const uint32_t end = min(rg.y, start + kChunk);
     const float4 s1 = work.state[(size_t)slot * kBlendThreads + threadIdx.x];
-    Pixel px{1.0f, 0.0f, 0.0f, 0.0f, !g.inside || s1.w < 0.0f, false};
+    Pixel px{1.0f, 0.0f, 0.0f, 0.0f, 0u, !g.inside || s1.w < 0.0f, false};
     composite_range(sh, start, end, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
     work.part[(size_t)w * kBlendThreads + threadIdx.x] = make_float4(px.r, px.g, px.b, px.stopped ? -px.T : px.T);
 }
@@ -305,7 +312,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W,
     const TileGeom g = tile_geom(tile, tiles_x, W, H);
     const uint2 rg = ranges[tile];
     const float4 sb = mine ? work.state[pix] : make_float4(0.f, 0.f, 0.f, 1.f);
-    Pixel px{sb.w, sb.x, sb.y, sb.z, !mine, false};
+    Pixel px{sb.w, sb.x, sb.y, sb.z, 0u, !mine, false};
     const uint32_t start = rg.x + kBudget + (w - work.cand_chunk0[slot]) * kChunk;
     composite_range(sh, start, min(rg.y, start + kChunk), pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
     if (mine && g.inside) out[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, 1.0f - px.T);
@@ -360,11 +367,16 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
     const size_t max_chunks = blend_max_chunks((size_t)n, n_pairs);
     if (work.contrib) {
         // statistics: every list composited in one pass
-        k_blend<true><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+        k_blend<1><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+        return 1;
+    }
+    if (work.px_end) {
+        // training forward: one pass, per-pixel state for the backward
+        k_blend<2><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
         return 1;
     }
     k_blend_plan<<<1, 1024, 0, st>>>(n, ranges, work);
-    k_blend<false><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+    k_blend<0><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
     // no tile has pairs left after pass 1
     if (n_pairs <= kBudget) return 2;
     k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);

@@ -114,6 +114,10 @@ struct TemplateArrays {
     const uint4 *qb;
     const uint4 *sh16;
     int storage;  // CS_STORE_FP32 or CS_STORE_BF16
+    // scales (x, y, z, 0) and quaternions (w, x, y, z) as uploaded (FP32
+    // storage; read by the backward only)
+    const float4 *scale;
+    const float4 *quat;
 };
 
 // BF16 halves of a 32-bit word, widened exactly to FP32
@@ -290,7 +294,12 @@ struct BlendWork {
     // when set: per splat, sum over pixels of its compositing weight
     // alpha * T (added to); lists are then composited in one pass
     float *contrib;
+    // when set (training forward): per pixel, one past the index of its last
+    // composited pair and its final transmittance; one pass as well
+    uint32_t *px_end;
+    float *px_T;
 };
+constexpr int kBlendBlockW = 8, kBlendBlockH = 4;  // pixels of one warp in a 16x16 tile
 constexpr uint32_t kBlendBudget = 8192;  // pairs composited by pass 1 per tile
 constexpr uint32_t kBlendChunk = 1024;   // pairs per pass-2 chunk
 constexpr size_t blend_max_slots(size_t n_tiles, size_t n_pairs) {
@@ -301,5 +310,42 @@ constexpr size_t blend_max_chunks(size_t n_tiles, size_t n_pairs) {
 }
 int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, const uint32_t *pval,
                  const float4 *rec, float4 *out, const BlendWork &work, uint32_t n_pairs, cudaStream_t st);
+
+}  // namespace cs
+
+namespace cs {
+
+// Gradients of the last training frame (cs_backward): everything the four
+// backward kernels read and write.
+struct BackwardArgs {
+    int tiles_x, tiles_y, W, H;
+    uint32_t n_pairs;
+    const uint2 *ranges;
+    const uint32_t *pval;
+    const float4 *rec;
+    const uint32_t *px_end;
+    const float *px_T;
+    const float4 *dl_drgba;
+    float4 *dsplat;  // [S][3]: du, dv, dA, dB | dC, do, dr, dg | db, -, -, -
+    int proj_blocks;
+    const Group *groups;
+    int n_groups;
+    const int32_t *vis;
+    const float *B, *V, *Cloc, *root;
+    TemplateArrays ta;
+    const TemplateInfo *tpls;
+    CamParams cam;
+    LodParams lod;
+    int skin_mode, sh_frame;
+    float *g_mean, *g_cov, *g_opacity, *g_sh, *g_B;
+    int n_inst, n_tpl;
+    const int32_t *tid;
+    const float *pose;
+    float *g_pose;
+    int n_gauss;
+    const float4 *scale, *quat;
+    float *g_scale, *g_quat;
+};
+int launch_backward(const BackwardArgs &a, cudaStream_t st);
 
 }  // namespace cs

@@ -7,7 +7,7 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("crowdsplat.h", "crowdsplat_lod.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("crowdsplat.h", "crowdsplat_lod.h", "crowdsplat_grad.h")]
 
 
 def declared_functions():
@@ -30,7 +30,8 @@ def test_header_declares_the_boundary():
     for must in ("cs_create", "cs_destroy", "cs_upload_templates", "cs_set_lod", "cs_set_instances",
                  "cs_render", "cs_render_to_host", "cs_get_stage_times", "cs_memory_stats",
                  "cs_last_error", "cs_debug_read", "cs_version", "cs_set_lod_subset", "cs_render_contrib",
-                 "cs_lod_features", "cs_lod_rank", "cs_mlp_create", "cs_mlp_forward", "cs_mlp_train_step"):
+                 "cs_lod_features", "cs_lod_rank", "cs_mlp_create", "cs_mlp_forward", "cs_mlp_train_step",
+                 "cs_render_train", "cs_backward"):
         assert must in names
     assert sorted(os.listdir(os.path.join(ROOT, "include"))) == sorted(os.path.basename(h) for h in HEADERS)
 
