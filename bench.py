@@ -595,6 +595,68 @@ def run_learned_lod(args):
     return line
 
 
+def run_grad(args):
+    """Forward (training) + backward of the differentiable path on 1
+    template of 65,536 Gaussians (SH degree 3), 64 instances, 512x512:
+    steps per second of render_train + backward (loss gradient = random
+    weights per pixel), CUDA events on the default stream."""
+    import numpy as np
+    import torch
+    from paper_2501_17792_gb300 import binding, build
+    from paper_2501_17792_gb300 import scene as S
+    build.build()
+    tpl = S.make_template(2100, 65536, 3)
+    rng = np.random.default_rng(9)
+    roots = [S.yaw_root(rng.uniform(0, 2 * math.pi), (col - 3.5) * 0.9, 0.0, 3.0 + row * 0.9)
+             for row in range(8) for col in range(8)]
+    n = 64
+    cam = S.look_camera((0.0, 1.4, 0.0), 12.0, 512, 512, vfov_deg=60.0)
+    r = binding.Renderer(device=0)
+    r.upload_templates([tpl])
+    frames = args.warmup + args.steps
+    poses = [torch.from_numpy(S.random_poses(77 + f, n)).cuda() for f in range(frames)]
+    tid = torch.zeros(n, dtype=torch.int32, device="cuda")
+    root = torch.from_numpy(np.stack(roots).astype(np.float32).reshape(n, 12)).cuda()
+    dl = torch.from_numpy(rng.normal(0, 1, (512, 512, 4)).astype(np.float32)).cuda()
+    out = torch.empty((512, 512, 4), dtype=torch.float32, device="cuda")
+    G = r.n_gauss_total
+    grads = dict(means=torch.zeros((G, 3), device="cuda"), scales=torch.zeros((G, 3), device="cuda"),
+                 quats=torch.zeros((G, 4), device="cuda"), opacity=torch.zeros(G, device="cuda"),
+                 sh=torch.zeros((G, 16, 3), device="cuda"), pose=torch.zeros((n, 24, 3), device="cuda"))
+
+    def step(f, ev=None):
+        r.set_instances(tid, root, poses[f])
+        r.render_train(cam, out=out)
+        if ev is not None:
+            ev.record()
+        r.backward(dl, n, grads)
+
+    r.set_instances(tid, root, poses[0])
+    _, st = r.render_train(cam, out=out, stats=True)
+    for f in range(args.warmup):
+        step(f)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e0.record()
+    for k in range(args.steps):
+        starts[k].record()
+        step(args.warmup + k, mids[k])
+    e1.record()
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    fwd = sum(s_.elapsed_time(m) for s_, m in zip(starts, mids)) / args.steps
+    line = {"metric": "differentiable render: forward + backward steps per second", "value": args.steps / (total / 1e3),
+            "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps, "ms_forward": fwd, "ms_backward": total / args.steps - fwd,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grad_1x65536g_sh3_64inst_512x512", "splats": st["splats"], "pairs": st["pairs"]}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -609,6 +671,8 @@ def main():
                     help="paper Table 1/2 sweep at 1280x720 (one JSON line per cell)")
     ap.add_argument("--storage", choices=["fp32", "bf16"], default="fp32",
                     help="template storage precision (bf16: BF16 attributes, FP16 SH, tensor-core skinning)")
+    ap.add_argument("--grad", action="store_true",
+                    help="forward + backward of the differentiable path (65,536 Gaussians, 64 instances, 512x512)")
     ap.add_argument("--learned-lod", action="store_true",
                     help="learned vs distance LoD at 10,000 instances, 3840x2160 (one JSON line)")
     ap.add_argument("--lod-steps", type=int, default=1500, help="MLP training steps for --learned-lod")
@@ -621,6 +685,9 @@ def main():
         return
     if args.learned_lod:
         run_learned_lod(args)
+        return
+    if args.grad:
+        run_grad(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

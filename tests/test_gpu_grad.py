@@ -222,3 +222,45 @@ def test_gradient_at_scale():
     for kind in ("means", "scales", "quats", "opacity", "sh", "pose"):
         ok, res = check_kind(sc, wt, lat, g, kind, n_pick=4, seed=11, steps=steps)
         assert ok.all(), (kind, res[~ok])
+
+
+def test_autograd_function_and_a_fit():
+    """The torch.autograd wrapper gives the library's gradients, and a few
+    Adam steps on the template means pull a rendered crowd towards a target
+    rendered from shifted means."""
+    from paper_2501_17792_gb300 import autograd as AG
+    from paper_2501_17792_gb300 import binding
+    sc = grad_scene(n_gauss=256, seed=6)
+    t = sc.templates[0]
+    wt, lat = loss_weights(sc, seed=7)
+    _, g_ref = gpu_grads(sc, wt)
+    r = binding.Renderer(device=0)
+    params = [torch.tensor(a, requires_grad=True) for a in (t.means, t.scales, t.quats, t.opacity, t.sh)]
+    pose = torch.tensor(sc.instances.pose, requires_grad=True)
+    img = AG.render(r, sc.camera, sc.instances, t, *params, pose)
+    (img * torch.from_numpy(wt).cuda()).sum().backward()
+    def close(a, b):  # float32 atomics: the summation order varies between runs
+        return np.allclose(a, b, rtol=1e-4, atol=1e-5 * np.abs(b).max())
+
+    for name, p in zip(("means", "scales", "quats", "opacity"), params[:4]):
+        assert close(p.grad.numpy(), g_ref[name].reshape(p.shape)), name
+    K = t.sh.shape[1]
+    assert close(params[4].grad.numpy(), g_ref["sh"][:, :K, :])
+    assert close(pose.grad.numpy(), g_ref["pose"])
+    # fit: target from means shifted by 5 mm
+    shift = np.float32(0.005)
+    with torch.no_grad():
+        target = AG.render(r, sc.camera, sc.instances, t, params[0] + shift, *params[1:], pose).clone()
+    means = torch.tensor(t.means, requires_grad=True)
+    opt = torch.optim.Adam([means], lr=5e-4)
+    losses = []
+    for _ in range(30):
+        opt.zero_grad()
+        img = AG.render(r, sc.camera, sc.instances, t, means, *params[1:], pose)
+        loss = ((img - target) ** 2).sum()
+        loss.backward()
+        opt.step()
+        losses.append(float(loss))
+    print(f"\n[grad fit] loss {losses[0]:.4f} -> {losses[-1]:.4f}; mean shift recovered "
+          f"{float((means.detach() - torch.tensor(t.means)).mean()):.5f} m of {shift}")
+    assert losses[-1] < 0.2 * losses[0]
