@@ -37,6 +37,7 @@ namespace cs {
 
 constexpr int kBlendThreads = kTile * kTile;
 constexpr int kBlockW = kBlendBlockW, kBlockH = kBlendBlockH;  // pixels per warp
+constexpr int kPass1Threads = 128;  // pass 1 of the plain frame: half-tile CTAs
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr uint32_t kBudget = kBlendBudget;  // pairs of pass 1 per tile
 constexpr uint32_t kChunk = kBlendChunk;    // pairs per pass-2 chunk
@@ -67,14 +68,16 @@ __device__ __forceinline__ void load_record(StagedRecord &r, const uint32_t *__r
     }
 }
 
+// kT threads stage batches of kT splats, double-buffered
+template <int kT = kBlendThreads>
 struct BlendShared {
     // staged splats: {u, v, a', b'}, {c', log2 o, radius, -}, {r, g, b, -} with
     // p = q log2 e = a' dx^2 + b' dx dy + c' dy^2
-    float4 s0[2][kBlendThreads];
-    float4 s1[2][kBlendThreads];
-    float4 s2[2][kBlendThreads];
-    uint32_t sid[2][kBlendThreads];
-    uint8_t mask[2][kBlendThreads];
+    float4 s0[2][kT];
+    float4 s1[2][kT];
+    float4 s2[2][kT];
+    uint32_t sid[2][kT];
+    uint8_t mask[2][kT];
 };
 
 struct Pixel {
@@ -88,12 +91,14 @@ struct Pixel {
 // Every thread of the CTA must call it with the same range.  kMode 1
 // (statistics): also add each composited weight alpha * T to
 // contrib[splat]; kMode 2 (training): also track the last composited pair.
-template <int kMode = 0>
-__device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start, uint32_t end,
+// kT: threads of the CTA, covering kT / 32 of the tile's 8x4 warp blocks
+// from block row brow0 (a 16x16 tile has 8: two columns, four rows).
+template <int kMode = 0, int kT = kBlendThreads>
+__device__ __forceinline__ void composite_range(BlendShared<kT> &sh, uint32_t start, uint32_t end,
                                                 const uint32_t *__restrict__ pval,
                                                 const float4 *__restrict__ rec, int tx0, int ty0,
                                                 float fpx, float fpy, Pixel &px,
-                                                float *__restrict__ contrib = nullptr) {
+                                                float *__restrict__ contrib = nullptr, int brow0 = 0) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t wbit = 1u << warp;
     auto stage = [&](const StagedRecord &r, int h) {
@@ -103,8 +108,8 @@ __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start,
             const int x0 = (int)(rx & 0xFFFFu) - tx0, x1 = (int)(rx >> 16) - tx0;
             const int y0 = (int)(ry & 0xFFFFu) - ty0, y1 = (int)(ry >> 16) - ty0;
 #pragma unroll
-            for (int w = 0; w < kBlendThreads / 32; ++w) {
-                const int bx = (w & 1) * kBlockW, by = (w >> 1) * kBlockH;
+            for (int w = 0; w < kT / 32; ++w) {
+                const int bx = (w & 1) * kBlockW, by = ((w >> 1) + brow0) * kBlockH;
                 if (x0 <= bx + kBlockW - 1 && x1 >= bx && y0 <= by + kBlockH - 1 && y1 >= by) m |= 1u << w;
             }
             sh.s0[h][tid] = make_float4(r.a.x, r.a.y, -0.5f * kLog2e * r.a.z, -kLog2e * r.a.w);
@@ -115,15 +120,15 @@ __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start,
         sh.mask[h][tid] = (uint8_t)m;
     };
     // the buffers may still be read by a previous call; leave when no pixel is open
-    if (__syncthreads_count(px.done) == kBlendThreads || start >= end) return;
+    if (__syncthreads_count(px.done) == kT || start >= end) return;
     StagedRecord nxt;
     load_record(nxt, pval, rec, start + tid, end);
     stage(nxt, 0);
-    load_record(nxt, pval, rec, start + kBlendThreads + tid, end);
+    load_record(nxt, pval, rec, start + kT + tid, end);
     __syncthreads();
     int h = 0;
-    for (uint32_t base = start; base < end; base += kBlendThreads, h ^= 1) {
-        const int nb = (int)min((uint32_t)kBlendThreads, end - base);
+    for (uint32_t base = start; base < end; base += kT, h ^= 1) {
+        const int nb = (int)min((uint32_t)kT, end - base);
         for (int c = 0; c < nb; c += 32) {
             if (__all_sync(0xffffffffu, px.done)) break;
             const bool mine = (sh.mask[h][c + lane] & wbit) != 0 && c + lane < nb;
@@ -159,11 +164,11 @@ __device__ __forceinline__ void composite_range(BlendShared &sh, uint32_t start,
         // the other half was last read before the previous barrier: refill it
         // with the next batch (loaded while this one was composited) and
         // start loading the batch after
-        if (base + kBlendThreads < end) {
+        if (base + kT < end) {
             stage(nxt, h ^ 1);
-            load_record(nxt, pval, rec, base + 2 * kBlendThreads + tid, end);
+            load_record(nxt, pval, rec, base + 2 * kT + tid, end);
         }
-        if (__syncthreads_count(px.done) == kBlendThreads) break;
+        if (__syncthreads_count(px.done) == kT) break;
     }
 }
 
@@ -173,10 +178,12 @@ struct TileGeom {
     float fpx, fpy;
 };
 
-__device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int H) {
+// Pixel of the calling thread: warp w of the tile (w0 = the CTA's first)
+// covers the 8x4 block at column w % 2, row w / 2.
+__device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int H, int w0 = 0) {
     TileGeom g;
     const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = w0 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     g.tx0 = txi * kTile;
     g.ty0 = tyi * kTile;
     g.px = g.tx0 + (warp & 1) * kBlockW + (lane & (kBlockW - 1));
@@ -188,30 +195,34 @@ __device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int 
 }
 
 // Pass 1: the first kBudget pairs of every tile (kMode 1 statistics, 2
-// training: every pair in one pass).
-template <int kMode>
-__global__ void __launch_bounds__(kBlendThreads) k_blend(int tiles_x, int W, int H,
-                                                         const uint2 *__restrict__ ranges,
-                                                         const uint32_t *__restrict__ pval,
-                                                         const float4 *__restrict__ rec,
-                                                         float4 *__restrict__ out, BlendWork work) {
-    __shared__ BlendShared sh;
-    const int tile = blockIdx.x;
-    const TileGeom g = tile_geom(tile, tiles_x, W, H);
+// training: every pair in one pass).  kT threads per CTA: 256 cover a tile,
+// 128 half a tile (two CTAs per tile, rows 0-7 and 8-15, each compositing
+// the tile's list on its own, so the halves do not wait for each other).
+template <int kMode, int kT>
+__global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const uint2 *__restrict__ ranges,
+                                              const uint32_t *__restrict__ pval, const float4 *__restrict__ rec,
+                                              float4 *__restrict__ out, BlendWork work) {
+    __shared__ BlendShared<kT> sh;
+    constexpr int kParts = kBlendThreads / kT;
+    const int tile = blockIdx.x / kParts, part = blockIdx.x % kParts;
+    const int w0 = part * (kT / 32);  // first warp block of this CTA
+    const TileGeom g = tile_geom(tile, tiles_x, W, H, w0);
     const uint2 rg = ranges[tile];
     Pixel px{1.0f, 0.0f, 0.0f, 0.0f, rg.x, !g.inside, false};
     const uint32_t end1 = rg.y - rg.x > kBudget && kMode == 0 ? rg.x + kBudget : rg.y;
-    composite_range<kMode>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib);
+    composite_range<kMode, kT>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib, w0 / 2);
     if (kMode == 2 && g.inside) {
         work.px_end[(size_t)g.py * W + g.px] = px.last;
         work.px_T[(size_t)g.py * W + g.px] = px.T;
     }
     if (end1 < rg.y) {
-        // pairs remain: record the pixel state for pass 2 and the merge
+        // pairs remain: record the pixel state for pass 2 and the merge (the
+        // plan set cand_done to 1; every part clears it unless all its
+        // pixels are done)
         const int slot = work.cand_slot[tile];
-        const int all = __syncthreads_count(px.done) == kBlendThreads;
-        if (threadIdx.x == 0) work.cand_done[slot] = (uint32_t)all;
-        work.state[(size_t)slot * kBlendThreads + threadIdx.x] =
+        const int all = __syncthreads_count(px.done) == kT;
+        if (threadIdx.x == 0 && !all) atomicAnd(work.cand_done + slot, 0u);
+        work.state[(size_t)slot * kBlendThreads + part * kT + threadIdx.x] =
             make_float4(px.r, px.g, px.b, px.done ? -px.T : px.T);
         if (!all) return;
     }
@@ -226,7 +237,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_chunks(int tiles_x, int
                                                                 const uint32_t *__restrict__ pval,
                                                                 const float4 *__restrict__ rec,
                                                                 BlendWork work) {
-    __shared__ BlendShared sh;
+    __shared__ BlendShared<> sh;
     const uint32_t w = blockIdx.x;
     const int n_cand = work.meta[0];
     if (w >= (uint32_t)work.meta[1]) return;
@@ -294,7 +305,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W,
                                                              const uint32_t *__restrict__ pval,
                                                              const float4 *__restrict__ rec,
                                                              float4 *__restrict__ out, BlendWork work) {
-    __shared__ BlendShared sh;
+    __shared__ BlendShared<> sh;
     const uint32_t w = blockIdx.x;
     const int n_cand = work.meta[0];
     if (w >= (uint32_t)work.meta[1]) return;
@@ -343,6 +354,7 @@ __global__ void __launch_bounds__(1024) k_blend_plan(int n_tiles, const uint2 *_
             if (cand) {
                 work.cand_tile[slot] = t;
                 work.cand_chunk0[slot] = run_k + ek;
+                work.cand_done[slot] = 1u;  // cleared by pass 1 unless every pixel is done
             }
         }
         __syncthreads();
@@ -367,16 +379,17 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
     const size_t max_chunks = blend_max_chunks((size_t)n, n_pairs);
     if (work.contrib) {
         // statistics: every list composited in one pass
-        k_blend<1><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+        k_blend<1, kBlendThreads><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
         return 1;
     }
     if (work.px_end) {
         // training forward: one pass, per-pixel state for the backward
-        k_blend<2><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+        k_blend<2, kBlendThreads><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
         return 1;
     }
     k_blend_plan<<<1, 1024, 0, st>>>(n, ranges, work);
-    k_blend<0><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+    k_blend<0, kPass1Threads><<<n * (kBlendThreads / kPass1Threads), kPass1Threads, 0, st>>>(tiles_x, W, H, ranges, pval,
+                                                                                           rec, out, work);
     // no tile has pairs left after pass 1
     if (n_pairs <= kBudget) return 2;
     k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);

@@ -467,7 +467,7 @@ __device__ void skin_blend_tc(const float4 *__restrict__ sB, const float w_in[4]
 // handles Gaussian chunk * 256 + t.  Splat ids are dense, grouped by
 // (template, level), instance-major within a group.
 template <int kStore>
-__global__ void __launch_bounds__(kProjThreads, 4) k_project(
+__global__ void __launch_bounds__(kProjThreads, 5) k_project(
     const Group *__restrict__ groups, int n_groups, const int32_t *__restrict__ vis,
     const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ Cloc,
     const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,

@@ -356,18 +356,44 @@ int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *
     return 1;
 }
 
+// Tile boundaries of the sorted pair list: each thread reads 8 tile keys
+// with one 16-byte load (the list starts 16-byte aligned) plus its two
+// neighbours, and writes the start / end of every tile that begins / ends
+// among its keys.
 __global__ void __launch_bounds__(256) k_tile_ranges(uint32_t n, const uint16_t *__restrict__ ptile,
                                                      uint2 *__restrict__ ranges) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint16_t t = ptile[i];
-    if (i == 0 || ptile[i - 1] != t) ranges[t].x = i;
-    if (i == n - 1 || ptile[i + 1] != t) ranges[t].y = i + 1;
+    const uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) * 8u;
+    if (base >= n) return;
+    uint32_t v[8];
+    if (base + 8u <= n) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(ptile + base));
+        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = ww[k] & 0xFFFFu;
+            v[2 * k + 1] = ww[k] >> 16;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = base + k < n ? (uint32_t)__ldg(ptile + base + k) : 0x10000u;
+    }
+    uint32_t prev = base > 0 ? (uint32_t)__ldg(ptile + base - 1) : 0x10000u;
+    const uint32_t next = base + 8u < n ? (uint32_t)__ldg(ptile + base + 8) : 0x10000u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t t = v[k];
+        if (t > 0xFFFFu) break;  // past the end
+        const uint32_t after = k < 7 ? v[k + 1] : next;
+        if (t != prev) ranges[t].x = base + k;
+        if (t != after) ranges[t].y = base + k + 1;
+        prev = t;
+    }
 }
 
 int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, cudaStream_t st) {
     if (n_pairs == 0) return 0;
-    k_tile_ranges<<<(n_pairs + 255) / 256, 256, 0, st>>>(n_pairs, ptile, ranges);
+    const uint32_t threads = (n_pairs + 7) / 8;
+    k_tile_ranges<<<(threads + 255) / 256, 256, 0, st>>>(n_pairs, ptile, ranges);
     return 1;
 }
 
