@@ -300,7 +300,7 @@ struct BlendWork {
     float *px_T;
 };
 constexpr int kBlendBlockW = 8, kBlendBlockH = 4;  // pixels of one warp in a 16x16 tile
-constexpr uint32_t kBlendBudget = 8192;  // pairs composited by pass 1 per tile
+constexpr uint32_t kBlendBudget = 16384;  // pairs composited by pass 1 per tile
 constexpr uint32_t kBlendChunk = 1024;   // pairs per pass-2 chunk
 constexpr size_t blend_max_slots(size_t n_tiles, size_t n_pairs) {
     return n_tiles < n_pairs / kBlendBudget + 1 ? n_tiles : n_pairs / kBlendBudget + 1;

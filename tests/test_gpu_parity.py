@@ -263,7 +263,7 @@ def test_nan_pose_is_culled_and_others_unchanged():
     assert np.abs(img - ref).max() <= 1e-6
 
 
-def _deep_field(seed=5, n=60000, w=48, h=32):
+def _deep_field(seed=5, n=60000, w=32, h=32):
     """Many faint small splats over a tiny image: every tile holds several
     compositing chunks of pairs, and the accumulated opacity is tuned so
     that pixels saturate at all depths of their lists, or never."""
@@ -276,7 +276,7 @@ def _deep_field(seed=5, n=60000, w=48, h=32):
     y = (py - h / 2) * z / f
     s = (1.5 * z / f)[:, None] * np.exp(rng.normal(0, 0.3, (n, 3)))
     q = rng.standard_normal((n, 4))
-    op = rng.uniform(0.008, 0.026, n)
+    op = rng.uniform(0.007, 0.017, n)
     sh = 0.3 * rng.standard_normal((n, 4, 3))
     tpl = U.template_from(np.stack([x, y, z], 1), s, q, op, sh)
     return U.scene_of([tpl], U.instances(1), U.identity_camera(w, h, f))
@@ -287,10 +287,10 @@ def test_split_compositing_of_long_tile_lists():
     r, img, ref, errs, st = full_check(sc, label="deep_field_split", max_boundary=0.2)
     rng = r.debug("tile_ranges").astype(np.int64)
     counts = rng[:, 1] - rng[:, 0]
-    assert counts.min() > 8192, counts  # every tile has pass-2 chunks
+    assert counts.min() > 16384, counts  # every tile has pass-2 chunks (pass-1 budget 16,384 pairs)
     # some pixels saturate (late in their lists), others never do
     A = ref["rgba"][..., 3]
-    assert (A < 0.999).mean() > 0.05 and (A > 0.9998).mean() > 0.5
+    assert (A < 0.999).mean() > 0.05 and (A > 0.9998).mean() > 0.3
 
 
 def test_error_codes():
