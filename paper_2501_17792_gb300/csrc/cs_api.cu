@@ -87,7 +87,7 @@ struct cs_ctx {
     CamParams train_cp{};
     int train_proj_blocks = 0;
     // split compositing of long tile lists
-    DevBuf<int32_t> bw_slot, bw_tile, bw_meta, bw_stop;
+    DevBuf<int32_t> bw_slot, bw_tile, bw_meta, bw_stop, bw_pp;
     DevBuf<uint32_t> bw_chunk0, bw_done;
     DevBuf<float4> bw_state, bw_part;
 
@@ -406,7 +406,7 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->ptile2); release(ctx->img); release(ctx->contrib_s);
     release(ctx->px_end); release(ctx->px_T); release(ctx->dsplat); release(ctx->g_cov); release(ctx->g_B);
     release(ctx->g_dummy);
-    release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_chunk0);
+    release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_pp); release(ctx->bw_chunk0);
     release(ctx->bw_done); release(ctx->bw_state); release(ctx->bw_part);
     if (ctx->d_meta) cudaFree(ctx->d_meta);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
@@ -902,7 +902,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         const size_t ms = blend_max_slots((size_t)T, (size_t)P), mc = blend_max_chunks((size_t)T, (size_t)P);
         CS_TRY(ensure(ctx, ctx->bw_slot, (size_t)T, "blend slots"));
         CS_TRY(ensure(ctx, ctx->bw_tile, ms, "blend slot tiles"));
-        CS_TRY(ensure(ctx, ctx->bw_meta, 2, "blend plan"));
+        CS_TRY(ensure(ctx, ctx->bw_meta, kBlendMetaWords, "blend plan"));
+        CS_TRY(ensure(ctx, ctx->bw_pp, (size_t)T, "blend pair-parallel tiles"));
         CS_TRY(ensure(ctx, ctx->bw_chunk0, ms + 1, "blend chunk offsets"));
         CS_TRY(ensure(ctx, ctx->bw_done, ms, "blend slot flags"));
         CS_TRY(ensure(ctx, ctx->bw_state, ms * 256, "blend pass-1 state"));
@@ -911,6 +912,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     }
     BlendWork bw{ctx->bw_slot.p, ctx->bw_tile.p, ctx->bw_chunk0.p, ctx->bw_done.p, ctx->bw_state.p, ctx->bw_part.p,
                  ctx->bw_meta.p, ctx->bw_stop.p, nullptr};
+    bw.pp_tile = ctx->bw_pp.p;
     if (contrib_tmpl) {
         CS_TRY(ensure(ctx, ctx->contrib_s, Sa, "splat contributions"));
         CS_CUDA(cudaMemsetAsync(ctx->contrib_s.p, 0, Sa * sizeof(float), st));
@@ -1163,7 +1165,7 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
                  bytes_of(ctx->pval2) + bytes_of(ctx->scratch) + bytes_of(ctx->rect) + bytes_of(ctx->ranges) +
                  bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img) + bytes_of(ctx->bw_slot) +
                  bytes_of(ctx->bw_tile) + bytes_of(ctx->bw_meta) + bytes_of(ctx->bw_chunk0) + bytes_of(ctx->bw_done) +
-                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop) + bytes_of(ctx->contrib_s) +
+                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop) + bytes_of(ctx->bw_pp) + bytes_of(ctx->contrib_s) +
                  bytes_of(ctx->px_end) + bytes_of(ctx->px_T) + bytes_of(ctx->dsplat) + bytes_of(ctx->g_cov) +
                  bytes_of(ctx->g_B) + bytes_of(ctx->g_dummy);
     out->template_bytes = tb;
@@ -1241,12 +1243,13 @@ constexpr size_t kStaticChunks = blend_max_chunks(kStaticTiles, kStaticPairs);
 constexpr size_t kOffBwSlot = kOffScratch + a256(kStaticScratchWords * 4);
 constexpr size_t kOffBwTile = kOffBwSlot + a256(kStaticTiles * 4);
 constexpr size_t kOffBwMeta = kOffBwTile + a256(kStaticSlots * 4);
-constexpr size_t kOffBwChunk0 = kOffBwMeta + a256(2 * 4);
+constexpr size_t kOffBwChunk0 = kOffBwMeta + a256(kBlendMetaWords * 4);
 constexpr size_t kOffBwDone = kOffBwChunk0 + a256((kStaticSlots + 1) * 4);
 constexpr size_t kOffBwState = kOffBwDone + a256(kStaticSlots * 4);
 constexpr size_t kOffBwPart = kOffBwState + a256(kStaticSlots * 256 * sizeof(float4));
 constexpr size_t kOffBwStop = kOffBwPart + a256(kStaticChunks * 256 * sizeof(float4));
-constexpr size_t kStaticBytes = kOffBwStop + a256(kStaticSlots * 256 * 4);  // about 11.6 MB
+constexpr size_t kOffBwPp = kOffBwStop + a256(kStaticSlots * 256 * 4);
+constexpr size_t kStaticBytes = kOffBwPp + a256(kStaticTiles * 4);  // about 11.6 MB
 
 }  // namespace
 
@@ -1383,6 +1386,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
                  reinterpret_cast<uint32_t *>(base + kOffBwChunk0), reinterpret_cast<uint32_t *>(base + kOffBwDone),
                  reinterpret_cast<float4 *>(base + kOffBwState), reinterpret_cast<float4 *>(base + kOffBwPart),
                  reinterpret_cast<int32_t *>(base + kOffBwMeta), reinterpret_cast<int32_t *>(base + kOffBwStop)};
+    bw.pp_tile = reinterpret_cast<int32_t *>(base + kOffBwPp);
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ranges, pval, rec, out, bw,
                              (uint32_t)P, st);
     CS_CUDA(cudaGetLastError());

@@ -208,6 +208,8 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
     const int w0 = part * (kT / 32);  // first warp block of this CTA
     const TileGeom g = tile_geom(tile, tiles_x, W, H, w0);
     const uint2 rg = ranges[tile];
+    // plain frames: long lists take the pair-parallel pass 1 (k_blend_pp)
+    if (kMode == 0 && rg.y - rg.x > kBlendPpMin) return;
     Pixel px{1.0f, 0.0f, 0.0f, 0.0f, rg.x, !g.inside, false};
     const uint32_t end1 = rg.y - rg.x > kBudget && kMode == 0 ? rg.x + kBudget : rg.y;
     composite_range<kMode, kT>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib, w0 / 2);
@@ -227,6 +229,169 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
         if (!all) return;
     }
     if (g.inside) out[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, 1.0f - px.T);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1, pair-parallel (plain frames, lists longer than kPpMin pairs).  A
+// CTA of kPpWarps warps composites one 8x4 pixel block of a tile, one pixel
+// per lane, in rounds of kPpRound pairs: warp k composites pairs
+// [32 k, 32 k + 32) of the round for the block's pixels from T = 1 (a
+// partial (C_k, T_k), no stop rule); warp 0 then chains the partials in
+// depth order, C += T C_k, T *= T_k, and where T T_k would fall below the
+// stop threshold it composites sub-range k again from the true T with the
+// stop rule, so the stop rule holds exactly as in the sequential definition
+// (only it needs the true T; the rest of the operator is associative).  A
+// block's dependency chain is one round per kPpRound pairs, split over
+// eight warps, instead of every pair in turn: a long list of large splats
+// no longer leaves the GPU waiting on a single CTA.  Persistent CTAs take
+// (tile, block) items from a list ordered by decreasing list length.
+// ---------------------------------------------------------------------------
+constexpr int kPpWarps = 8;
+constexpr int kPpThreads = 32 * kPpWarps;
+constexpr uint32_t kPpRound = 32 * kPpWarps;
+constexpr uint32_t kPpMin = kBlendPpMin;
+constexpr int kPpBlocks = kTile * kTile / 32;  // 8x4 blocks per tile
+constexpr int kPpBuckets = 8;                  // list lengths kPpMin 2^k .. for the item order
+
+struct PpShared {
+    float4 s0[kPpWarps][32];  // u, v, a', b' (as staged by composite_range)
+    float4 s1[kPpWarps][32];  // c', log2 o, radius, -
+    float4 s2[kPpWarps][32];  // r, g, b, -
+    float4 part[kPpWarps][32];
+    uint32_t m[kPpWarps];  // pairs of each sub-range whose reach box meets the block
+    uint32_t done;         // pixels of the block that are done
+    int item;
+};
+
+// alpha of a staged splat at a pixel centre; 0 when the splat does not
+// contribute there (outside its support box, q > 0, alpha < 1/255).  The
+// same arithmetic as composite_range.
+__device__ __forceinline__ float staged_alpha(const float4 &a, const float4 &b, float fpx, float fpy) {
+    const float dx = fpx - a.x, dy = fpy - a.y;
+    if (fmaxf(fabsf(dx), fabsf(dy)) > b.z) return 0.0f;
+    const float p = dx * (a.z * dx + a.w * dy) + b.x * dy * dy;
+    if (p > 0.0f) return 0.0f;
+    const float alpha = fminf(0.99f, ex2_approx(p + b.y));
+    return alpha < (1.0f / 255.0f) ? 0.0f : alpha;
+}
+
+__global__ void __launch_bounds__(kPpThreads) k_blend_pp(int tiles_x, int W, int H, const uint2 *__restrict__ ranges,
+                                                         const uint32_t *__restrict__ pval,
+                                                         const float4 *__restrict__ rec, float4 *__restrict__ out,
+                                                         BlendWork work) {
+    __shared__ PpShared sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_items = work.meta[2] * kPpBlocks;
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = (int)atomicAdd(reinterpret_cast<unsigned *>(work.meta + 3), 1u);
+        __syncthreads();
+        const int item = sh.item;
+        if (item >= n_items) return;
+        const int tile = work.pp_tile[item / kPpBlocks], blk = item % kPpBlocks;
+        const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
+        const int bx0 = txi * kTile + (blk & 1) * kBlockW, by0 = tyi * kTile + (blk >> 1) * kBlockH;
+        const int px = bx0 + (lane & (kBlockW - 1)), py = by0 + lane / kBlockW;
+        const bool inside = px < W && py < H;
+        const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+        const uint2 rg = ranges[tile];
+        const uint32_t end1 = rg.y - rg.x > kBudget ? rg.x + kBudget : rg.y;
+        // the block's chained state (warp 0)
+        float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+        bool done = !inside;
+        if (warp == 0) {
+            const uint32_t dm = __ballot_sync(0xffffffffu, done);
+            if (lane == 0) sh.done = dm;
+        }
+        __syncthreads();
+        for (uint32_t base = rg.x; base < end1; base += kPpRound) {
+            const uint32_t dmask = sh.done;
+            if (dmask == 0xffffffffu) break;
+            // stage this warp's sub-range
+            const uint32_t i = base + (uint32_t)warp * 32u + (uint32_t)lane;
+            bool mine = false;
+            if (i < end1) {
+                const uint32_t s = __ldg(pval + i);
+                const float4 *p = rec + (size_t)s * kRecVec;
+                const float4 ra = __ldg(p), rb = __ldg(p + 1), rc = __ldg(p + 2), rq = __ldg(p + 3);
+                const uint32_t rx = __float_as_uint(rq.x), ry = __float_as_uint(rq.y);
+                mine = (int)(rx & 0xFFFFu) <= bx0 + kBlockW - 1 && (int)(rx >> 16) >= bx0 &&
+                       (int)(ry & 0xFFFFu) <= by0 + kBlockH - 1 && (int)(ry >> 16) >= by0;
+                sh.s0[warp][lane] = make_float4(ra.x, ra.y, -0.5f * kLog2e * ra.z, -kLog2e * ra.w);
+                sh.s1[warp][lane] = make_float4(-0.5f * kLog2e * rb.x, rq.w, rb.z, 0.0f);
+                sh.s2[warp][lane] = rc;
+            }
+            uint32_t m = __ballot_sync(0xffffffffu, mine);
+            if (lane == 0) sh.m[warp] = m;
+            __syncwarp();
+            // the sub-range's partial composite from T = 1
+            const bool pdone = (dmask >> lane) & 1u;
+            float Tk = 1.0f, kr = 0.0f, kg = 0.0f, kb = 0.0f;
+            while (m) {
+                const int j = __ffs(m) - 1;
+                m &= m - 1;
+                if (pdone) continue;
+                const float alpha = staged_alpha(sh.s0[warp][j], sh.s1[warp][j], fpx, fpy);
+                if (alpha == 0.0f) continue;
+                const float4 col = sh.s2[warp][j];
+                const float wgt = alpha * Tk;
+                kr += col.x * wgt;
+                kg += col.y * wgt;
+                kb += col.z * wgt;
+                Tk *= 1.0f - alpha;
+            }
+            sh.part[warp][lane] = make_float4(kr, kg, kb, Tk);
+            __syncthreads();
+            // chain the partials in depth order
+            if (warp == 0) {
+                for (int k = 0; k < kPpWarps && !done; ++k) {
+                    const float4 q = sh.part[k][lane];
+                    if (T * q.w >= 1e-4f) {
+                        // no splat of the sub-range meets the stop rule from this T
+                        cr += T * q.x;
+                        cg += T * q.y;
+                        cb += T * q.z;
+                        T *= q.w;
+                        continue;
+                    }
+                    // the stop falls inside sub-range k: composite it from the true T
+                    uint32_t mk = sh.m[k];
+                    while (mk) {
+                        const int j = __ffs(mk) - 1;
+                        mk &= mk - 1;
+                        const float alpha = staged_alpha(sh.s0[k][j], sh.s1[k][j], fpx, fpy);
+                        if (alpha == 0.0f) continue;
+                        const float Tn = T * (1.0f - alpha);
+                        if (Tn < 1e-4f) {
+                            done = true;
+                            break;
+                        }
+                        const float4 col = sh.s2[k][j];
+                        const float wgt = alpha * T;
+                        cr += col.x * wgt;
+                        cg += col.y * wgt;
+                        cb += col.z * wgt;
+                        T = Tn;
+                    }
+                }
+                const uint32_t dm = __ballot_sync(0xffffffffu, done);
+                if (lane == 0) sh.done = dm;
+            }
+            __syncthreads();
+        }
+        if (warp == 0) {
+            bool final_out = true;
+            if (end1 < rg.y) {
+                // pairs remain: the state for pass 2 and the merge, as pass 1 records it
+                const int slot = work.cand_slot[tile];
+                const bool all = __all_sync(0xffffffffu, done);
+                if (lane == 0 && !all) atomicAnd(work.cand_done + slot, 0u);
+                work.state[(size_t)slot * kBlendThreads + blk * 32 + lane] = make_float4(cr, cg, cb, done ? -T : T);
+                final_out = all;
+            }
+            if (final_out && inside) out[(size_t)py * W + px] = make_float4(cr, cg, cb, 1.0f - T);
+        }
+        __syncthreads();  // sh.item and the staging buffers are reused by the next item
+    }
 }
 
 // Pass 2: chunk c of a tile's remaining pairs, from T = 1, for the pixels
@@ -369,6 +534,48 @@ __global__ void __launch_bounds__(1024) k_blend_plan(int n_tiles, const uint2 *_
         work.meta[0] = (int)run_c;
         work.meta[1] = (int)run_k;
     }
+    // tiles of the pair-parallel pass 1, grouped by list length (longest
+    // group first; the order inside a group does not affect any result)
+    __shared__ uint32_t bcount[kPpBuckets], bcursor[kPpBuckets];
+    if (threadIdx.x < kPpBuckets) bcount[threadIdx.x] = 0u;
+    __syncthreads();
+    auto bucket = [](uint32_t n) { return min(kPpBuckets - 1, 31 - __clz((int)(n / kPpMin))); };
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const uint32_t n = ranges[t].y - ranges[t].x;
+        if (n > kPpMin) atomicAdd(&bcount[bucket(n)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int k = kPpBuckets - 1; k >= 0; --k) {
+            bcursor[k] = run;
+            run += bcount[k];
+        }
+        work.meta[2] = (int)run;
+        work.meta[3] = 0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+        const uint32_t n = ranges[t].y - ranges[t].x;
+        if (n > kPpMin) work.pp_tile[atomicAdd(&bcursor[bucket(n)], 1u)] = t;
+    }
+}
+
+// Persistent grid of the pair-parallel pass: as many CTAs as fit on the
+// device at once.
+static unsigned pp_grid() {
+    static int cached_device = -1;
+    static unsigned grid = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != cached_device) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_blend_pp, kPpThreads, 0);
+        grid = (unsigned)std::max(1, sms * std::max(1, per_sm));
+        cached_device = dev;
+    }
+    return grid;
 }
 
 int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, const uint32_t *pval,
@@ -388,14 +595,20 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
         return 1;
     }
     k_blend_plan<<<1, 1024, 0, st>>>(n, ranges, work);
+    int launched = 2;
+    // long lists: pair-parallel pass 1; the others: one CTA per half tile
+    if (n_pairs > kPpMin) {
+        k_blend_pp<<<pp_grid(), kPpThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+        ++launched;
+    }
     k_blend<0, kPass1Threads><<<n * (kBlendThreads / kPass1Threads), kPass1Threads, 0, st>>>(tiles_x, W, H, ranges, pval,
                                                                                            rec, out, work);
     // no tile has pairs left after pass 1
-    if (n_pairs <= kBudget) return 2;
+    if (n_pairs <= kBudget) return launched;
     k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);
     k_blend_merge<<<(unsigned)max_cand, kBlendThreads, 0, st>>>(tiles_x, W, H, out, work);
     k_blend_fix<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
-    return 5;
+    return launched + 3;
 }
 
 }  // namespace cs

@@ -263,7 +263,7 @@ def test_nan_pose_is_culled_and_others_unchanged():
     assert np.abs(img - ref).max() <= 1e-6
 
 
-def _deep_field(seed=5, n=60000, w=32, h=32):
+def _deep_field(seed=5, n=135000, w=32, h=32, size=1.05, opacity=(0.006, 0.016)):
     """Many faint small splats over a tiny image: every tile holds several
     compositing chunks of pairs, and the accumulated opacity is tuned so
     that pixels saturate at all depths of their lists, or never."""
@@ -274,9 +274,9 @@ def _deep_field(seed=5, n=60000, w=32, h=32):
     py = rng.uniform(0, h, n)
     x = (px - w / 2) * z / f
     y = (py - h / 2) * z / f
-    s = (1.5 * z / f)[:, None] * np.exp(rng.normal(0, 0.3, (n, 3)))
+    s = (size * z / f)[:, None] * np.exp(rng.normal(0, 0.3, (n, 3)))
     q = rng.standard_normal((n, 4))
-    op = rng.uniform(0.007, 0.017, n)
+    op = rng.uniform(opacity[0], opacity[1], n)
     sh = 0.3 * rng.standard_normal((n, 4, 3))
     tpl = U.template_from(np.stack([x, y, z], 1), s, q, op, sh)
     return U.scene_of([tpl], U.instances(1), U.identity_camera(w, h, f))
@@ -287,8 +287,22 @@ def test_split_compositing_of_long_tile_lists():
     r, img, ref, errs, st = full_check(sc, label="deep_field_split", max_boundary=0.2)
     rng = r.debug("tile_ranges").astype(np.int64)
     counts = rng[:, 1] - rng[:, 0]
-    assert counts.min() > 16384, counts  # every tile has pass-2 chunks (pass-1 budget 16,384 pairs)
+    assert counts.min() > 32768, counts  # every tile has pass-2 chunks (pass-1 budget 32,768 pairs)
     # some pixels saturate (late in their lists), others never do
+    A = ref["rgba"][..., 3]
+    assert (A < 0.999).mean() > 0.05 and (A > 0.9998).mean() > 0.3
+
+
+def test_pair_parallel_pass_on_mid_length_lists():
+    """Lists between the pair-parallel threshold (1,024 pairs) and the pass-1
+    budget on a 40x24 image (ragged right and bottom tiles, blocks partly
+    outside the image): pass 1 chains eight sub-range partials per round,
+    and pixels meet the stop rule inside sub-ranges at all depths."""
+    sc = _deep_field(n=20000, w=40, h=24, size=2.0, opacity=(0.01, 0.03))
+    r, img, ref, errs, st = full_check(sc, label="mid_lists_pair_parallel", max_boundary=0.2)
+    rng = r.debug("tile_ranges").astype(np.int64)
+    counts = rng[:, 1] - rng[:, 0]
+    assert counts.min() > 1024 and counts.max() <= 32768, counts
     A = ref["rgba"][..., 3]
     assert (A < 0.999).mean() > 0.05 and (A > 0.9998).mean() > 0.3
 
