@@ -10,8 +10,14 @@
 // support box (|dx|, |dy| <= r), which makes the image independent of the
 // tile size.
 //
-// One CTA per tile, one thread per pixel, each warp an 8x4 block of the tile.
-// A CTA walks depth-ordered pairs in batches of 256, software pipelined:
+// Pass 1 of a plain frame (k_blend_pp) composites each 8x4 pixel block of
+// a tile with eight warps that split the block's depth-ordered pairs into
+// sub-ranges and chain their partial composites (described at the kernel).
+//
+// The one-pass kernels (statistics and training frames) and the split passes
+// below take one CTA per tile, one thread per pixel, each warp an 8x4 block
+// of the tile.  A CTA walks depth-ordered pairs in batches of 256, software
+// pipelined:
 // while the warps composite batch k from one half of a shared double buffer,
 // each thread holds in registers the record it loaded for batch k+1; after
 // compositing it stages that record into the other half (with the warp
@@ -37,7 +43,6 @@ namespace cs {
 
 constexpr int kBlendThreads = kTile * kTile;
 constexpr int kBlockW = kBlendBlockW, kBlockH = kBlendBlockH;  // pixels per warp
-constexpr int kPass1Threads = 128;  // pass 1 of the plain frame: half-tile CTAs
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr uint32_t kBudget = kBlendBudget;  // pairs of pass 1 per tile
 constexpr uint32_t kChunk = kBlendChunk;    // pairs per pass-2 chunk
@@ -208,8 +213,6 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
     const int w0 = part * (kT / 32);  // first warp block of this CTA
     const TileGeom g = tile_geom(tile, tiles_x, W, H, w0);
     const uint2 rg = ranges[tile];
-    // plain frames: long lists take the pair-parallel pass 1 (k_blend_pp)
-    if (kMode == 0 && rg.y - rg.x > kBlendPpMin) return;
     Pixel px{1.0f, 0.0f, 0.0f, 0.0f, rg.x, !g.inside, false};
     const uint32_t end1 = rg.y - rg.x > kBudget && kMode == 0 ? rg.x + kBudget : rg.y;
     composite_range<kMode, kT>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib, w0 / 2);
@@ -232,9 +235,9 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
 }
 
 // ---------------------------------------------------------------------------
-// Pass 1, pair-parallel (plain frames, lists longer than kPpMin pairs).  A
-// CTA of kPpWarps warps composites one 8x4 pixel block of a tile, one pixel
-// per lane, in rounds of kPpRound pairs: warp k composites pairs
+// Pass 1 of plain frames, pair-parallel.  A CTA of kPpWarps warps
+// composites one 8x4 pixel block of a tile, one pixel per lane, in rounds
+// of kPpRound pairs: warp k composites pairs
 // [32 k, 32 k + 32) of the round for the block's pixels from T = 1 (a
 // partial (C_k, T_k), no stop rule); warp 0 then chains the partials in
 // depth order, C += T C_k, T *= T_k, and where T T_k would fall below the
@@ -244,14 +247,13 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
 // block's dependency chain is one round per kPpRound pairs, split over
 // eight warps, instead of every pair in turn: a long list of large splats
 // no longer leaves the GPU waiting on a single CTA.  Persistent CTAs take
-// (tile, block) items from a list ordered by decreasing list length.
+// (tile, block) items from a list ordered by decreasing list length (so the
+// longest chains start first), then one item per empty tile (background).
 // ---------------------------------------------------------------------------
 constexpr int kPpWarps = 8;
 constexpr int kPpThreads = 32 * kPpWarps;
 constexpr uint32_t kPpRound = 32 * kPpWarps;
-constexpr uint32_t kPpMin = kBlendPpMin;
 constexpr int kPpBlocks = kTile * kTile / 32;  // 8x4 blocks per tile
-constexpr int kPpBuckets = 8;                  // list lengths kPpMin 2^k .. for the item order
 
 struct PpShared {
     float4 s0[kPpWarps][32];  // u, v, a', b' (as staged by composite_range)
@@ -275,18 +277,28 @@ __device__ __forceinline__ float staged_alpha(const float4 &a, const float4 &b, 
     return alpha < (1.0f / 255.0f) ? 0.0f : alpha;
 }
 
-__global__ void __launch_bounds__(kPpThreads) k_blend_pp(int tiles_x, int W, int H, const uint2 *__restrict__ ranges,
+__global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, int H, const uint2 *__restrict__ ranges,
                                                          const uint32_t *__restrict__ pval,
                                                          const float4 *__restrict__ rec, float4 *__restrict__ out,
                                                          BlendWork work) {
+    static_assert(kPpThreads == kBlendThreads, "an empty-tile item writes one tile, a pixel per thread");
     __shared__ PpShared sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_items = work.meta[2] * kPpBlocks;
+    const int n_busy = work.meta[2];
+    const int n_busy_items = n_busy * kPpBlocks;
+    const int n_items = n_busy_items + work.meta[4];
     for (;;) {
         if (threadIdx.x == 0) sh.item = (int)atomicAdd(reinterpret_cast<unsigned *>(work.meta + 3), 1u);
         __syncthreads();
         const int item = sh.item;
         if (item >= n_items) return;
+        if (item >= n_busy_items) {
+            // a tile without pairs: background (C = 0, T = 1)
+            const TileGeom g = tile_geom(work.pp_tile[n_busy + (item - n_busy_items)], tiles_x, W, H);
+            if (g.inside) out[(size_t)g.py * W + g.px] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            __syncthreads();  // sh.item is reused by the next item
+            continue;
+        }
         const int tile = work.pp_tile[item / kPpBlocks], blk = item % kPpBlocks;
         const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
         const int bx0 = txi * kTile + (blk & 1) * kBlockW, by0 = tyi * kTile + (blk >> 1) * kBlockH;
@@ -534,31 +546,29 @@ __global__ void __launch_bounds__(1024) k_blend_plan(int n_tiles, const uint2 *_
         work.meta[0] = (int)run_c;
         work.meta[1] = (int)run_k;
     }
-    // tiles of the pair-parallel pass 1, grouped by list length (longest
-    // group first; the order inside a group does not affect any result)
-    __shared__ uint32_t bcount[kPpBuckets], bcursor[kPpBuckets];
-    if (threadIdx.x < kPpBuckets) bcount[threadIdx.x] = 0u;
+    // pass-1 items, grouped by list length, longest first (the order inside
+    // a group does not affect any result): eight block items per tile with
+    // pairs, then one item per empty tile
+    constexpr int kClasses = 24;  // 0: empty; k >= 1: 2^(k-1) <= pairs < 2^k
+    __shared__ uint32_t ccount[kClasses], ccursor[kClasses];
+    if (threadIdx.x < kClasses) ccount[threadIdx.x] = 0u;
     __syncthreads();
-    auto bucket = [](uint32_t n) { return min(kPpBuckets - 1, 31 - __clz((int)(n / kPpMin))); };
-    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-        const uint32_t n = ranges[t].y - ranges[t].x;
-        if (n > kPpMin) atomicAdd(&bcount[bucket(n)], 1u);
-    }
+    auto cls = [](uint32_t n) { return n == 0u ? 0 : 1 + min(kClasses - 2, 31 - __clz((int)n)); };
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&ccount[cls(ranges[t].y - ranges[t].x)], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
-        for (int k = kPpBuckets - 1; k >= 0; --k) {
-            bcursor[k] = run;
-            run += bcount[k];
+        for (int k = kClasses - 1; k >= 0; --k) {
+            ccursor[k] = run;
+            run += ccount[k];
         }
-        work.meta[2] = (int)run;
+        work.meta[2] = (int)(run - ccount[0]);
         work.meta[3] = 0;
+        work.meta[4] = (int)ccount[0];
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-        const uint32_t n = ranges[t].y - ranges[t].x;
-        if (n > kPpMin) work.pp_tile[atomicAdd(&bcursor[bucket(n)], 1u)] = t;
-    }
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
+        work.pp_tile[atomicAdd(&ccursor[cls(ranges[t].y - ranges[t].x)], 1u)] = t;
 }
 
 // Persistent grid of the pair-parallel pass: as many CTAs as fit on the
@@ -595,14 +605,9 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
         return 1;
     }
     k_blend_plan<<<1, 1024, 0, st>>>(n, ranges, work);
-    int launched = 2;
-    // long lists: pair-parallel pass 1; the others: one CTA per half tile
-    if (n_pairs > kPpMin) {
-        k_blend_pp<<<pp_grid(), kPpThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
-        ++launched;
-    }
-    k_blend<0, kPass1Threads><<<n * (kBlendThreads / kPass1Threads), kPass1Threads, 0, st>>>(tiles_x, W, H, ranges, pval,
-                                                                                           rec, out, work);
+    // pass 1 of every tile: persistent CTAs, longest lists first
+    k_blend_pp<<<pp_grid(), kPpThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+    const int launched = 2;
     // no tile has pairs left after pass 1
     if (n_pairs <= kBudget) return launched;
     k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);

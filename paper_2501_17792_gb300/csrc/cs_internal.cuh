@@ -281,9 +281,10 @@ int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cud
 // pixel state (r, g, b, T; T negated when saturated); per chunk, the chunk's
 // pixel composite (r, g, b, T; T negated when it met the stop rule); per
 // slot pixel, the chunk in which it meets the stop rule (-1 if none);
-// meta[0] = slots, meta[1] = chunks, meta[2] = tiles of the pair-parallel
-// pass 1, meta[3] = its work counter; pp_tile lists those tiles, longest
-// lists first (by powers of two).
+// meta[0] = slots, meta[1] = chunks; pass 1 (plain frames): meta[2] =
+// tiles with pairs, meta[4] = empty tiles, meta[3] = the work counter of its
+// persistent CTAs; pp_tile lists the tiles with pairs, longest lists first
+// (by powers of two), then the empty ones.
 struct BlendWork {
     int32_t *cand_slot;
     int32_t *cand_tile;
@@ -302,11 +303,10 @@ struct BlendWork {
     float *px_T;
     int32_t *pp_tile;  // [tiles]
 };
-constexpr int kBlendMetaWords = 4;
+constexpr int kBlendMetaWords = 8;
 constexpr int kBlendBlockW = 8, kBlendBlockH = 4;  // pixels of one warp in a 16x16 tile
 constexpr uint32_t kBlendBudget = 32768;  // pairs composited by pass 1 per tile
 constexpr uint32_t kBlendChunk = 1024;   // pairs per pass-2 chunk
-constexpr uint32_t kBlendPpMin = 1024;   // longer lists take the pair-parallel pass 1
 constexpr size_t blend_max_slots(size_t n_tiles, size_t n_pairs) {
     return n_tiles < n_pairs / kBlendBudget + 1 ? n_tiles : n_pairs / kBlendBudget + 1;
 }

@@ -294,10 +294,10 @@ def test_split_compositing_of_long_tile_lists():
 
 
 def test_pair_parallel_pass_on_mid_length_lists():
-    """Lists between the pair-parallel threshold (1,024 pairs) and the pass-1
-    budget on a 40x24 image (ragged right and bottom tiles, blocks partly
-    outside the image): pass 1 chains eight sub-range partials per round,
-    and pixels meet the stop rule inside sub-ranges at all depths."""
+    """Lists of several rounds but below the pass-1 budget on a 40x24 image
+    (ragged right and bottom tiles, blocks partly outside the image): pass 1
+    chains eight sub-range partials per round, and pixels meet the stop rule
+    inside sub-ranges at all depths."""
     sc = _deep_field(n=20000, w=40, h=24, size=2.0, opacity=(0.01, 0.03))
     r, img, ref, errs, st = full_check(sc, label="mid_lists_pair_parallel", max_boundary=0.2)
     rng = r.debug("tile_ranges").astype(np.int64)
