@@ -281,7 +281,6 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
                                                          const uint32_t *__restrict__ pval,
                                                          const float4 *__restrict__ rec, float4 *__restrict__ out,
                                                          BlendWork work) {
-    static_assert(kPpThreads == kBlendThreads, "an empty-tile item writes one tile, a pixel per thread");
     __shared__ PpShared sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_busy = work.meta[2];
@@ -294,8 +293,12 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
         if (item >= n_items) return;
         if (item >= n_busy_items) {
             // a tile without pairs: background (C = 0, T = 1)
-            const TileGeom g = tile_geom(work.pp_tile[n_busy + (item - n_busy_items)], tiles_x, W, H);
-            if (g.inside) out[(size_t)g.py * W + g.px] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const int tile = work.pp_tile[n_busy + (item - n_busy_items)];
+            const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
+            for (int q = threadIdx.x; q < kTile * kTile; q += kPpThreads) {
+                const int x = txi * kTile + (q & (kTile - 1)), y = tyi * kTile + q / kTile;
+                if (x < W && y < H) out[(size_t)y * W + x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
             __syncthreads();  // sh.item is reused by the next item
             continue;
         }

@@ -110,15 +110,18 @@ int exclusive_scan_bins(const uint32_t *bins, uint32_t *out, uint32_t n, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort, 8-bit digits, reduce-then-scan per pass
+// stable LSD radix sort, digits of up to 8 bits, reduce-then-scan per pass
 //
-// A block owns 4,096 consecutive elements; warp w owns 512 of them, read in
-// 16 rounds of 32 consecutive elements (coalesced, all loads issued before
-// any shared-memory update).  Histogram pass: per-warp digit counts (shared
+// A sort of b-bit keys takes ceil(b / 8) passes of near-equal digit width
+// (13-bit tile keys: 7 + 6 bits; 32-bit depth keys: 4 x 8): a narrower
+// digit needs fewer ballots to rank and smaller count tables.  A block owns
+// 4,096 consecutive elements; warp w owns 512 of them, read in 16 rounds of
+// 32 consecutive elements (coalesced, all loads issued before any
+// shared-memory update).  Histogram pass: per-warp digit counts (shared
 // atomics), one row per digit in the global count matrix (digit-major),
 // which an exclusive scan turns into each block's global digit offsets.
 // Scatter pass: stable ranks from per-warp running counts, the lanes that
-// share a digit found with 8 ballots (one per digit bit), then a block-local
+// share a digit found with one ballot per digit bit, then a block-local
 // sort in shared memory, then each digit's run is written out with
 // consecutive threads on consecutive addresses.
 // ---------------------------------------------------------------------------
@@ -128,28 +131,30 @@ constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kRadixItems = 16;                              // per lane
 constexpr int kRadixTile = kRadixThreads * kRadixItems;      // per block (4,096)
 constexpr int kRadixWarpTile = 32 * kRadixItems;             // per warp (512)
-constexpr int kRadixDigits = 256;
+constexpr int kRadixMaxBits = 8;
+constexpr int kRadixDigits = 1 << kRadixMaxBits;             // largest digit range
 
-template <typename K>
+template <typename K, int kBits>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const K *__restrict__ keys, uint32_t n,
                                                               int shift, uint32_t *__restrict__ hist,
                                                               uint32_t nblocks) {
-    __shared__ uint32_t h[kRadixWarps][kRadixDigits];
+    constexpr uint32_t kDigits = 1u << kBits;
+    __shared__ uint32_t h[kRadixWarps][kDigits];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int d = threadIdx.x; d < kRadixWarps * kRadixDigits; d += kRadixThreads) (&h[0][0])[d] = 0;
+    for (int d = threadIdx.x; d < kRadixWarps * (int)kDigits; d += kRadixThreads) (&h[0][0])[d] = 0;
     const uint32_t base = blockIdx.x * kRadixTile + warp * kRadixWarpTile;
     uint32_t dig[kRadixItems];
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
         const uint32_t i = base + r * 32 + lane;
-        dig[r] = i < n ? (uint32_t)((keys[i] >> shift) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
+        dig[r] = i < n ? (uint32_t)((keys[i] >> shift) & (kDigits - 1)) : kDigits;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r)
-        if (dig[r] < kRadixDigits) atomicAdd(&h[warp][dig[r]], 1u);
+        if (dig[r] < kDigits) atomicAdd(&h[warp][dig[r]], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < kRadixDigits; d += kRadixThreads) {
+    for (int d = threadIdx.x; d < (int)kDigits; d += kRadixThreads) {
         uint32_t s = 0;
 #pragma unroll
         for (int w = 0; w < kRadixWarps; ++w) s += h[w][d];
@@ -157,19 +162,21 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const K *__restric
     }
 }
 
-template <typename K>
+template <typename K, int kBits>
 __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ offs,
     uint32_t nblocks, const uint32_t *__restrict__ gsrc, uint32_t *__restrict__ gdst) {
-    __shared__ uint32_t wcnt[kRadixWarps][kRadixDigits];  // running counts, then warp offsets
-    __shared__ uint32_t dstart[kRadixDigits];              // block-local start of each digit
-    __shared__ uint32_t gbase[kRadixDigits];               // global start of each digit
+    constexpr uint32_t kDigits = 1u << kBits;
+    static_assert(kDigits <= (uint32_t)kRadixThreads, "one digit per thread in the digit prefix");
+    __shared__ uint32_t wcnt[kRadixWarps][kDigits];  // running counts, then warp offsets
+    __shared__ uint32_t dstart[kDigits];             // block-local start of each digit
+    __shared__ uint32_t gbase[kDigits];              // global start of each digit
     __shared__ uint32_t total;
     __shared__ K skey[kRadixTile];
     __shared__ uint32_t sval[kRadixTile];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int d = threadIdx.x; d < kRadixWarps * kRadixDigits; d += kRadixThreads) (&wcnt[0][0])[d] = 0;
+    for (int d = threadIdx.x; d < kRadixWarps * (int)kDigits; d += kRadixThreads) (&wcnt[0][0])[d] = 0;
     const uint32_t blk0 = blockIdx.x * kRadixTile;
     const uint32_t base = blk0 + warp * kRadixWarpTile;
     K k[kRadixItems];
@@ -189,44 +196,44 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
     for (int r = 0; r < kRadixItems; ++r) {
         const uint32_t i = base + r * 32 + lane;
         const bool ok = i < n;
-        const uint32_t d = ok ? (uint32_t)((k[r] >> shift) & (kRadixDigits - 1)) : (uint32_t)kRadixDigits;
-        // lanes holding the same digit: agree on all 8 bits, among valid lanes
+        const uint32_t d = ok ? (uint32_t)((k[r] >> shift) & (kDigits - 1)) : kDigits;
+        // lanes holding the same digit: agree on all kBits bits, among valid lanes
         unsigned peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
+        for (int b = 0; b < kBits; ++b) {
             const unsigned m = __ballot_sync(0xffffffffu, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? m : ~m;
         }
-        const uint32_t before = d < kRadixDigits ? wcnt[warp][d] : 0u;
+        const uint32_t before = d < kDigits ? wcnt[warp][d] : 0u;
         __syncwarp();
-        if (d < kRadixDigits && (peers & lt) == 0u) wcnt[warp][d] = before + __popc(peers);
+        if (d < kDigits && (peers & lt) == 0u) wcnt[warp][d] = before + __popc(peers);
         __syncwarp();
         dr[r] = d | ((before + __popc(peers & lt)) << 16);
     }
     __syncthreads();
     // per digit: exclusive prefix over warps, and the digit's block total
     uint32_t tot = 0;
-    {
-        const int d = threadIdx.x;  // kRadixThreads == kRadixDigits
+    const int dt = threadIdx.x;
+    if (dt < (int)kDigits) {
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kRadixWarps; ++w) {
-            const uint32_t c = wcnt[w][d];
-            wcnt[w][d] = run;
+            const uint32_t c = wcnt[w][dt];
+            wcnt[w][dt] = run;
             run += c;
         }
         tot = run;
-        gbase[d] = offs[(size_t)d * nblocks + blockIdx.x];
+        gbase[dt] = offs[(size_t)dt * nblocks + blockIdx.x];
     }
     // block-local digit starts
     const uint32_t ex = block_excl_scan(tot, &total);
-    dstart[threadIdx.x] = ex;
+    if (dt < (int)kDigits) dstart[dt] = ex;
     __syncthreads();
     // block-local sort in shared memory
 #pragma unroll
     for (int r = 0; r < kRadixItems; ++r) {
         const uint32_t d = dr[r] & 0xFFFFu;
-        if (d < kRadixDigits) {
+        if (d < kDigits) {
             const uint32_t lp = dstart[d] + wcnt[warp][d] + (dr[r] >> 16);
             skey[lp] = k[r];
             sval[lp] = v[r];
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
 #pragma unroll 4
     for (uint32_t p = threadIdx.x; p < cnt; p += kRadixThreads) {
         const K key = skey[p];
-        const uint32_t d = (uint32_t)((key >> shift) & (kRadixDigits - 1));
+        const uint32_t d = (uint32_t)((key >> shift) & (kDigits - 1));
         const uint32_t g = gbase[d] + (p - dstart[d]);
         const uint32_t val = sval[p];
         kout[g] = key;
@@ -254,6 +261,20 @@ size_t radix_scratch_words(size_t n) {
     return 2 * hist + 1 + scan_scratch_words(hist);
 }
 
+// one pass over digit bits [shift, shift + kBits)
+template <typename K, int kBits>
+static int radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, uint32_t n, int shift, uint32_t nb,
+                      uint32_t *scratch, const uint32_t *gsrc, uint32_t *gdst, cudaStream_t st) {
+    const uint32_t hn = (1u << kBits) * nb;
+    uint32_t *hist = scratch;
+    uint32_t *offs = scratch + hn;
+    uint32_t *sc = scratch + 2 * hn + 1;
+    k_radix_hist<K, kBits><<<nb, kRadixThreads, 0, st>>>(ki, n, shift, hist, nb);
+    int launched = 1 + exclusive_scan(hist, nullptr, offs, hn, sc, st);
+    k_radix_scatter<K, kBits><<<nb, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, offs, nb, gsrc, gdst);
+    return launched + 1;
+}
+
 template <typename K>
 static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int bits,
                       uint32_t *scratch, cudaStream_t st, int *in_second, const uint32_t *gsrc,
@@ -262,22 +283,27 @@ static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int 
     if (n == 0 || bits <= 0) return 0;
     int launched = 0;
     const uint32_t nb = (n + kRadixTile - 1) / kRadixTile;
-    const uint32_t hn = kRadixDigits * nb;
-    uint32_t *hist = scratch;
-    uint32_t *offs = scratch + hn;
-    uint32_t *sc = scratch + 2 * hn + 1;
+    // fewest passes of at most 8 bits, near-equal widths (4 bits at least)
+    const int passes = (bits + kRadixMaxBits - 1) / kRadixMaxBits;
     int cur = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int p = 0, shift = 0; p < passes; ++p) {
         const K *ki = cur ? k1 : k0;
         const uint32_t *vi = cur ? v1 : v0;
         K *ko = cur ? k0 : k1;
         uint32_t *vo = cur ? v0 : v1;
-        const bool last = shift + 8 >= bits;
-        k_radix_hist<K><<<nb, kRadixThreads, 0, st>>>(ki, n, shift, hist, nb);
-        launched += 1 + exclusive_scan(hist, nullptr, offs, hn, sc, st);
-        k_radix_scatter<K><<<nb, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, offs, nb,
-                                                          last ? gsrc : nullptr, last ? gdst : nullptr);
-        launched += 1;
+        const int left = bits - shift;
+        const int width = std::max(4, (left + (passes - p) - 1) / (passes - p));
+        const bool last = p == passes - 1;
+        const uint32_t *gs = last ? gsrc : nullptr;
+        uint32_t *gd = last ? gdst : nullptr;
+        switch (width) {
+            case 4: launched += radix_pass<K, 4>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
+            case 5: launched += radix_pass<K, 5>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
+            case 6: launched += radix_pass<K, 6>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
+            case 7: launched += radix_pass<K, 7>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
+            default: launched += radix_pass<K, 8>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
+        }
+        shift += width;
         cur ^= 1;
     }
     *in_second = cur;
