@@ -265,7 +265,9 @@ const char *cs_last_error(const cs_ctx *ctx);
 #define CS_DBG_RECORDS 4     /* float [S][16]: u, v, conic A, B, C, opacity, radius,
                                 depth, r, g, b, 0, reach x, reach y (pixel ranges lo | hi
                                 << 16 as float bits), fcut, log2 opacity              */
-#define CS_DBG_DEPTH_KEYS 5  /* uint32 [S]: depth bits in depth order, 0xFFFFFFFF = culled */
+#define CS_DBG_DEPTH_KEYS 5  /* uint32 [S]: depth keys in depth order: float bits of the
+                                depth minus those of the frame's lower depth bound
+                                (from the instance cull), 0xFFFFFFFF = culled      */
 #define CS_DBG_RECTS 6       /* uint16 [S][4]: tile rect x0, y0, x1, y1 (inclusive)    */
 #define CS_DBG_DEPTH_ORDER 7 /* uint32 [S]: splat ids sorted by depth                  */
 #define CS_DBG_PAIR_TILES 8  /* uint16 [P]: tile of each pair, (tile, depth) order     */

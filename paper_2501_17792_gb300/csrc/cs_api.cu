@@ -307,6 +307,9 @@ void cam_params(const cs_ctx *c, const cs_camera *cam, CamParams &p) {
     const double fmax = std::max(cam->fx, cam->fy), fmin = std::min(cam->fx, cam->fy);
     p.cull_sigma_k = (float)(3.0 * std::sqrt(2.0 + (double)p.limx * p.limx + (double)p.limy * p.limy) *
                              (fmax / fmin) * 1.01);
+    // full-range depth keys until the cull has bounded the frame's depths
+    p.key_lo = 0u;
+    p.key_hi = 0xFFFFFFFEu;
     const double tr = (cam->width - cam->cx + margin) / cam->fx;
     const double tl = (cam->cx + margin) / cam->fx;
     const double tb = (cam->height - cam->cy + margin) / cam->fy;
@@ -321,6 +324,13 @@ void cam_params(const cs_ctx *c, const cs_camera *cam, CamParams &p) {
 }
 
 // Add the stage times of event set k (a completed frame) to the running sums.
+// Depth keys of this frame: the cull's bounds of every live depth (float
+// bits); no visible instance leaves an empty range.
+void set_depth_key_range(CamParams &cp, const int32_t *meta) {
+    cp.key_lo = (uint32_t)meta[kMetaZlo];
+    cp.key_hi = std::max((uint32_t)meta[kMetaZhi], cp.key_lo);
+}
+
 int accumulate_stage_times(cs_ctx *ctx, int k) {
     if (!ctx->ev_pending[k]) return CS_OK;
     CS_CUDA(cudaEventSynchronize(ctx->ev[k][kStages]));
@@ -831,6 +841,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         CS_CUDA(cudaStreamSynchronize(st));
         ctx->visible = ctx->h_meta[kMetaVisible];
         ctx->n_groups = ctx->h_meta[kMetaGroups];
+        set_depth_key_range(cp, ctx->h_meta);
         S = ctx->h_meta[kMetaSplats];
         proj_blocks = ctx->h_meta[kMetaBlocks];
         for (int l = 0; l < kMaxLevels; ++l) ctx->per_level[l] = ctx->h_meta[kMetaLevel0 + l];
@@ -861,8 +872,9 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     if (timing) CS_CUDA(cudaEventRecord(ev[3], st));
     // 4. depth sort of the splats (stable, ties by splat id)
     int ob = 0;
-    if (S > 0) launched += radix_sort_u32(ctx->key.p, ctx->ids.p, ctx->key2.p, ctx->ids2.p, (uint32_t)S, 32,
-                                          ctx->scratch.p, st, &ob, ctx->bins.p, ctx->bins_sorted.p);
+    if (S > 0) launched += radix_sort_u32(ctx->key.p, ctx->ids.p, ctx->key2.p, ctx->ids2.p, (uint32_t)S,
+                                          depth_key_bits(cp.key_lo, cp.key_hi), ctx->scratch.p, st, &ob,
+                                          ctx->bins.p, ctx->bins_sorted.p);
     ctx->order_buf = ob;
     uint32_t *order = ob ? ctx->ids2.p : ctx->ids.p;
     uint32_t *sorted_keys = ob ? ctx->key2.p : ctx->key.p;
@@ -1342,6 +1354,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
         CS_CUDA(cudaStreamSynchronize(st));
         visible = ctx->h_meta[kMetaVisible];
         n_groups = ctx->h_meta[kMetaGroups];
+        set_depth_key_range(cp, ctx->h_meta);
         S = ctx->h_meta[kMetaSplats];
         proj_blocks = ctx->h_meta[kMetaBlocks];
         for (int l = 0; l < kMaxLevels; ++l) per_level[l] = ctx->h_meta[kMetaLevel0 + l];
@@ -1358,7 +1371,8 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
         scan_scratch_words((size_t)S + 1) > kStaticScratchWords)
         return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: scratch too small for %lld splats", (long long)S);
     int ob = 0;
-    if (S > 0) launched += radix_sort_u32(key, ids, key2, ids2, (uint32_t)S, 32, scratch, st, &ob, bins, bins_sorted);
+    if (S > 0) launched += radix_sort_u32(key, ids, key2, ids2, (uint32_t)S, depth_key_bits(cp.key_lo, cp.key_hi),
+                                          scratch, st, &ob, bins, bins_sorted);
     uint32_t *order = ob ? ids2 : ids;
     uint32_t *sorted_keys = ob ? key2 : key;
     launched += exclusive_scan_bins(bins_sorted, pair_off, (uint32_t)S, scratch, st);

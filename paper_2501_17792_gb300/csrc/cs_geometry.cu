@@ -120,9 +120,14 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
     extern __shared__ uint8_t grp[];  // [n_inst] group of each instance
     __shared__ int32_t gcount[kMaxTemplates * kMaxLevels];
     __shared__ int32_t gslot[kMaxTemplates * kMaxLevels];
+    __shared__ uint32_t zlo_bits, zhi_bits;
     const int L = lod.n_levels;
     const int n_grp = n_tpl * L;
     for (int g = threadIdx.x; g < n_grp; g += blockDim.x) gcount[g] = 0;
+    if (threadIdx.x == 0) {
+        zlo_bits = 0x7F7FFFFFu;  // FLT_MAX
+        zhi_bits = __float_as_uint(cam.near_z);
+    }
     __syncthreads();
 
     for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
@@ -173,6 +178,21 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
                 if (s > grow) visible = false;
             }
         }
+        if (visible) {
+            // view-depth interval of the instance's splat means: a mean p
+            // lies within reach of the pelvis rest position c (instance
+            // frame), so its depth is within |v| reach of v.c + t_z, v the
+            // depth row of camera o root (Cauchy-Schwarz); widened for
+            // rounding and clipped below at the near plane
+            const TemplateInfo &T = tpls[t];
+            const float czs = Vm[8] * T.rest[0] + Vm[9] * T.rest[1] + Vm[10] * T.rest[2] + Vm[11];
+            const float vn = sqrtf(Vm[8] * Vm[8] + Vm[9] * Vm[9] + Vm[10] * Vm[10]);
+            const float ext = T.reach[lvl] * vn * 1.001f + 1e-3f;
+            const float zl = fmaxf(cam.near_z, (czs - ext) * 0.999f - 1e-3f);
+            const float zh = fmaxf(cam.near_z, (czs + ext) * 1.001f + 1e-3f);
+            atomicMin(&zlo_bits, __float_as_uint(zl));  // positive floats order as their bits
+            atomicMax(&zhi_bits, __float_as_uint(zh));
+        }
         uint8_t g = visible ? (uint8_t)(t * L + lvl) : kHidden;
         grp[i] = g;
         if (visible) atomicAdd(&gcount[g], 1);
@@ -207,6 +227,8 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
         meta[kMetaSplats] = (int32_t)(splat < 0x7fffffffLL ? splat : 0x7fffffffLL);
         for (int l = 0; l < kMaxLevels; ++l) meta[kMetaLevel0 + l] = per_level[l];
         meta[kMetaBlocks] = (int32_t)(blocks < 0x7fffffffLL ? blocks : 0x7fffffffLL);
+        meta[kMetaZlo] = (int32_t)zlo_bits;
+        meta[kMetaZhi] = (int32_t)zhi_bits;
     }
     __syncthreads();
     // stable placement: one warp per group sweeps the instances in order
@@ -700,7 +722,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
             }
         }
     }
-    key[s] = live ? __float_as_uint(tz) : 0xFFFFFFFFu;
+    key[s] = live ? min(max(__float_as_uint(tz), cam.key_lo), cam.key_hi) - cam.key_lo : 0xFFFFFFFFu;
     rect[s] = rc;
     bin[s] = live ? bword : 0u;
 }

@@ -86,7 +86,20 @@ struct CamParams {
     int32_t tiles_x, tiles_y;
     float plane[4][4];     // conservative frustum side planes (camera space, unit normals)
     float cull_sigma_k;    // instance cull: 3D growth per unit of Gaussian scale
+    // depth keys: float bits of the view depth clamped to [key_lo, key_hi]
+    // (bits of bounds of every live depth), minus key_lo; culled = all ones
+    uint32_t key_lo, key_hi;
 };
+
+// Bits of the depth keys of a frame whose live depths lie in float-bit range
+// [lo, hi]: live keys are at most hi - lo, the culled key (all ones in these
+// bits) must exceed them.
+inline int depth_key_bits(uint32_t lo, uint32_t hi) {
+    const uint64_t span = (uint64_t)(hi - lo) + 2u;  // live keys 0 .. hi - lo, then the culled key
+    int b = 1;
+    while (b < 32 && (1ull << b) < span) ++b;
+    return b;
+}
 
 struct LodParams {
     int32_t n_levels;
@@ -217,7 +230,9 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
 
 // meta words written by the cull kernel and read back by the host
 enum MetaIndex {
-    kMetaVisible = 0, kMetaGroups = 1, kMetaSplats = 2, kMetaLevel0 = 3, kMetaBlocks = 7, kMetaWords = 12
+    kMetaVisible = 0, kMetaGroups = 1, kMetaSplats = 2, kMetaLevel0 = 3, kMetaBlocks = 7,
+    kMetaZlo = 8, kMetaZhi = 9,  // float bits of a lower / upper bound of every live splat depth
+    kMetaWords = 12
 };
 
 // Every launch_* function returns the number of kernels it launched.

@@ -110,11 +110,12 @@ int exclusive_scan_bins(const uint32_t *bins, uint32_t *out, uint32_t n, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort, digits of up to 8 bits, reduce-then-scan per pass
+// stable LSD radix sort, digits of up to 9 bits, reduce-then-scan per pass
 //
-// A sort of b-bit keys takes ceil(b / 8) passes of near-equal digit width
-// (13-bit tile keys: 7 + 6 bits; 32-bit depth keys: 4 x 8): a narrower
-// digit needs fewer ballots to rank and smaller count tables.  A block owns
+// A sort of b-bit keys takes ceil(b / 9) passes of near-equal digit width
+// (13-bit tile keys: 7 + 6 bits; 26-bit depth keys: 9 + 9 + 8; 32-bit keys:
+// 4 x 8): a narrower digit needs fewer ballots to rank and smaller count
+// tables, a wider one may save a pass.  A block owns
 // 4,096 consecutive elements; warp w owns 512 of them, read in 16 rounds of
 // 32 consecutive elements (coalesced, all loads issued before any
 // shared-memory update).  Histogram pass: per-warp digit counts (shared
@@ -131,7 +132,7 @@ constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kRadixItems = 16;                              // per lane
 constexpr int kRadixTile = kRadixThreads * kRadixItems;      // per block (4,096)
 constexpr int kRadixWarpTile = 32 * kRadixItems;             // per warp (512)
-constexpr int kRadixMaxBits = 8;
+constexpr int kRadixMaxBits = 9;
 constexpr int kRadixDigits = 1 << kRadixMaxBits;             // largest digit range
 
 template <typename K, int kBits>
@@ -168,13 +169,16 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
     uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ offs,
     uint32_t nblocks, const uint32_t *__restrict__ gsrc, uint32_t *__restrict__ gdst) {
     constexpr uint32_t kDigits = 1u << kBits;
-    static_assert(kDigits <= (uint32_t)kRadixThreads, "one digit per thread in the digit prefix");
+    constexpr int kPer = kDigits > (uint32_t)kRadixThreads ? (int)kDigits / kRadixThreads : 1;  // digits per thread
     __shared__ uint32_t wcnt[kRadixWarps][kDigits];  // running counts, then warp offsets
     __shared__ uint32_t dstart[kDigits];             // block-local start of each digit
     __shared__ uint32_t gbase[kDigits];              // global start of each digit
     __shared__ uint32_t total;
-    __shared__ K skey[kRadixTile];
-    __shared__ uint32_t sval[kRadixTile];
+    // block-local sort buffers (dynamic: with 9-bit digits the CTA needs
+    // more than the 48 KB of static shared memory)
+    extern __shared__ __align__(16) unsigned char radix_dyn[];
+    uint32_t *sval = reinterpret_cast<uint32_t *>(radix_dyn);
+    K *skey = reinterpret_cast<K *>(radix_dyn + kRadixTile * sizeof(uint32_t));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int d = threadIdx.x; d < kRadixWarps * (int)kDigits; d += kRadixThreads) (&wcnt[0][0])[d] = 0;
     const uint32_t blk0 = blockIdx.x * kRadixTile;
@@ -211,23 +215,34 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
         dr[r] = d | ((before + __popc(peers & lt)) << 16);
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps, and the digit's block total
-    uint32_t tot = 0;
-    const int dt = threadIdx.x;
-    if (dt < (int)kDigits) {
-        uint32_t run = 0;
+    // per digit (thread t: digits t kPer .. t kPer + kPer - 1): exclusive
+    // prefix over warps, and the digit's block total
+    uint32_t tot = 0, dtot[kPer];
 #pragma unroll
-        for (int w = 0; w < kRadixWarps; ++w) {
-            const uint32_t c = wcnt[w][dt];
-            wcnt[w][dt] = run;
-            run += c;
+    for (int j = 0; j < kPer; ++j) {
+        const int d = threadIdx.x * kPer + j;
+        dtot[j] = 0;
+        if (d < (int)kDigits) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kRadixWarps; ++w) {
+                const uint32_t c = wcnt[w][d];
+                wcnt[w][d] = run;
+                run += c;
+            }
+            dtot[j] = run;
+            tot += run;
+            gbase[d] = offs[(size_t)d * nblocks + blockIdx.x];
         }
-        tot = run;
-        gbase[dt] = offs[(size_t)dt * nblocks + blockIdx.x];
     }
     // block-local digit starts
-    const uint32_t ex = block_excl_scan(tot, &total);
-    if (dt < (int)kDigits) dstart[dt] = ex;
+    uint32_t ex = block_excl_scan(tot, &total);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int d = threadIdx.x * kPer + j;
+        if (d < (int)kDigits) dstart[d] = ex;
+        ex += dtot[j];
+    }
     __syncthreads();
     // block-local sort in shared memory
 #pragma unroll
@@ -269,9 +284,17 @@ static int radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, uint
     uint32_t *hist = scratch;
     uint32_t *offs = scratch + hn;
     uint32_t *sc = scratch + 2 * hn + 1;
+    constexpr int kDyn = kRadixTile * (int)(sizeof(uint32_t) + sizeof(K));
+    static int configured_device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_device != dev) {
+        cudaFuncSetAttribute(k_radix_scatter<K, kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+        configured_device = dev;
+    }
     k_radix_hist<K, kBits><<<nb, kRadixThreads, 0, st>>>(ki, n, shift, hist, nb);
     int launched = 1 + exclusive_scan(hist, nullptr, offs, hn, sc, st);
-    k_radix_scatter<K, kBits><<<nb, kRadixThreads, 0, st>>>(ki, vi, ko, vo, n, shift, offs, nb, gsrc, gdst);
+    k_radix_scatter<K, kBits><<<nb, kRadixThreads, kDyn, st>>>(ki, vi, ko, vo, n, shift, offs, nb, gsrc, gdst);
     return launched + 1;
 }
 
@@ -283,7 +306,7 @@ static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int 
     if (n == 0 || bits <= 0) return 0;
     int launched = 0;
     const uint32_t nb = (n + kRadixTile - 1) / kRadixTile;
-    // fewest passes of at most 8 bits, near-equal widths (4 bits at least)
+    // fewest passes of at most 9 bits, near-equal widths (4 bits at least)
     const int passes = (bits + kRadixMaxBits - 1) / kRadixMaxBits;
     int cur = 0;
     for (int p = 0, shift = 0; p < passes; ++p) {
@@ -301,7 +324,8 @@ static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int 
             case 5: launched += radix_pass<K, 5>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
             case 6: launched += radix_pass<K, 6>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
             case 7: launched += radix_pass<K, 7>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
-            default: launched += radix_pass<K, 8>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
+            case 8: launched += radix_pass<K, 8>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
+            default: launched += radix_pass<K, 9>(ki, vi, ko, vo, n, shift, nb, scratch, gs, gd, st); break;
         }
         shift += width;
         cur ^= 1;

@@ -406,6 +406,15 @@ def test_paper_scale_sort_properties(paper_scene):
     assert np.array_equal(np.sort(order), np.arange(order.size, dtype=order.dtype))
     live = int((keys != 0xFFFFFFFF).sum())
     assert live == st["splats_live"]
+    # live keys are the depth's float bits minus one per-frame offset (the
+    # cull's depth bound): no live depth was clamped, and the key width the
+    # sort uses (the bits of the largest live key) is below 32
+    rec32 = r.debug("records")
+    lk = keys[keys != 0xFFFFFFFF].astype(np.int64)
+    db = rec32[order[keys != 0xFFFFFFFF].astype(np.int64), 7].astype(np.float32).view(np.uint32).astype(np.int64)
+    off = db - lk
+    assert (off == off[0]).all() and off[0] > 0
+    assert int(lk.max()) < 2 ** 28
     rects = r.debug("rects").astype(np.int64)
     ntiles = (rects[:, 2] - rects[:, 0] + 1) * (rects[:, 3] - rects[:, 1] + 1)
     lv = np.zeros(order.size, bool)
