@@ -93,7 +93,7 @@ struct cs_ctx {
 
     // last frame
     int64_t S = 0, P = 0;
-    int n_groups = 0, visible = 0, tiles_x = 0, tiles_y = 0;
+    int n_groups = 0, visible = 0, tiles_x = 0, tiles_y = 0, frame_w = 0, frame_h = 0;
     int order_buf = 0, pair_buf = 0;  // which ping-pong half holds the result
     int per_level[kMaxLevels] = {0, 0, 0, 0};
     int launches = 0;  // kernels launched by the last cs_render
@@ -808,6 +808,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     const int I = ctx->n_inst;
     const bool timing = ctx->stage_timing != 0;
     ctx->tiles_x = cp.tiles_x;
+    ctx->frame_w = cam->width;
+    ctx->frame_h = cam->height;
     ctx->tiles_y = cp.tiles_y;
     ctx->timed = false;
     int launched = 0;
@@ -859,7 +861,6 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->ids, Sa, "splat ids"));
     CS_TRY(ensure(ctx, ctx->key2, Sa, "depth keys (ping-pong)"));
     CS_TRY(ensure(ctx, ctx->ids2, Sa, "splat ids (ping-pong)"));
-    CS_TRY(ensure(ctx, ctx->rect, Sa, "tile rects"));
     CS_TRY(ensure(ctx, ctx->bins, Sa, "bin words"));
     CS_TRY(ensure(ctx, ctx->bins_sorted, Sa, "bin words in depth order"));
     CS_TRY(ensure(ctx, ctx->pair_off, Sa + 1, "pair offsets"));
@@ -868,13 +869,13 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     if (S > 0)
         launched += launch_project(proj_blocks, ctx->groups.p, ctx->n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                        ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
-                       ctx->rec.p, ctx->key.p, ctx->ids.p, ctx->rect.p, ctx->bins.p, st);
+                       ctx->rec.p, ctx->key.p, ctx->bins.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[3], st));
     // 4. depth sort of the splats (stable, ties by splat id)
     int ob = 0;
     if (S > 0) launched += radix_sort_u32(ctx->key.p, ctx->ids.p, ctx->key2.p, ctx->ids2.p, (uint32_t)S,
                                           depth_key_bits(cp.key_lo, cp.key_hi), ctx->scratch.p, st, &ob,
-                                          ctx->bins.p, ctx->bins_sorted.p);
+                                          ctx->bins.p, ctx->bins_sorted.p, true);
     ctx->order_buf = ob;
     uint32_t *order = ob ? ctx->ids2.p : ctx->ids.p;
     uint32_t *sorted_keys = ob ? ctx->key2.p : ctx->key.p;
@@ -1199,7 +1200,17 @@ int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size
         case CS_DBG_GROUPS: src = ctx->groups.p; size = (size_t)ctx->n_groups * sizeof(Group); break;
         case CS_DBG_RECORDS: src = ctx->rec.p; size = (size_t)ctx->S * kRecVec * sizeof(float4); break;
         case CS_DBG_DEPTH_KEYS: src = ctx->order_buf ? ctx->key2.p : ctx->key.p; size = (size_t)ctx->S * 4; break;
-        case CS_DBG_RECTS: src = ctx->rect.p; size = (size_t)ctx->S * 8; break;
+        case CS_DBG_RECTS:
+            // recomputed from the records of the last frame
+            if (ctx->S > 0) {
+                CS_TRY(ensure(ctx, ctx->rect, (size_t)ctx->S, "tile rects"));
+                launch_debug_rects((int)ctx->S, ctx->rec.p, ctx->bins.p, ctx->frame_w, ctx->frame_h, ctx->rect.p,
+                                   ctx->stream);
+                CS_CUDA(cudaGetLastError());
+            }
+            src = ctx->rect.p;
+            size = (size_t)ctx->S * 8;
+            break;
         case CS_DBG_DEPTH_ORDER: src = ctx->order_buf ? ctx->ids2.p : ctx->ids.p; size = (size_t)ctx->S * 4; break;
         case CS_DBG_PAIR_TILES: src = ctx->pair_buf ? ctx->ptile2.p : ctx->ptile.p; size = (size_t)ctx->P * 2; break;
         case CS_DBG_PAIR_SPLATS: src = ctx->pair_buf ? ctx->pval2.p : ctx->pval.p; size = (size_t)ctx->P * 4; break;
@@ -1240,8 +1251,7 @@ constexpr size_t kOffKey = kOffRec + a256(kStaticSplats * kRecVec * sizeof(float
 constexpr size_t kOffIds = kOffKey + a256(kStaticSplats * 4);
 constexpr size_t kOffKey2 = kOffIds + a256(kStaticSplats * 4);
 constexpr size_t kOffIds2 = kOffKey2 + a256(kStaticSplats * 4);
-constexpr size_t kOffRect = kOffIds2 + a256(kStaticSplats * 4);
-constexpr size_t kOffBins = kOffRect + a256(kStaticSplats * sizeof(uint2));
+constexpr size_t kOffBins = kOffIds2 + a256(kStaticSplats * 4);
 constexpr size_t kOffBinsSorted = kOffBins + a256(kStaticSplats * 4);
 constexpr size_t kOffPairOff = kOffBinsSorted + a256(kStaticSplats * 4);
 constexpr size_t kOffPtile = kOffPairOff + a256((kStaticSplats + 1) * 4);
@@ -1328,7 +1338,6 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     uint32_t *ids = reinterpret_cast<uint32_t *>(base + kOffIds);
     uint32_t *key2 = reinterpret_cast<uint32_t *>(base + kOffKey2);
     uint32_t *ids2 = reinterpret_cast<uint32_t *>(base + kOffIds2);
-    uint2 *rect = reinterpret_cast<uint2 *>(base + kOffRect);
     uint32_t *bins = reinterpret_cast<uint32_t *>(base + kOffBins);
     uint32_t *bins_sorted = reinterpret_cast<uint32_t *>(base + kOffBinsSorted);
     uint32_t *pair_off = reinterpret_cast<uint32_t *>(base + kOffPairOff);
@@ -1366,13 +1375,13 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     if (S > 0)
         launched += launch_project(proj_blocks, ctx->groups.p, n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                                    ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
-                                   rec, key, ids, rect, bins, st);
+                                   rec, key, bins, st);
     if (radix_scratch_words((size_t)std::max<int64_t>(S, 1)) > kStaticScratchWords ||
         scan_scratch_words((size_t)S + 1) > kStaticScratchWords)
         return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: scratch too small for %lld splats", (long long)S);
     int ob = 0;
     if (S > 0) launched += radix_sort_u32(key, ids, key2, ids2, (uint32_t)S, depth_key_bits(cp.key_lo, cp.key_hi),
-                                          scratch, st, &ob, bins, bins_sorted);
+                                          scratch, st, &ob, bins, bins_sorted, true);
     uint32_t *order = ob ? ids2 : ids;
     uint32_t *sorted_keys = ob ? key2 : key;
     launched += exclusive_scan_bins(bins_sorted, pair_off, (uint32_t)S, scratch, st);

@@ -494,8 +494,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ Cloc,
     const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,
     CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
-    uint32_t *__restrict__ key, uint32_t *__restrict__ ids, uint2 *__restrict__ rect,
-    uint32_t *__restrict__ bin) {
+    uint32_t *__restrict__ key, uint32_t *__restrict__ bin) {
     __shared__ float4 sB[kJoints * 3];
     __shared__ int s_group;
     __shared__ __align__(16) unsigned char s_tc[kStore == kStoreBf16 ? kSkinTcBytes : 16];
@@ -532,7 +531,6 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
         const int sub = T.lod_idx_off[G.lvl];
         gsrc = sub >= 0 ? (int)__ldg(ta.lod_idx + sub + gg) : gg;
         gi = T.g_off + gsrc;
-        ids[s] = (uint32_t)s;
     }
 
     // LBS (CrowdSplat Sec. 2): M = sum_k w_k B_{idx_k} (instance local)
@@ -577,7 +575,6 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     const float tz = v2.x * lx + v2.y * ly + v2.z * lz + v2.w;
 
     bool live = tz > cam.near_z;  // also false for NaN
-    uint2 rc = make_uint2(0u, 0u);
     uint32_t nt = 0, bword = 0;
     if (live) {
         // covariance in camera space: Wc = (V_R A) (m^2 Sigma) (V_R A)^T,
@@ -674,11 +671,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
                 const bool small = ax0 <= ax1 && ay0 <= ay1 && (ax1 >> 4) - wx0 < 3 && (ay1 >> 4) - wy0 < 3;
                 bword = small ? ((uint32_t)wx0 | ((uint32_t)wy0 << 8) | (mask << 16)) : (kBinLarge | nt);
             }
-            if (live) {
-                rc = make_uint2((uint32_t)(px0 >> 4) | ((uint32_t)(py0 >> 4) << 16),
-                                (uint32_t)(px1 >> 4) | ((uint32_t)(py1 >> 4) << 16));
-                live = nt > 0;
-            }
+            live = live && nt > 0;
             if (live) {
                 // colour: SH at the viewing direction (camera centre -> mean)
                 float ddx, ddy, ddz;
@@ -723,7 +716,6 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
         }
     }
     key[s] = live ? min(max(__float_as_uint(tz), cam.key_lo), cam.key_hi) - cam.key_lo : 0xFFFFFFFFu;
-    rect[s] = rc;
     bin[s] = live ? bword : 0u;
 }
 
@@ -731,14 +723,38 @@ int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_
                     const float *B, const float *V, const float *Cloc, const float *root,
                     const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
                     const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
-                    uint32_t *ids, uint2 *rect, uint32_t *bin, cudaStream_t st) {
+                    uint32_t *bin, cudaStream_t st) {
     if (n_blocks <= 0) return 0;
     if (ta.storage == kStoreBf16)
         k_project<kStoreBf16><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, vis, B, V, Cloc, root, ta, tpls,
-                                                                cam, lod, skin_mode, sh_frame, rec, key, ids, rect, bin);
+                                                                cam, lod, skin_mode, sh_frame, rec, key, bin);
     else
         k_project<kStoreFp32><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, vis, B, V, Cloc, root, ta, tpls,
-                                                                cam, lod, skin_mode, sh_frame, rec, key, ids, rect, bin);
+                                                                cam, lod, skin_mode, sh_frame, rec, key, bin);
+    return 1;
+}
+
+__global__ void __launch_bounds__(256) k_debug_rects(int n, const float4 *__restrict__ rec,
+                                                     const uint32_t *__restrict__ bins, int W, int H,
+                                                     uint2 *__restrict__ rect) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint2 rc = make_uint2(0u, 0u);
+    if (bins[s] != 0u) {
+        const float4 r0 = rec[(size_t)s * kRecVec], r1 = rec[(size_t)s * kRecVec + 1];
+        int px0, px1, py0, py1;
+        box_range(r0.x, r1.z, W, px0, px1);
+        box_range(r0.y, r1.z, H, py0, py1);
+        rc = make_uint2((uint32_t)(px0 >> 4) | ((uint32_t)(py0 >> 4) << 16),
+                        (uint32_t)(px1 >> 4) | ((uint32_t)(py1 >> 4) << 16));
+    }
+    rect[s] = rc;
+}
+
+int launch_debug_rects(int n_splats, const float4 *rec, const uint32_t *bins, int W, int H, uint2 *rect,
+                       cudaStream_t st) {
+    if (n_splats <= 0) return 0;
+    k_debug_rects<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, rec, bins, W, H, rect);
     return 1;
 }
 

@@ -261,7 +261,11 @@ int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_
                     const float *B, const float *V, const float *Cloc, const float *root,
                     const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
                     const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
-                    uint32_t *ids, uint2 *rect, uint32_t *bin, cudaStream_t st);
+                    uint32_t *bin, cudaStream_t st);
+// Tile rectangle of each splat's support box (debug view; recomputed from the
+// records: x0 | y0 << 16, x1 | y1 << 16; zero for splats without pairs).
+int launch_debug_rects(int n_splats, const float4 *rec, const uint32_t *bins, int W, int H, uint2 *rect,
+                       cudaStream_t st);
 
 // ---- sort and binning (cs_sort.cu) ----
 // scratch words needed by exclusive_scan / radix_sort for n elements
@@ -277,9 +281,11 @@ int exclusive_scan_bins(const uint32_t *bins, uint32_t *out, uint32_t n, uint32_
 // result is in (k0, v0), 1 when in (k1, v1).  Returns kernels launched.
 // When gather_dst is non-null, the last pass also writes, for every output
 // position, gather_src[value] to gather_dst (a payload in sorted order).
+// With iota_values, the values of the input are taken to be 0 .. n - 1 (v0
+// is not read, only written as a ping-pong buffer).
 int radix_sort_u32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t n, int bits,
                    uint32_t *scratch, cudaStream_t st, int *in_second,
-                   const uint32_t *gather_src = nullptr, uint32_t *gather_dst = nullptr);
+                   const uint32_t *gather_src = nullptr, uint32_t *gather_dst = nullptr, bool iota_values = false);
 int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint32_t n, int bits,
                    uint32_t *scratch, cudaStream_t st, int *in_second);
 int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,

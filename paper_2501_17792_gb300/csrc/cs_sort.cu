@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
         const uint32_t i = base + r * 32 + lane;
         const bool ok = i < n;
         k[r] = ok ? kin[i] : (K)0;
-        v[r] = ok ? vin[i] : 0u;
+        v[r] = ok ? (vin ? vin[i] : i) : 0u;
     }
     __syncthreads();
     // stable rank within the warp's 512 elements; packed as digit | rank << 16
@@ -301,7 +301,7 @@ static int radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, uint
 template <typename K>
 static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int bits,
                       uint32_t *scratch, cudaStream_t st, int *in_second, const uint32_t *gsrc,
-                      uint32_t *gdst) {
+                      uint32_t *gdst, bool iota_values) {
     *in_second = 0;
     if (n == 0 || bits <= 0) return 0;
     int launched = 0;
@@ -311,7 +311,7 @@ static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int 
     int cur = 0;
     for (int p = 0, shift = 0; p < passes; ++p) {
         const K *ki = cur ? k1 : k0;
-        const uint32_t *vi = cur ? v1 : v0;
+        const uint32_t *vi = p == 0 && iota_values ? nullptr : (cur ? v1 : v0);
         K *ko = cur ? k0 : k1;
         uint32_t *vo = cur ? v0 : v1;
         const int left = bits - shift;
@@ -336,13 +336,14 @@ static int radix_sort(K *k0, uint32_t *v0, K *k1, uint32_t *v1, uint32_t n, int 
 
 int radix_sort_u32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t n, int bits,
                    uint32_t *scratch, cudaStream_t st, int *in_second, const uint32_t *gather_src,
-                   uint32_t *gather_dst) {
-    return radix_sort<uint32_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second, gather_src, gather_dst);
+                   uint32_t *gather_dst, bool iota_values) {
+    return radix_sort<uint32_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second, gather_src, gather_dst,
+                                iota_values);
 }
 
 int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint32_t n, int bits,
                    uint32_t *scratch, cudaStream_t st, int *in_second) {
-    return radix_sort<uint16_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second, nullptr, nullptr);
+    return radix_sort<uint16_t>(k0, v0, k1, v1, n, bits, scratch, st, in_second, nullptr, nullptr, false);
 }
 
 // ---------------------------------------------------------------------------
