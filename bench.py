@@ -117,21 +117,27 @@ class ClockSampler:
 
 def stage_bytes(st, n_inst, tpl_bytes, pixels):
     S, P = st["splats"], st["pairs"]
+    live = st.get("splats_live", S) or S
     V = st["instances_visible"]
-    sort_passes_depth = 4
-    sort_passes_tile = math.ceil(max(1, math.ceil(math.log2(max(2, st["tiles_x"] * st["tiles_y"])))) / 8)
+    # radix passes: ceil(bits / 9) (digits of at most 9 bits)
+    passes_depth = max(1, math.ceil(max(1, st.get("depth_key_bits", 32)) / 9))
+    tile_bits = max(1, math.ceil(math.log2(max(2, st["tiles_x"] * st["tiles_y"]))))
+    passes_tile = math.ceil(tile_bits / 9)
     return {
         "fk": n_inst * (4 + 72 * 4 + 24 * 48),
         "cull_lod": n_inst * (4 + 48 + 48 + 16 + 4),
         # template attributes once (shared, L2-resident across a group) +
-        # per-instance transforms + per-splat outputs (record 64 B, key 4,
-        # id 4, rect 8, bin word 4)
-        "skin_project": tpl_bytes + V * (24 * 48 + 64) + S * 84,
-        # per pass: keys read by the histogram, key+value read and written
-        "depth_sort": S * sort_passes_depth * (4 + 8 + 8),
-        # order + gathered tile count (scan: read twice), rect, pair writes
-        "pair_emit": S * (4 + 4 + 4 + 4 + 8 + 8) + P * 6,
-        "tile_sort": P * sort_passes_tile * (2 + 6 + 6),
+        # per-instance transforms + per-splat key and bin word + the 64 B
+        # record of every live splat
+        "skin_project": tpl_bytes + V * (24 * 48 + 64) + S * (4 + 4) + live * 64,
+        # per pass: keys read by the histogram, key+value read and written;
+        # the first pass reads no values (they are the indices), the last
+        # writes the bin words in depth order (gathered)
+        "depth_sort": S * (passes_depth * (4 + 8 + 8) - 4 + 8),
+        # scan: bin words read twice, offsets written; emit: offsets, order
+        # and bin words read, 6 B per pair written
+        "pair_emit": S * (4 + 4 + 4 + 4 + 4 + 4) + P * 6,
+        "tile_sort": P * passes_tile * (2 + 6 + 6),
         "tile_ranges": P * 2 * 2,
         # each pair: splat id + 64 B record; each pixel: 16 B written
         "blend": P * (4 + 64) + pixels * 16,

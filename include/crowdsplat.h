@@ -127,6 +127,7 @@ typedef struct {
     int64_t pairs;                  /* (tile, splat) pairs sorted and blended         */
     int32_t tiles_x, tiles_y;
     int32_t kernel_launches;        /* CUDA kernels this frame launched               */
+    int32_t depth_key_bits;         /* bits of the depth keys the depth sort ranked   */
 } cs_frame_stats;
 
 typedef struct {

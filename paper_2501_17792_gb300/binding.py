@@ -51,13 +51,14 @@ class FrameStats(C.Structure):
     _fields_ = [("instances", C.c_int32), ("instances_visible", C.c_int32),
                 ("instances_per_level", C.c_int32 * 4), ("splats", C.c_int64),
                 ("splats_live", C.c_int64), ("pairs", C.c_int64), ("tiles_x", C.c_int32),
-                ("tiles_y", C.c_int32), ("kernel_launches", C.c_int32)]
+                ("tiles_y", C.c_int32), ("kernel_launches", C.c_int32), ("depth_key_bits", C.c_int32)]
 
     def as_dict(self) -> dict:
         return dict(instances=self.instances, instances_visible=self.instances_visible,
                     instances_per_level=list(self.instances_per_level), splats=self.splats,
                     splats_live=self.splats_live, pairs=self.pairs, tiles_x=self.tiles_x,
-                    tiles_y=self.tiles_y, kernel_launches=self.kernel_launches)
+                    tiles_y=self.tiles_y, kernel_launches=self.kernel_launches,
+                    depth_key_bits=self.depth_key_bits)
 
 
 class Grads(C.Structure):

@@ -963,6 +963,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         stats->tiles_x = cp.tiles_x;
         stats->tiles_y = cp.tiles_y;
         stats->kernel_launches = launched;
+        stats->depth_key_bits = S > 0 ? depth_key_bits(cp.key_lo, cp.key_hi) : 0;
     }
     return CS_OK;
 }
@@ -1423,6 +1424,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
         stats->tiles_x = cp.tiles_x;
         stats->tiles_y = cp.tiles_y;
         stats->kernel_launches = launched;
+        stats->depth_key_bits = S > 0 ? depth_key_bits(cp.key_lo, cp.key_hi) : 0;
     }
     return CS_OK;
 }
