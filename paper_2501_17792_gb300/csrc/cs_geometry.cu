@@ -654,22 +654,20 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
                 ax1 = min(ax1, px1);
                 ay0 = max(ay0, py0);
                 ay1 = min(ay1, py1);
-                // tiles holding a pixel the compositing would use; a 3x3
-                // window of them is kept as a mask (bin word)
-                const int wx0 = ax0 >> 4, wy0 = ay0 >> 4;
-                uint32_t mask = 0;
-                for (int yy = wy0; yy <= (ay1 >> 4) && ay0 <= ay1; ++yy) {
-                    const int qy0 = max(yy * kTile, ay0), qy1 = min(yy * kTile + kTile - 1, ay1);
-                    for (int xx = wx0; xx <= (ax1 >> 4) && ax0 <= ax1; ++xx) {
-                        const int qx0 = max(xx * kTile, ax0), qx1 = min(xx * kTile + kTile - 1, ax1);
-                        if (splat_rect_hits(u, v, cA, cB, cC, fcut, qx0, qx1, qy0, qy1)) {
-                            ++nt;
-                            if (xx - wx0 < 3 && yy - wy0 < 3) mask |= 1u << ((yy - wy0) * 3 + (xx - wx0));
-                        }
+                // the tiles the reach box meets: a 3x3 window of them is kept
+                // as a mask (bin word), larger boxes as a count
+                if (ax0 <= ax1 && ay0 <= ay1) {
+                    const int wx0 = ax0 >> 4, wy0 = ay0 >> 4;
+                    const int nx = (ax1 >> 4) - wx0 + 1, ny = (ay1 >> 4) - wy0 + 1;
+                    nt = (uint32_t)(nx * ny);
+                    if (nx <= 3 && ny <= 3) {
+                        const uint32_t row = (1u << nx) - 1u;
+                        const uint32_t mask = row | (ny > 1 ? row << 3 : 0u) | (ny > 2 ? row << 6 : 0u);
+                        bword = (uint32_t)wx0 | ((uint32_t)wy0 << 8) | (mask << 16);
+                    } else {
+                        bword = kBinLarge | nt;
                     }
                 }
-                const bool small = ax0 <= ax1 && ay0 <= ay1 && (ax1 >> 4) - wx0 < 3 && (ay1 >> 4) - wy0 < 3;
-                bword = small ? ((uint32_t)wx0 | ((uint32_t)wy0 << 8) | (mask << 16)) : (kBinLarge | nt);
             }
             live = live && nt > 0;
             if (live) {

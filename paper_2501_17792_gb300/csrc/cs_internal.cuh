@@ -138,46 +138,22 @@ __device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v 
 __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
 
 // ---------------------------------------------------------------------------
-// Exact (conservative) splat-rectangle test shared by binning and blending.
+// Reach of a splat: where it can contribute.
 //
 // A splat contributes to a pixel only where alpha = o e^q >= 1/255, i.e. where
 // f(d) = A dx^2 + 2 B dx dy + C dy^2 <= fcut = 2 ln(255 o) (d = pixel centre -
-// splat centre, conic (A, B, C)).  splat_rect_hits() tells whether f reaches
-// fcut + 2 * kAlphaMargin anywhere on the continuous rectangle spanned by the
-// pixel centres [px0, px1] x [py0, py1]: the minimum of the positive-definite
-// form over a rectangle is 0 if the centre is inside, else it lies on an
-// edge, where it is a clamped 1-D quadratic.  A rectangle that fails holds no
-// pixel the compositing would use (the margin absorbs FP32 rounding), so
-// dropping it leaves every pixel unchanged.  Explicitly rounded intrinsics
-// keep the result bit-identical in every kernel that calls it.
+// splat centre, conic (A, B, C)).  The axis-aligned extent of that ellipse,
+// widened by kAlphaMargin in the exponent (FP32 rounding) and clipped to the
+// support box, is the splat's reach box; binning keeps every tile the reach
+// box meets, and the compositing's warp masks test the reach box against
+// each 8x4 pixel block.  A tile or block outside it holds no pixel the
+// compositing would use, so skipping it leaves every pixel unchanged.
 // ---------------------------------------------------------------------------
 constexpr float kAlphaMargin = 2e-3f;  // in the exponent: alpha within 0.2 %
 
 __device__ __forceinline__ float splat_fcut(float opacity) {
     // 2 (ln(255 o) + margin); negative when o < 1/255 (never contributes)
     return __fmul_rn(2.0f, __fadd_rn(__logf(__fmul_rn(255.0f, opacity)), kAlphaMargin));
-}
-
-__device__ __forceinline__ float edge_quad(float A, float B, float C, float invC, float a, float lo, float hi) {
-    // min over t in [lo, hi] of A a^2 + 2 B a t + C t^2 (C > 0), at t = -B a / C
-    float t = __fmul_rn(-__fmul_rn(B, a), invC);
-    t = fminf(fmaxf(t, lo), hi);
-    return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A, a), a), __fmul_rn(__fmul_rn(2.0f, B), __fmul_rn(a, t))),
-                     __fmul_rn(__fmul_rn(C, t), t));
-}
-
-__device__ __forceinline__ bool splat_rect_hits(float u, float v, float A, float B, float C, float fcut,
-                                                int px0, int px1, int py0, int py1) {
-    if (!(fcut >= 0.0f)) return false;
-    const float a1 = __fsub_rn(__fadd_rn((float)px0, 0.5f), u), a2 = __fsub_rn(__fadd_rn((float)px1, 0.5f), u);
-    const float b1 = __fsub_rn(__fadd_rn((float)py0, 0.5f), v), b2 = __fsub_rn(__fadd_rn((float)py1, 0.5f), v);
-    if (a1 <= 0.0f && a2 >= 0.0f && b1 <= 0.0f && b2 >= 0.0f) return true;
-    const float iA = __frcp_rn(A), iC = __frcp_rn(C);
-    float f = edge_quad(A, B, C, iC, a1, b1, b2);
-    f = fminf(f, edge_quad(A, B, C, iC, a2, b1, b2));
-    f = fminf(f, edge_quad(C, B, A, iA, b1, a1, a2));
-    f = fminf(f, edge_quad(C, B, A, iA, b2, a1, a2));
-    return f <= fcut;
 }
 
 // Pixel range [lo, hi] of a splat's support box on one axis (centres within

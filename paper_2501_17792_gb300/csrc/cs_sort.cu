@@ -350,10 +350,10 @@ int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint3
 // pair emission in depth order, tile ranges, live count
 // ---------------------------------------------------------------------------
 
-// Pairs of one splat (in depth order): every tile of its reach box that
-// holds a pixel the compositing would use.  Small splats carry those tiles
-// as a 3x3 mask in their bin word (gathered into depth order by the depth
-// sort); larger ones repeat the counting test on the values in the record.
+// Pairs of one splat (in depth order): every tile its reach box meets.  Small
+// splats carry those tiles as a 3x3 mask in their bin word (gathered into
+// depth order by the depth sort); larger ones take the reach box from the
+// record.
 __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *__restrict__ order,
                                                     const uint32_t *__restrict__ bins,
                                                     const uint32_t *__restrict__ pair_off,
@@ -379,17 +379,12 @@ __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *
         }
         return;
     }
-    const float4 r0 = rec[(size_t)s * kRecVec + 0];  // u, v, A, B
-    const float4 r1 = rec[(size_t)s * kRecVec + 1];  // C, opacity, radius, depth
     const float4 r3 = rec[(size_t)s * kRecVec + 3];  // reach x, reach y, fcut, log2 o
     const uint32_t rx = __float_as_uint(r3.x), ry = __float_as_uint(r3.y);
     const int ax0 = (int)(rx & 0xFFFFu), ax1 = (int)(rx >> 16);
     const int ay0 = (int)(ry & 0xFFFFu), ay1 = (int)(ry >> 16);
     for (int yy = ay0 >> 4; yy <= (ay1 >> 4); ++yy) {
-        const int qy0 = max(yy * kTile, ay0), qy1 = min(yy * kTile + kTile - 1, ay1);
         for (int xx = ax0 >> 4; xx <= (ax1 >> 4); ++xx) {
-            const int qx0 = max(xx * kTile, ax0), qx1 = min(xx * kTile + kTile - 1, ax1);
-            if (!splat_rect_hits(r0.x, r0.y, r0.z, r0.w, r1.x, r3.z, qx0, qx1, qy0, qy1)) continue;
             if (o >= e) return;
             ptile[o] = (uint16_t)(yy * tiles_x + xx);
             pval[o] = s;
