@@ -87,7 +87,7 @@ struct cs_ctx {
     CamParams train_cp{};
     int train_proj_blocks = 0;
     // split compositing of long tile lists
-    DevBuf<int32_t> bw_slot, bw_tile, bw_meta, bw_stop, bw_pp;
+    DevBuf<int32_t> bw_slot, bw_tile, bw_meta, bw_stop, bw_pp, bw_cslot;
     DevBuf<uint32_t> bw_chunk0, bw_done;
     DevBuf<float4> bw_state, bw_part;
 
@@ -416,7 +416,7 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->ptile2); release(ctx->img); release(ctx->contrib_s);
     release(ctx->px_end); release(ctx->px_T); release(ctx->dsplat); release(ctx->g_cov); release(ctx->g_B);
     release(ctx->g_dummy);
-    release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_pp); release(ctx->bw_chunk0);
+    release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_pp); release(ctx->bw_cslot); release(ctx->bw_chunk0);
     release(ctx->bw_done); release(ctx->bw_state); release(ctx->bw_part);
     if (ctx->d_meta) cudaFree(ctx->d_meta);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
@@ -921,11 +921,13 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         CS_TRY(ensure(ctx, ctx->bw_done, ms, "blend slot flags"));
         CS_TRY(ensure(ctx, ctx->bw_state, ms * 256, "blend pass-1 state"));
         CS_TRY(ensure(ctx, ctx->bw_part, mc * 256, "blend chunk partials"));
+        CS_TRY(ensure(ctx, ctx->bw_cslot, mc, "blend chunk slots"));
         CS_TRY(ensure(ctx, ctx->bw_stop, ms * 256, "blend stop chunks"));
     }
     BlendWork bw{ctx->bw_slot.p, ctx->bw_tile.p, ctx->bw_chunk0.p, ctx->bw_done.p, ctx->bw_state.p, ctx->bw_part.p,
                  ctx->bw_meta.p, ctx->bw_stop.p, nullptr};
     bw.pp_tile = ctx->bw_pp.p;
+    bw.chunk_slot = ctx->bw_cslot.p;
     if (contrib_tmpl) {
         CS_TRY(ensure(ctx, ctx->contrib_s, Sa, "splat contributions"));
         CS_CUDA(cudaMemsetAsync(ctx->contrib_s.p, 0, Sa * sizeof(float), st));
@@ -1179,7 +1181,7 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
                  bytes_of(ctx->pval2) + bytes_of(ctx->scratch) + bytes_of(ctx->rect) + bytes_of(ctx->ranges) +
                  bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img) + bytes_of(ctx->bw_slot) +
                  bytes_of(ctx->bw_tile) + bytes_of(ctx->bw_meta) + bytes_of(ctx->bw_chunk0) + bytes_of(ctx->bw_done) +
-                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop) + bytes_of(ctx->bw_pp) + bytes_of(ctx->contrib_s) +
+                 bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop) + bytes_of(ctx->bw_pp) + bytes_of(ctx->bw_cslot) + bytes_of(ctx->contrib_s) +
                  bytes_of(ctx->px_end) + bytes_of(ctx->px_T) + bytes_of(ctx->dsplat) + bytes_of(ctx->g_cov) +
                  bytes_of(ctx->g_B) + bytes_of(ctx->g_dummy);
     out->template_bytes = tb;
@@ -1272,7 +1274,8 @@ constexpr size_t kOffBwState = kOffBwDone + a256(kStaticSlots * 4);
 constexpr size_t kOffBwPart = kOffBwState + a256(kStaticSlots * 256 * sizeof(float4));
 constexpr size_t kOffBwStop = kOffBwPart + a256(kStaticChunks * 256 * sizeof(float4));
 constexpr size_t kOffBwPp = kOffBwStop + a256(kStaticSlots * 256 * 4);
-constexpr size_t kStaticBytes = kOffBwPp + a256(kStaticTiles * 4);  // about 11.6 MB
+constexpr size_t kOffBwCslot = kOffBwPp + a256(kStaticTiles * 4);
+constexpr size_t kStaticBytes = kOffBwCslot + a256(kStaticChunks * 4);  // about 11.6 MB
 
 }  // namespace
 
@@ -1411,6 +1414,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
                  reinterpret_cast<float4 *>(base + kOffBwState), reinterpret_cast<float4 *>(base + kOffBwPart),
                  reinterpret_cast<int32_t *>(base + kOffBwMeta), reinterpret_cast<int32_t *>(base + kOffBwStop)};
     bw.pp_tile = reinterpret_cast<int32_t *>(base + kOffBwPp);
+    bw.chunk_slot = reinterpret_cast<int32_t *>(base + kOffBwCslot);
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ranges, pval, rec, out, bw,
                              (uint32_t)P, st);
     CS_CUDA(cudaGetLastError());

@@ -419,15 +419,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_chunks(int tiles_x, int
                                                                 BlendWork work) {
     __shared__ BlendShared<> sh;
     const uint32_t w = blockIdx.x;
-    const int n_cand = work.meta[0];
     if (w >= (uint32_t)work.meta[1]) return;
-    // slot: last candidate whose first chunk <= w
-    int lo = 0, hi = n_cand - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (work.cand_chunk0[mid] <= w) lo = mid; else hi = mid - 1;
-    }
-    const int slot = lo;
+    const int slot = work.chunk_slot[w];
     if (work.cand_done[slot]) return;
     const int tile = work.cand_tile[slot];
     const TileGeom g = tile_geom(tile, tiles_x, W, H);
@@ -457,20 +450,28 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_merge(int tiles_x, int 
     bool done = !g.inside || s1.w < 0.0f;
     int32_t stop = -1;
     const uint32_t c0 = work.cand_chunk0[slot], c1 = work.cand_chunk0[slot + 1];
-    for (uint32_t w = c0; w < c1 && !done; ++w) {
-        const float4 pk = work.part[(size_t)w * kBlendThreads + threadIdx.x];
-        const float Tk = fabsf(pk.w);
-        if (T * Tk >= 1e-4f) {
-            // no splat of the chunk reaches the stop rule from this T: the
-            // chunk's composite applies as a whole
-            r += T * pk.x;
-            gg += T * pk.y;
-            b += T * pk.z;
-            T *= Tk;
-            done = pk.w < 0.0f;
-        } else {
-            stop = (int32_t)w;
-            done = true;
+    // four chunks' partials loaded at a time (independent loads), applied in order
+    for (uint32_t w0 = c0; w0 < c1 && !done; w0 += 4) {
+        float4 pk[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            pk[i] = w0 + i < c1 ? work.part[(size_t)(w0 + i) * kBlendThreads + threadIdx.x] : make_float4(0.f, 0.f, 0.f, 1.f);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (done || w0 + i >= c1) break;
+            const float Tk = fabsf(pk[i].w);
+            if (T * Tk >= 1e-4f) {
+                // no splat of the chunk reaches the stop rule from this T: the
+                // chunk's composite applies as a whole
+                r += T * pk[i].x;
+                gg += T * pk[i].y;
+                b += T * pk[i].z;
+                T *= Tk;
+                done = pk[i].w < 0.0f;
+            } else {
+                stop = (int32_t)(w0 + i);
+                done = true;
+            }
         }
     }
     work.stop[pix] = stop;
@@ -487,14 +488,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W,
                                                              float4 *__restrict__ out, BlendWork work) {
     __shared__ BlendShared<> sh;
     const uint32_t w = blockIdx.x;
-    const int n_cand = work.meta[0];
     if (w >= (uint32_t)work.meta[1]) return;
-    int lo = 0, hi = n_cand - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (work.cand_chunk0[mid] <= w) lo = mid; else hi = mid - 1;
-    }
-    const int slot = lo;
+    const int slot = work.chunk_slot[w];
     if (work.cand_done[slot]) return;
     const size_t pix = (size_t)slot * kBlendThreads + threadIdx.x;
     const bool mine = work.stop[pix] == (int32_t)w;
@@ -549,6 +544,10 @@ __global__ void __launch_bounds__(1024) k_blend_plan(int n_tiles, const uint2 *_
         work.meta[0] = (int)run_c;
         work.meta[1] = (int)run_k;
     }
+    __syncthreads();
+    // slot of every chunk (the chunk kernels read it instead of searching)
+    for (uint32_t sl = threadIdx.x; sl < run_c; sl += blockDim.x)
+        for (uint32_t c = work.cand_chunk0[sl], c1 = work.cand_chunk0[sl + 1]; c < c1; ++c) work.chunk_slot[c] = (int)sl;
     // pass-1 items, grouped by list length, longest first (the order inside
     // a group does not affect any result): eight block items per tile with
     // pairs, then one item per empty tile

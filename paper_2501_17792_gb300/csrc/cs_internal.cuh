@@ -298,7 +298,8 @@ struct BlendWork {
     // composited pair and its final transmittance; one pass as well
     uint32_t *px_end;
     float *px_T;
-    int32_t *pp_tile;  // [tiles]
+    int32_t *pp_tile;     // [tiles]
+    int32_t *chunk_slot;  // [chunks]: the slot of each pass-2 chunk
 };
 constexpr int kBlendMetaWords = 8;
 constexpr int kBlendBlockW = 8, kBlendBlockH = 4;  // pixels of one warp in a 16x16 tile
