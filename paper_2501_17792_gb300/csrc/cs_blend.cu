@@ -358,29 +358,46 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
             __syncthreads();
             // chain the partials in depth order
             if (warp == 0) {
-                for (int k = 0; k < kPpWarps && !done; ++k) {
-                    const float4 q = sh.part[k][lane];
-                    if (T * q.w >= 1e-4f) {
+                for (int k = 0; k < kPpWarps && !done;) {
+                    // the first sub-range from k in which the stop rule can
+                    // fall (its transmittances read at once), then the ones
+                    // before it applied as wholes, in order
+                    float Tq[kPpWarps];
+#pragma unroll
+                    for (int i = 0; i < kPpWarps; ++i) Tq[i] = i >= k ? sh.part[i][lane].w : 1.0f;
+                    int ks = kPpWarps;
+                    float Tb = T;
+#pragma unroll
+                    for (int i = 0; i < kPpWarps; ++i) {
+                        if (i < k || ks < kPpWarps) continue;
+                        if (Tb * Tq[i] < 1e-4f) ks = i;
+                        else Tb *= Tq[i];
+                    }
+#pragma unroll
+                    for (int i = 0; i < kPpWarps; ++i) {
+                        if (i < k || i >= ks) continue;
                         // no splat of the sub-range meets the stop rule from this T
+                        const float4 q = sh.part[i][lane];
                         cr += T * q.x;
                         cg += T * q.y;
                         cb += T * q.z;
                         T *= q.w;
-                        continue;
                     }
-                    // the stop falls inside sub-range k: composite it from the true T
-                    uint32_t mk = sh.m[k];
+                    if (ks == kPpWarps) break;
+                    k = ks + 1;
+                    // the stop falls inside sub-range ks: composite it from the true T
+                    uint32_t mk = sh.m[ks];
                     while (mk) {
                         const int j = __ffs(mk) - 1;
                         mk &= mk - 1;
-                        const float alpha = staged_alpha(sh.s0[k][j], sh.s1[k][j], fpx, fpy);
+                        const float alpha = staged_alpha(sh.s0[ks][j], sh.s1[ks][j], fpx, fpy);
                         if (alpha == 0.0f) continue;
                         const float Tn = T * (1.0f - alpha);
                         if (Tn < 1e-4f) {
                             done = true;
                             break;
                         }
-                        const float4 col = sh.s2[k][j];
+                        const float4 col = sh.s2[ks][j];
                         const float wgt = alpha * T;
                         cr += col.x * wgt;
                         cg += col.y * wgt;
