@@ -498,14 +498,15 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     __shared__ float4 sB[kJoints * 3];
     __shared__ int s_group;
     __shared__ __align__(16) unsigned char s_tc[kStore == kStoreBf16 ? kSkinTcBytes : 16];
-    if (threadIdx.x == 0) {
-        // group whose CTA range holds this CTA: last group with block0 <= blockIdx.x
-        int lo = 0, hi = n_groups - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (groups[mid].block0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    if (threadIdx.x < 32) {
+        // group whose CTA range holds this CTA: the last group with
+        // block0 <= blockIdx.x (block0 ascends from 0), counted by ballots
+        int cnt = 0;
+        for (int g0 = 0; g0 < n_groups; g0 += 32) {
+            const int g = g0 + (int)threadIdx.x;
+            cnt += __popc(__ballot_sync(0xffffffffu, g < n_groups && groups[g].block0 <= (int)blockIdx.x));
         }
-        s_group = lo;
+        if (threadIdx.x == 0) s_group = max(cnt - 1, 0);
     }
     __syncthreads();
     const Group G = groups[s_group];
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     // LBS (CrowdSplat Sec. 2): M = sum_k w_k B_{idx_k} (instance local)
     float M[12];
     float4 mo;        // mean (template local), opacity
-    float cv[6];      // canonical covariance xx, xy, xz, yy, yz, zz (BF16 storage)
+    float cv[6];      // canonical covariance xx, xy, xz, yy, yz, zz
     if constexpr (kStore == kStoreBf16) {
         const uint4 qa = valid ? __ldg(ta.qa + gi) : make_uint4(0u, 0u, 0u, 0u);
         const uint4 qb = valid ? __ldg(ta.qb + gi) : make_uint4(0u, 0u, 0u, 0u);
@@ -563,6 +564,11 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
             M[8] += wk[k] * b2.x; M[9] += wk[k] * b2.y; M[10] += wk[k] * b2.z; M[11] += wk[k] * b2.w;
         }
         mo = __ldg(ta.mean_op + gi);
+        // the covariance is loaded with the other attributes (one round of
+        // L2 latency instead of two)
+        const float4 ca = __ldg(ta.cov_a + gi);
+        const float2 cb = __ldg(ta.cov_b + gi);
+        cv[0] = ca.x; cv[1] = ca.y; cv[2] = ca.z; cv[3] = ca.w; cv[4] = cb.x; cv[5] = cb.y;
     }
     const float lx = M[0] * mo.x + M[1] * mo.y + M[2] * mo.z + M[3];
     const float ly = M[4] * mo.x + M[5] * mo.y + M[6] * mo.z + M[7];
@@ -592,19 +598,10 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
             W[3] = v1.x; W[4] = v1.y; W[5] = v1.z;
             W[6] = v2.x; W[7] = v2.y; W[8] = v2.z;
         }
-        float4 ca;
-        float2 cb;
-        if constexpr (kStore == kStoreBf16) {
-            ca = make_float4(cv[0], cv[1], cv[2], cv[3]);
-            cb = make_float2(cv[4], cv[5]);
-        } else {
-            ca = __ldg(ta.cov_a + gi);
-            cb = __ldg(ta.cov_b + gi);
-        }
         const float m = lod.mult[G.lvl];
         const float m2 = m * m;
-        const float S0 = ca.x * m2, S1 = ca.y * m2, S2 = ca.z * m2, S3 = ca.w * m2, S4 = cb.x * m2,
-                    S5 = cb.y * m2;
+        const float S0 = cv[0] * m2, S1 = cv[1] * m2, S2 = cv[2] * m2, S3 = cv[3] * m2, S4 = cv[4] * m2,
+                    S5 = cv[5] * m2;
         // EWA Jacobian at the mean, x/z and y/z clamped (3DGS)
         // hardware reciprocal and square root (relative error ~1e-7): far
         // inside the boundary windows the parity tests derive
