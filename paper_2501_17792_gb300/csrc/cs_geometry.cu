@@ -484,42 +484,16 @@ __device__ void skin_blend_tc(const float4 *__restrict__ sB, const float w_in[4]
     for (int e = 0; e < 12; ++e) M[e] = sM[t * kTcMld + e] * iw;
 }
 
-// One CTA per (visible instance, 256 Gaussians of its level): the CTA
-// stages the instance's 24 skinning transforms in shared memory; thread t
-// handles Gaussian chunk * 256 + t.  Splat ids are dense, grouped by
-// (template, level), instance-major within a group.
+// Gaussians chunk * 256 + t of one visible instance (thread t), with the
+// instance's 24 skinning transforms staged in shared memory (sB).  Splat ids
+// are dense, grouped by (template, level), instance-major within a group.
 template <int kStore>
-__global__ void __launch_bounds__(kProjThreads, 5) k_project(
-    const Group *__restrict__ groups, int n_groups, const int32_t *__restrict__ vis,
-    const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ Cloc,
-    const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,
-    CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
-    uint32_t *__restrict__ key, uint32_t *__restrict__ bin) {
-    __shared__ float4 sB[kJoints * 3];
-    __shared__ int s_group;
-    __shared__ __align__(16) unsigned char s_tc[kStore == kStoreBf16 ? kSkinTcBytes : 16];
-    if (threadIdx.x < 32) {
-        // group whose CTA range holds this CTA: the last group with
-        // block0 <= blockIdx.x (block0 ascends from 0), counted by ballots
-        int cnt = 0;
-        for (int g0 = 0; g0 < n_groups; g0 += 32) {
-            const int g = g0 + (int)threadIdx.x;
-            cnt += __popc(__ballot_sync(0xffffffffu, g < n_groups && groups[g].block0 <= (int)blockIdx.x));
-        }
-        if (threadIdx.x == 0) s_group = max(cnt - 1, 0);
-    }
-    __syncthreads();
-    const Group G = groups[s_group];
-    const int per_inst = (G.ng + kProjThreads - 1) / kProjThreads;
-    const int rb = (int)blockIdx.x - G.block0;
-    const int islot = rb / per_inst;
-    const int chunk = rb - islot * per_inst;
-    const int inst = vis[G.slot0 + islot];
-    {
-        const float4 *Bi = reinterpret_cast<const float4 *>(Bm + (size_t)inst * kJoints * 12);
-        for (int k = threadIdx.x; k < kJoints * 3; k += kProjThreads) sB[k] = __ldg(Bi + k);
-    }
-    __syncthreads();
+__device__ __forceinline__ void project_chunk(
+    const Group &G, int islot, int chunk, int inst, const float4 *__restrict__ sB, unsigned char *s_tc,
+    const float *__restrict__ Vm, const float *__restrict__ Cloc, const float *__restrict__ root,
+    const TemplateArrays &ta, const TemplateInfo *__restrict__ tpls, const CamParams &cam, const LodParams &lod,
+    int skin_mode, int sh_frame, float4 *__restrict__ rec, uint32_t *__restrict__ key,
+    uint32_t *__restrict__ bin) {
     const int gg = chunk * kProjThreads + threadIdx.x;
     const bool valid = gg < G.ng;
     // the tensor-core blend needs every thread of the CTA
@@ -714,18 +688,78 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     bin[s] = live ? bword : 0u;
 }
 
+// Projection CTAs: kChunks consecutive virtual blocks each, a virtual block
+// being 256 Gaussians of one visible instance (cull_group numbers them:
+// Group::block0).  Consecutive virtual blocks mostly belong to one instance,
+// whose transforms are then staged once.  kChunks = 1 for BF16 storage (its
+// tensor-core blend reuses shared memory between barriers).
+template <int kStore, int kChunks>
+__global__ void __launch_bounds__(kProjThreads, 5) k_project(
+    const Group *__restrict__ groups, int n_groups, int n_vblocks, const int32_t *__restrict__ vis,
+    const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ Cloc,
+    const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,
+    CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
+    uint32_t *__restrict__ key, uint32_t *__restrict__ bin) {
+    static_assert(kStore == kStoreFp32 || kChunks == 1, "the BF16 blend needs one chunk per CTA");
+    __shared__ float4 sB[kJoints * 3];
+    __shared__ int s_group[kChunks];
+    __shared__ __align__(16) unsigned char s_tc[kStore == kStoreBf16 ? kSkinTcBytes : 16];
+    if (threadIdx.x < 32) {
+        // group of each virtual block: the last group with block0 <= vb
+        // (block0 ascends from 0), counted by ballots
+#pragma unroll
+        for (int j = 0; j < kChunks; ++j) {
+            const int vb = (int)blockIdx.x * kChunks + j;
+            int cnt = 0;
+            for (int g0 = 0; g0 < n_groups; g0 += 32) {
+                const int g = g0 + (int)threadIdx.x;
+                cnt += __popc(__ballot_sync(0xffffffffu, g < n_groups && groups[g].block0 <= vb));
+            }
+            if (threadIdx.x == 0) s_group[j] = max(cnt - 1, 0);
+        }
+    }
+    __syncthreads();
+    int staged = -1;
+#pragma unroll 1
+    for (int j = 0; j < kChunks; ++j) {
+        const int vb = (int)blockIdx.x * kChunks + j;
+        if (vb >= n_vblocks) break;
+        const Group G = groups[s_group[j]];
+        const int per_inst = (G.ng + kProjThreads - 1) / kProjThreads;
+        const int rb = vb - G.block0;
+        const int islot = rb / per_inst;
+        const int chunk = rb - islot * per_inst;
+        const int inst = vis[G.slot0 + islot];
+        if (inst != staged) {
+            if (j > 0) __syncthreads();  // the previous chunk is done with sB
+            const float4 *Bi = reinterpret_cast<const float4 *>(Bm + (size_t)inst * kJoints * 12);
+            for (int k = threadIdx.x; k < kJoints * 3; k += kProjThreads) sB[k] = __ldg(Bi + k);
+            __syncthreads();
+            staged = inst;
+        }
+        project_chunk<kStore>(G, islot, chunk, inst, sB, s_tc, Vm, Cloc, root, ta, tpls, cam, lod, skin_mode,
+                              sh_frame, rec, key, bin);
+    }
+}
+
+constexpr int kProjChunksFp32 = 4;
+
 int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_t *vis,
                     const float *B, const float *V, const float *Cloc, const float *root,
                     const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
                     const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
                     uint32_t *bin, cudaStream_t st) {
     if (n_blocks <= 0) return 0;
-    if (ta.storage == kStoreBf16)
-        k_project<kStoreBf16><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, vis, B, V, Cloc, root, ta, tpls,
-                                                                cam, lod, skin_mode, sh_frame, rec, key, bin);
-    else
-        k_project<kStoreFp32><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, vis, B, V, Cloc, root, ta, tpls,
-                                                                cam, lod, skin_mode, sh_frame, rec, key, bin);
+    if (ta.storage == kStoreBf16) {
+        k_project<kStoreBf16, 1><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, n_blocks, vis, B, V, Cloc, root,
+                                                                   ta, tpls, cam, lod, skin_mode, sh_frame, rec,
+                                                                   key, bin);
+    } else {
+        const int grid = (n_blocks + kProjChunksFp32 - 1) / kProjChunksFp32;
+        k_project<kStoreFp32, kProjChunksFp32><<<grid, kProjThreads, 0, st>>>(
+            groups, n_groups, n_blocks, vis, B, V, Cloc, root, ta, tpls, cam, lod, skin_mode, sh_frame, rec, key,
+            bin);
+    }
     return 1;
 }
 
