@@ -688,10 +688,10 @@ __device__ __forceinline__ void project_chunk(
     bin[s] = live ? bword : 0u;
 }
 
-// Projection CTAs: kChunks consecutive virtual blocks each, a virtual block
-// being 256 Gaussians of one visible instance (cull_group numbers them:
-// Group::block0).  Consecutive virtual blocks mostly belong to one instance,
-// whose transforms are then staged once.  kChunks = 1 for BF16 storage (its
+// Projection CTAs: kChunks consecutive virtual blocks each (8 with FP32
+// storage), a virtual block being 256 Gaussians of one visible instance
+// (cull_group numbers them: Group::block0).  Consecutive virtual blocks
+// mostly belong to one instance, whose transforms are then staged once.  kChunks = 1 for BF16 storage (its
 // tensor-core blend reuses shared memory between barriers).
 template <int kStore, int kChunks>
 __global__ void __launch_bounds__(kProjThreads, 5) k_project(
@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     }
 }
 
-constexpr int kProjChunksFp32 = 4;
+constexpr int kProjChunksFp32 = 8;
 
 int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_t *vis,
                     const float *B, const float *V, const float *Cloc, const float *root,
