@@ -70,6 +70,7 @@ struct cs_ctx {
     std::vector<int32_t> tid_host_check;
     DevBuf<Group> groups;
     int32_t *d_meta = nullptr, *h_meta = nullptr;  // pinned mirror
+    Group *h_groups = nullptr;                     // pinned mirror of the frame's groups
     uint32_t *h_pairs = nullptr;                   // pinned
 
     // per-frame buffers
@@ -390,6 +391,7 @@ int cs_create(cs_ctx **out, const cs_create_params *p) {
         if (cudaMalloc(&ctx->d_meta, kMetaWords * sizeof(int32_t)) != cudaSuccess) { rc = CS_ERR_OOM; break; }
         if (cudaHostAlloc(&ctx->h_meta, kMetaWords * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) { rc = CS_ERR_OOM; break; }
         if (cudaHostAlloc(&ctx->h_pairs, 4 * sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) { rc = CS_ERR_OOM; break; }
+        if (cudaHostAlloc(&ctx->h_groups, kMaxGroups * sizeof(Group), cudaHostAllocDefault) != cudaSuccess) { rc = CS_ERR_OOM; break; }
         for (int k = 0; k < 2 && rc == CS_OK; ++k)
             for (int i = 0; i <= kStages; ++i)
                 if (cudaEventCreate(&ctx->ev[k][i]) != cudaSuccess) { rc = CS_ERR_CUDA; break; }
@@ -420,6 +422,7 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->bw_done); release(ctx->bw_state); release(ctx->bw_part);
     if (ctx->d_meta) cudaFree(ctx->d_meta);
     if (ctx->h_meta) cudaFreeHost(ctx->h_meta);
+    if (ctx->h_groups) cudaFreeHost(ctx->h_groups);
     if (ctx->h_pairs) cudaFreeHost(ctx->h_pairs);
     for (int k = 0; k < 2; ++k)
         for (int i = 0; i <= kStages; ++i)
@@ -840,6 +843,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
                           ctx->d_meta, st);
         CS_CUDA(cudaGetLastError());
         CS_CUDA(cudaMemcpyAsync(ctx->h_meta, ctx->d_meta, kMetaWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CS_CUDA(cudaMemcpyAsync(ctx->h_groups, ctx->groups.p, kMaxGroups * sizeof(Group), cudaMemcpyDeviceToHost, st));
         CS_CUDA(cudaStreamSynchronize(st));
         ctx->visible = ctx->h_meta[kMetaVisible];
         ctx->n_groups = ctx->h_meta[kMetaGroups];
@@ -867,7 +871,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Sa), scan_scratch_words(Sa + 1)), "scratch"));
     const TemplateArrays ta = template_arrays(ctx);
     if (S > 0)
-        launched += launch_project(proj_blocks, ctx->groups.p, ctx->n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
+        launched += launch_project(proj_blocks, ctx->groups.p, ctx->h_groups, ctx->n_groups, ctx->tpl_host.data(),
+                                   ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                        ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
                        ctx->rec.p, ctx->key.p, ctx->bins.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[3], st));
@@ -1364,6 +1369,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
                                       ctx->d_meta, st);
         CS_CUDA(cudaGetLastError());
         CS_CUDA(cudaMemcpyAsync(ctx->h_meta, ctx->d_meta, kMetaWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CS_CUDA(cudaMemcpyAsync(ctx->h_groups, ctx->groups.p, kMaxGroups * sizeof(Group), cudaMemcpyDeviceToHost, st));
         CS_CUDA(cudaStreamSynchronize(st));
         visible = ctx->h_meta[kMetaVisible];
         n_groups = ctx->h_meta[kMetaGroups];
@@ -1377,7 +1383,8 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
                     (long long)S, kStaticSplats);
     const TemplateArrays ta = template_arrays(ctx);
     if (S > 0)
-        launched += launch_project(proj_blocks, ctx->groups.p, n_groups, ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
+        launched += launch_project(proj_blocks, ctx->groups.p, ctx->h_groups, n_groups, ctx->tpl_host.data(),
+                                   ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
                                    ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
                                    rec, key, bins, st);
     if (radix_scratch_words((size_t)std::max<int64_t>(S, 1)) > kStaticScratchWords ||

@@ -489,7 +489,7 @@ __device__ void skin_blend_tc(const float4 *__restrict__ sB, const float w_in[4]
 // are dense, grouped by (template, level), instance-major within a group.
 template <int kStore>
 __device__ __forceinline__ void project_chunk(
-    const Group &G, int islot, int chunk, int inst, const float4 *__restrict__ sB, unsigned char *s_tc,
+    const ProjGroup &G, int islot, int chunk, int inst, const float4 *__restrict__ sB, unsigned char *s_tc,
     const float *__restrict__ Vm, const float *__restrict__ Cloc, const float *__restrict__ root,
     const TemplateArrays &ta, const TemplateInfo *__restrict__ tpls, const CamParams &cam, const LodParams &lod,
     int skin_mode, int sh_frame, float4 *__restrict__ rec, uint32_t *__restrict__ key,
@@ -499,13 +499,11 @@ __device__ __forceinline__ void project_chunk(
     // the tensor-core blend needs every thread of the CTA
     if (kStore == kStoreFp32 && !valid) return;
     const int s = G.splat0 + islot * G.ng + gg;
-    const TemplateInfo &T = tpls[G.tpl];
     // the level's Gaussians: a prefix of the template, or a chosen subset
     int gsrc = 0, gi = 0;
     if (valid) {
-        const int sub = T.lod_idx_off[G.lvl];
-        gsrc = sub >= 0 ? (int)__ldg(ta.lod_idx + sub + gg) : gg;
-        gi = T.g_off + gsrc;
+        gsrc = G.sub >= 0 ? (int)__ldg(ta.lod_idx + G.sub + gg) : gg;
+        gi = G.g_off + gsrc;
     }
 
     // LBS (CrowdSplat Sec. 2): M = sum_k w_k B_{idx_k} (instance local)
@@ -519,8 +517,9 @@ __device__ __forceinline__ void project_chunk(
         skin_blend_tc(sB, wq, qb.w, valid, s_tc, M);
         if (!valid) return;
         const int j0 = qb.w & 0xFF;
-        mo = make_float4(T.rest[j0 * 3] + bf16_lo(qa.x), T.rest[j0 * 3 + 1] + bf16_hi(qa.x),
-                         T.rest[j0 * 3 + 2] + bf16_lo(qa.y), bf16_hi(qa.y));
+        const float *rest = tpls[G.tpl].rest;
+        mo = make_float4(rest[j0 * 3] + bf16_lo(qa.x), rest[j0 * 3 + 1] + bf16_hi(qa.x),
+                         rest[j0 * 3 + 2] + bf16_lo(qa.y), bf16_hi(qa.y));
         cv[0] = bf16_lo(qa.z); cv[1] = bf16_hi(qa.z); cv[2] = bf16_lo(qa.w); cv[3] = bf16_hi(qa.w);
         cv[4] = bf16_lo(qb.x); cv[5] = bf16_hi(qb.x);
     } else {
@@ -658,20 +657,20 @@ __device__ __forceinline__ void project_chunk(
                 const float inv = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
                 ddx *= inv; ddy *= inv; ddz *= inv;
                 float rgb[3];
-                const int64_t base = T.sh_off + gsrc;
+                const int64_t base = G.sh_off + gsrc;
                 if constexpr (kStore == kStoreBf16) {
-                    switch (T.sh_deg) {
-                        case 0: sh_colour16<0>(ta.sh16, base, T.n, ddx, ddy, ddz, rgb); break;
-                        case 1: sh_colour16<1>(ta.sh16, base, T.n, ddx, ddy, ddz, rgb); break;
-                        case 2: sh_colour16<2>(ta.sh16, base, T.n, ddx, ddy, ddz, rgb); break;
-                        default: sh_colour16<3>(ta.sh16, base, T.n, ddx, ddy, ddz, rgb); break;
+                    switch (G.sh_deg) {
+                        case 0: sh_colour16<0>(ta.sh16, base, G.n, ddx, ddy, ddz, rgb); break;
+                        case 1: sh_colour16<1>(ta.sh16, base, G.n, ddx, ddy, ddz, rgb); break;
+                        case 2: sh_colour16<2>(ta.sh16, base, G.n, ddx, ddy, ddz, rgb); break;
+                        default: sh_colour16<3>(ta.sh16, base, G.n, ddx, ddy, ddz, rgb); break;
                     }
                 } else {
-                    switch (T.sh_deg) {
-                        case 0: sh_colour<0>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
-                        case 1: sh_colour<1>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
-                        case 2: sh_colour<2>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
-                        default: sh_colour<3>(ta.sh, base, T.n, ddx, ddy, ddz, rgb); break;
+                    switch (G.sh_deg) {
+                        case 0: sh_colour<0>(ta.sh, base, G.n, ddx, ddy, ddz, rgb); break;
+                        case 1: sh_colour<1>(ta.sh, base, G.n, ddx, ddy, ddz, rgb); break;
+                        case 2: sh_colour<2>(ta.sh, base, G.n, ddx, ddy, ddz, rgb); break;
+                        default: sh_colour<3>(ta.sh, base, G.n, ddx, ddy, ddz, rgb); break;
                     }
                 }
                 float4 *ro = rec + (size_t)s * kRecVec;
@@ -699,7 +698,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ Cloc,
     const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,
     CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
-    uint32_t *__restrict__ key, uint32_t *__restrict__ bin) {
+    uint32_t *__restrict__ key, uint32_t *__restrict__ bin, const __grid_constant__ ProjGroups pg) {
     static_assert(kStore == kStoreFp32 || kChunks == 1, "the BF16 blend needs one chunk per CTA");
     __shared__ float4 sB[kJoints * 3];
     __shared__ int s_group[kChunks];
@@ -724,7 +723,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     for (int j = 0; j < kChunks; ++j) {
         const int vb = (int)blockIdx.x * kChunks + j;
         if (vb >= n_vblocks) break;
-        const Group G = groups[s_group[j]];
+        const ProjGroup &G = pg.g[s_group[j]];
         const int per_inst = (G.ng + kProjThreads - 1) / kProjThreads;
         const int rb = vb - G.block0;
         const int islot = rb / per_inst;
@@ -744,21 +743,38 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
 
 constexpr int kProjChunksFp32 = 8;
 
-int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_t *vis,
-                    const float *B, const float *V, const float *Cloc, const float *root,
-                    const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
-                    const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
-                    uint32_t *bin, cudaStream_t st) {
-    if (n_blocks <= 0) return 0;
+int launch_project(int n_blocks, const Group *groups, const Group *groups_host, int n_groups,
+                   const TemplateInfo *tpl_host, const int32_t *vis, const float *B, const float *V,
+                   const float *Cloc, const float *root, const TemplateArrays &ta, const TemplateInfo *tpls,
+                   const CamParams &cam, const LodParams &lod, int skin_mode, int sh_frame, float4 *rec,
+                   uint32_t *key, uint32_t *bin, cudaStream_t st) {
+    if (n_blocks <= 0 || n_groups <= 0 || n_groups > kMaxGroups) return 0;
+    ProjGroups pg;
+    for (int i = 0; i < n_groups; ++i) {
+        const Group &G = groups_host[i];
+        const TemplateInfo &T = tpl_host[G.tpl];
+        ProjGroup &P = pg.g[i];
+        P.tpl = G.tpl;
+        P.lvl = G.lvl;
+        P.slot0 = G.slot0;
+        P.ng = G.ng;
+        P.splat0 = G.splat0;
+        P.block0 = G.block0;
+        P.g_off = T.g_off;
+        P.n = T.n;
+        P.sh_deg = T.sh_deg;
+        P.sub = T.lod_idx_off[G.lvl];
+        P.sh_off = T.sh_off;
+    }
     if (ta.storage == kStoreBf16) {
         k_project<kStoreBf16, 1><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, n_blocks, vis, B, V, Cloc, root,
                                                                    ta, tpls, cam, lod, skin_mode, sh_frame, rec,
-                                                                   key, bin);
+                                                                   key, bin, pg);
     } else {
         const int grid = (n_blocks + kProjChunksFp32 - 1) / kProjChunksFp32;
         k_project<kStoreFp32, kProjChunksFp32><<<grid, kProjThreads, 0, st>>>(
             groups, n_groups, n_blocks, vis, B, V, Cloc, root, ta, tpls, cam, lod, skin_mode, sh_frame, rec, key,
-            bin);
+            bin, pg);
     }
     return 1;
 }

@@ -76,6 +76,20 @@ struct Group {         // visible instances of one (template, level)
     int32_t block0;    // first projection CTA (each CTA: 256 Gaussians of one instance)
 };
 
+// A group as the projection reads it: the Group fields and those of its
+// template (level subset offset, Gaussian and SH offsets, sizes).  The host
+// passes all groups of a frame as one kernel parameter (constant bank), so
+// every thread reads them through the constant cache.
+struct ProjGroup {
+    int32_t tpl, lvl, slot0, ng, splat0, block0;
+    int32_t g_off, n, sh_deg, sub;  // sub: level subset offset in lod_idx, -1 for a prefix
+    int64_t sh_off;
+};
+constexpr int kMaxGroups = kMaxTemplates * kMaxLevels;
+struct ProjGroups {
+    ProjGroup g[kMaxGroups];
+};
+
 struct CamParams {
     float R[9], t[3];
     float fx, fy, cx, cy;
@@ -233,11 +247,11 @@ int launch_cull_group(int n_inst, int n_tpl, const int32_t *tid, const float *ro
                        const TemplateInfo *tpls, const CamParams &cam, const LodParams &lod,
                        int do_cull, float *V, float *Cloc, int32_t *vis, Group *groups,
                        int32_t *meta, cudaStream_t st);
-int launch_project(int n_blocks, const Group *groups, int n_groups, const int32_t *vis,
-                    const float *B, const float *V, const float *Cloc, const float *root,
-                    const TemplateArrays &ta, const TemplateInfo *tpls, const CamParams &cam,
-                    const LodParams &lod, int skin_mode, int sh_frame, float4 *rec, uint32_t *key,
-                    uint32_t *bin, cudaStream_t st);
+int launch_project(int n_blocks, const Group *groups, const Group *groups_host, int n_groups,
+                   const TemplateInfo *tpl_host, const int32_t *vis, const float *B, const float *V,
+                   const float *Cloc, const float *root, const TemplateArrays &ta, const TemplateInfo *tpls,
+                   const CamParams &cam, const LodParams &lod, int skin_mode, int sh_frame, float4 *rec,
+                   uint32_t *key, uint32_t *bin, cudaStream_t st);
 // Tile rectangle of each splat's support box (debug view; recomputed from the
 // records: x0 | y0 << 16, x1 | y1 << 16; zero for splats without pairs).
 int launch_debug_rects(int n_splats, const float4 *rec, const uint32_t *bins, int W, int H, uint2 *rect,
