@@ -489,7 +489,8 @@ __device__ void skin_blend_tc(const float4 *__restrict__ sB, const float w_in[4]
 // are dense, grouped by (template, level), instance-major within a group.
 template <int kStore>
 __device__ __forceinline__ void project_chunk(
-    const ProjGroup &G, int islot, int chunk, int inst, const float4 *__restrict__ sB, unsigned char *s_tc,
+    const ProjGroup &G, int islot, int chunk, int inst, const float4 *__restrict__ sB,
+    const float4 *__restrict__ sV, unsigned char *s_tc,
     const float *__restrict__ Vm, const float *__restrict__ Cloc, const float *__restrict__ root,
     const TemplateArrays &ta, const TemplateInfo *__restrict__ tpls, const CamParams &cam, const LodParams &lod,
     int skin_mode, int sh_frame, float4 *__restrict__ rec, uint32_t *__restrict__ key,
@@ -543,15 +544,26 @@ __device__ __forceinline__ void project_chunk(
         const float2 cb = __ldg(ta.cov_b + gi);
         cv[0] = ca.x; cv[1] = ca.y; cv[2] = ca.z; cv[3] = ca.w; cv[4] = cb.x; cv[5] = cb.y;
     }
-    const float lx = M[0] * mo.x + M[1] * mo.y + M[2] * mo.z + M[3];
-    const float ly = M[4] * mo.x + M[5] * mo.y + M[6] * mo.z + M[7];
-    const float lz = M[8] * mo.x + M[9] * mo.y + M[10] * mo.z + M[11];
-    // view transform (camera o root)
-    const float4 *Vi = reinterpret_cast<const float4 *>(Vm + (size_t)inst * 12);
-    const float4 v0 = __ldg(Vi), v1 = __ldg(Vi + 1), v2 = __ldg(Vi + 2);
-    const float tx = v0.x * lx + v0.y * ly + v0.z * lz + v0.w;
-    const float ty = v1.x * lx + v1.y * ly + v1.z * lz + v1.w;
-    const float tz = v2.x * lx + v2.y * ly + v2.z * lz + v2.w;
+    // view transform V = camera o root.  FP32 storage: M is already in
+    // camera axes (the staged transforms are V_R B_j), only V's translation
+    // is left to add; BF16 storage: M is instance local.
+    float4 v0, v1, v2;
+    float tx, ty, tz;
+    if constexpr (kStore == kStoreFp32) {
+        v0 = sV[0]; v1 = sV[1]; v2 = sV[2];
+        tx = M[0] * mo.x + M[1] * mo.y + M[2] * mo.z + M[3] + v0.w;
+        ty = M[4] * mo.x + M[5] * mo.y + M[6] * mo.z + M[7] + v1.w;
+        tz = M[8] * mo.x + M[9] * mo.y + M[10] * mo.z + M[11] + v2.w;
+    } else {
+        const float lx = M[0] * mo.x + M[1] * mo.y + M[2] * mo.z + M[3];
+        const float ly = M[4] * mo.x + M[5] * mo.y + M[6] * mo.z + M[7];
+        const float lz = M[8] * mo.x + M[9] * mo.y + M[10] * mo.z + M[11];
+        const float4 *Vi = reinterpret_cast<const float4 *>(Vm + (size_t)inst * 12);
+        v0 = __ldg(Vi); v1 = __ldg(Vi + 1); v2 = __ldg(Vi + 2);
+        tx = v0.x * lx + v0.y * ly + v0.z * lz + v0.w;
+        ty = v1.x * lx + v1.y * ly + v1.z * lz + v1.w;
+        tz = v2.x * lx + v2.y * ly + v2.z * lz + v2.w;
+    }
 
     bool live = tz > cam.near_z;  // also false for NaN
     uint32_t nt = 0, bword = 0;
@@ -559,7 +571,12 @@ __device__ __forceinline__ void project_chunk(
         // covariance in camera space: Wc = (V_R A) (m^2 Sigma) (V_R A)^T,
         // A = the 3x3 part of M (full LBS) or identity (means only)
         float W[9];
-        if (skin_mode == 0) {
+        if (skin_mode == 0 && kStore == kStoreFp32) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) W[r * 3 + c] = M[r * 4 + c];
+        } else if (skin_mode == 0) {
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 const float4 vr = r == 0 ? v0 : (r == 1 ? v1 : v2);
@@ -642,11 +659,11 @@ __device__ __forceinline__ void project_chunk(
             live = live && nt > 0;
             if (live) {
                 // colour: SH at the viewing direction (camera centre -> mean)
-                float ddx, ddy, ddz;
-                const float4 cl = __ldg(reinterpret_cast<const float4 *>(Cloc) + inst);
-                ddx = lx - cl.x;
-                ddy = ly - cl.y;
-                ddz = lz - cl.z;
+                // in the instance's root frame: V_R^T t (V is rigid, the
+                // camera centre is at the origin of camera space)
+                float ddx = v0.x * tx + v1.x * ty + v2.x * tz;
+                float ddy = v0.y * tx + v1.y * ty + v2.y * tz;
+                float ddz = v0.z * tx + v1.z * ty + v2.z * tz;
                 if (sh_frame == 1) {
                     const float *rt = root + (size_t)inst * 12;
                     const float wx = rt[0] * ddx + rt[1] * ddy + rt[2] * ddz;
@@ -700,7 +717,8 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
     uint32_t *__restrict__ key, uint32_t *__restrict__ bin, const __grid_constant__ ProjGroups pg) {
     static_assert(kStore == kStoreFp32 || kChunks == 1, "the BF16 blend needs one chunk per CTA");
-    __shared__ float4 sB[kJoints * 3];
+    __shared__ float4 sB[kJoints * 3];  // skinning transforms (FP32 storage: V_R B_j)
+    __shared__ float4 sV[3];            // V = camera o root, rows
     __shared__ int s_group[kChunks];
     __shared__ __align__(16) unsigned char s_tc[kStore == kStoreBf16 ? kSkinTcBytes : 16];
     if (threadIdx.x < 32) {
@@ -732,11 +750,25 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
         if (inst != staged) {
             if (j > 0) __syncthreads();  // the previous chunk is done with sB
             const float4 *Bi = reinterpret_cast<const float4 *>(Bm + (size_t)inst * kJoints * 12);
-            for (int k = threadIdx.x; k < kJoints * 3; k += kProjThreads) sB[k] = __ldg(Bi + k);
+            const float4 *Vi = reinterpret_cast<const float4 *>(Vm + (size_t)inst * 12);
+            const int t = (int)threadIdx.x;
+            if (kStore == kStoreFp32 && t < kJoints * 3) {
+                // row r of V_R B_j: the joint transform in camera axes, without
+                // V's translation (the blend stays at instance scale)
+                const int jj = t / 3, r = t - 3 * jj;
+                const float4 vr = __ldg(Vi + r);
+                const float4 b0 = __ldg(Bi + jj * 3), b1 = __ldg(Bi + jj * 3 + 1), b2 = __ldg(Bi + jj * 3 + 2);
+                sB[t] = make_float4(vr.x * b0.x + vr.y * b1.x + vr.z * b2.x, vr.x * b0.y + vr.y * b1.y + vr.z * b2.y,
+                                    vr.x * b0.z + vr.y * b1.z + vr.z * b2.z, vr.x * b0.w + vr.y * b1.w + vr.z * b2.w);
+            } else if (kStore == kStoreBf16 && t < kJoints * 3) {
+                sB[t] = __ldg(Bi + t);
+            } else if (t >= kJoints * 3 && t < kJoints * 3 + 3) {
+                sV[t - kJoints * 3] = __ldg(Vi + (t - kJoints * 3));
+            }
             __syncthreads();
             staged = inst;
         }
-        project_chunk<kStore>(G, islot, chunk, inst, sB, s_tc, Vm, Cloc, root, ta, tpls, cam, lod, skin_mode,
+        project_chunk<kStore>(G, islot, chunk, inst, sB, sV, s_tc, Vm, Cloc, root, ta, tpls, cam, lod, skin_mode,
                               sh_frame, rec, key, bin);
     }
 }

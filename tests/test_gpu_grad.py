@@ -87,6 +87,19 @@ def perturbed(sc, kind, index, delta):
     return dataclasses.replace(sc, templates=[t2]), float(new) - float(old)
 
 
+def input_value(sc, kind, index):
+    if kind == "pose":
+        return float(sc.instances.pose.reshape(-1)[index])
+    return float(getattr(sc.templates[0], kind).reshape(-1)[index])
+
+
+def step_scale(sc, kind, index, h_min):
+    """Power of two by which a step of h_min must grow to move the float32
+    input at all: one unit in the last place of its value at least."""
+    ulp = float(np.spacing(np.float32(abs(input_value(sc, kind, index)))))
+    return max(1.0, ulp / h_min)
+
+
 def fd(sc, wt, lat, kind, index, h):
     sp, dp = perturbed(sc, kind, index, h)
     sm, dm = perturbed(sc, kind, index, -h)
@@ -123,8 +136,9 @@ def check_kind(sc, wt, lat, g, kind, n_pick=10, seed=0, steps=None):
         pairs = [(int(i), flat[i], int(i)) for i in pick]
     res = []
     for idx, gval, oidx in pairs:
-        f = fd(sc, wt, lat, kind, oidx, steps[kind])
-        f4 = fd(sc, wt, lat, kind, oidx, steps[kind] / 4)
+        h = steps[kind] * step_scale(sc, kind, oidx, steps[kind] / 4)
+        f = fd(sc, wt, lat, kind, oidx, h)
+        f4 = fd(sc, wt, lat, kind, oidx, h / 4)
         res.append((idx, gval, f, f4))
     res = np.array(res)
     gpu, ref, ref4 = res[:, 1], res[:, 2], res[:, 3]
