@@ -327,13 +327,18 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
             if (i < end1) {
                 const uint32_t s = __ldg(pval + i);
                 const float4 *p = rec + (size_t)s * kRecVec;
-                const float4 ra = __ldg(p), rb = __ldg(p + 1), rc = __ldg(p + 2), rq = __ldg(p + 3);
+                // the reach box first: the rest of the record only for
+                // splats whose reach box meets this block
+                const float4 rq = __ldg(p + 3);
                 const uint32_t rx = __float_as_uint(rq.x), ry = __float_as_uint(rq.y);
                 mine = (int)(rx & 0xFFFFu) <= bx0 + kBlockW - 1 && (int)(rx >> 16) >= bx0 &&
                        (int)(ry & 0xFFFFu) <= by0 + kBlockH - 1 && (int)(ry >> 16) >= by0;
-                sh.s0[warp][lane] = make_float4(ra.x, ra.y, -0.5f * kLog2e * ra.z, -kLog2e * ra.w);
-                sh.s1[warp][lane] = make_float4(-0.5f * kLog2e * rb.x, rq.w, rb.z, 0.0f);
-                sh.s2[warp][lane] = rc;
+                if (mine) {
+                    const float4 ra = __ldg(p), rb = __ldg(p + 1), rc = __ldg(p + 2);
+                    sh.s0[warp][lane] = make_float4(ra.x, ra.y, -0.5f * kLog2e * ra.z, -kLog2e * ra.w);
+                    sh.s1[warp][lane] = make_float4(-0.5f * kLog2e * rb.x, rq.w, rb.z, 0.0f);
+                    sh.s2[warp][lane] = rc;
+                }
             }
             uint32_t m = __ballot_sync(0xffffffffu, mine);
             if (lane == 0) sh.m[warp] = m;
