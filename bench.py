@@ -134,9 +134,9 @@ def stage_bytes(st, n_inst, tpl_bytes, pixels):
         # the first pass reads no values (they are the indices), the last
         # writes the bin words in depth order (gathered)
         "depth_sort": S * (passes_depth * (4 + 8 + 8) - 4 + 8),
-        # scan: bin words read twice, offsets written; emit: offsets, order
-        # and bin words read, 6 B per pair written
-        "pair_emit": S * (4 + 4 + 4 + 4 + 4 + 4) + P * 6,
+        # block sums of the pair counts: bin words read; emission (with the
+        # scan's down-sweep): bin words and order read, 6 B per pair written
+        "pair_emit": S * (4 + 4 + 4) + P * 6,
         "tile_sort": P * passes_tile * (2 + 6 + 6),
         "tile_ranges": P * 2 * 2,
         # each pair: splat id + 64 B record; each pixel: 16 B written

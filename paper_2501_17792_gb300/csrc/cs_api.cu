@@ -867,7 +867,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->ids2, Sa, "splat ids (ping-pong)"));
     CS_TRY(ensure(ctx, ctx->bins, Sa, "bin words"));
     CS_TRY(ensure(ctx, ctx->bins_sorted, Sa, "bin words in depth order"));
-    CS_TRY(ensure(ctx, ctx->pair_off, Sa + 1, "pair offsets"));
+    CS_TRY(ensure(ctx, ctx->pair_off, bin_scan_blocks(Sa) + 1, "pair-count block sums"));
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Sa), scan_scratch_words(Sa + 1)), "scratch"));
     const TemplateArrays ta = template_arrays(ctx);
     if (S > 0)
@@ -886,10 +886,13 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     uint32_t *sorted_keys = ob ? ctx->key2.p : ctx->key.p;
     if (timing) CS_CUDA(cudaEventRecord(ev[4], st));
     // 5. pair offsets in depth order and pair emission
-    launched += exclusive_scan_bins(ctx->bins_sorted.p, ctx->pair_off.p, (uint32_t)S, ctx->scratch.p, st);
+    // (the per-block sums of the pair counts live in pair_off)
+    const size_t nbs = bin_scan_blocks((size_t)S);
+    launched += bin_scan_sums(ctx->bins_sorted.p, (uint32_t)S, ctx->pair_off.p, st);
     CS_CUDA(cudaGetLastError());
     if (stats && S > 0) launched += launch_count_live((uint32_t)S, sorted_keys, ctx->d_meta + kMetaWords - 1, st);
-    CS_CUDA(cudaMemcpyAsync(ctx->h_pairs, ctx->pair_off.p + S, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    if (S > 0) CS_CUDA(cudaMemcpyAsync(ctx->h_pairs, ctx->pair_off.p + nbs, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    else ctx->h_pairs[0] = 0;
     if (stats) CS_CUDA(cudaMemcpyAsync(ctx->h_pairs + 1, ctx->d_meta + kMetaWords - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CS_CUDA(cudaStreamSynchronize(st));
     const int64_t P = ctx->h_pairs[0];
@@ -900,8 +903,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->pval, Pa, "pair splats"));
     CS_TRY(ensure(ctx, ctx->pval2, Pa, "pair splats (ping-pong)"));
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Pa), radix_scratch_words(Sa)), "scratch"));
-    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, ctx->bins_sorted.p, ctx->pair_off.p, ctx->rec.p,
-                                             cp.tiles_x, ctx->ptile.p, ctx->pval.p, st);
+    if (P > 0) launched += launch_emit_pairs_scan((uint32_t)S, order, ctx->bins_sorted.p, ctx->pair_off.p, ctx->rec.p,
+                                                  cp.tiles_x, ctx->ptile.p, ctx->pval.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[5], st));
     // 6. stable sort of the pairs by tile
     int pb = 0;

@@ -278,6 +278,16 @@ int radix_sort_u32(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint3
                    const uint32_t *gather_src = nullptr, uint32_t *gather_dst = nullptr, bool iota_values = false);
 int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint32_t n, int bits,
                    uint32_t *scratch, cudaStream_t st, int *in_second);
+// Pair emission in two steps around the host's read of the pair count:
+// bin_scan_sums writes the per-block sums of the sorted bin words' pair
+// counts, exclusively scanned, to sums[0 .. nb) and the total to sums[nb]
+// (nb = bin_scan_blocks(n)); launch_emit_pairs_scan then writes every
+// splat's pairs (the scan's down-sweep fused into the emission).
+size_t bin_scan_blocks(size_t n);
+int bin_scan_sums(const uint32_t *bins, uint32_t n, uint32_t *sums, cudaStream_t st);
+int launch_emit_pairs_scan(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
+                           const uint32_t *sums, const float4 *rec, int tiles_x, uint16_t *ptile, uint32_t *pval,
+                           cudaStream_t st);
 int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
                       const uint32_t *pair_off, const float4 *rec, int tiles_x, uint16_t *ptile,
                       uint32_t *pval, cudaStream_t st);

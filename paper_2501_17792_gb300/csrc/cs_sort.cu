@@ -350,23 +350,14 @@ int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint3
 // pair emission in depth order, tile ranges, live count
 // ---------------------------------------------------------------------------
 
-// Pairs of one splat (in depth order): every tile its reach box meets.  Small
-// splats carry those tiles as a 3x3 mask in their bin word (gathered into
-// depth order by the depth sort); larger ones take the reach box from the
-// record.
-__global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *__restrict__ order,
-                                                    const uint32_t *__restrict__ bins,
-                                                    const uint32_t *__restrict__ pair_off,
-                                                    const float4 *__restrict__ rec, int tiles_x,
-                                                    uint16_t *__restrict__ ptile,
-                                                    uint32_t *__restrict__ pval) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t o = pair_off[i];
-    const uint32_t e = pair_off[i + 1];
-    if (o == e) return;
-    const uint32_t s = order[i];
-    const uint32_t b = bins[i];
+// Pairs of one splat: every tile its reach box meets, written to
+// ptile / pval from position o (at most e - o of them).  Small splats carry
+// those tiles as a 3x3 mask in their bin word (gathered into depth order by
+// the depth sort); larger ones take the reach box from the record.
+__device__ __forceinline__ void emit_splat_pairs(uint32_t b, uint32_t s, uint32_t o, uint32_t e,
+                                                 const float4 *__restrict__ rec, int tiles_x,
+                                                 uint16_t *__restrict__ ptile, uint32_t *__restrict__ pval) {
+    if (o >= e) return;
     if (!(b & kBinLarge)) {
         const uint32_t x0 = b & 0xFFu, y0 = (b >> 8) & 0xFFu;
         uint32_t m = (b >> 16) & 0x1FFu;
@@ -391,6 +382,61 @@ __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *
             ++o;
         }
     }
+}
+
+// Thread per sorted splat, offsets from a scan of the sorted bin words.
+__global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *__restrict__ order,
+                                                    const uint32_t *__restrict__ bins,
+                                                    const uint32_t *__restrict__ pair_off,
+                                                    const float4 *__restrict__ rec, int tiles_x,
+                                                    uint16_t *__restrict__ ptile,
+                                                    uint32_t *__restrict__ pval) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    emit_splat_pairs(bins[i], order[i], pair_off[i], pair_off[i + 1], rec, tiles_x, ptile, pval);
+}
+
+// Pair emission fused with the down-sweep of the pair-count scan: block b
+// takes the kScanTile splats from b kScanTile in depth order, in kScanItems
+// rounds of kScanThreads consecutive splats (one per thread, coalesced); its
+// offset comes from the scanned block sums, each round is scanned in the
+// block, so no per-splat offset array is written or read.
+__global__ void __launch_bounds__(kScanThreads) k_emit_pairs_scan(uint32_t n, const uint32_t *__restrict__ order,
+                                                                 const uint32_t *__restrict__ bins,
+                                                                 const uint32_t *__restrict__ sums,
+                                                                 const float4 *__restrict__ rec, int tiles_x,
+                                                                 uint16_t *__restrict__ ptile,
+                                                                 uint32_t *__restrict__ pval) {
+    __shared__ uint32_t total;
+    uint32_t carry = sums[blockIdx.x];
+#pragma unroll 1
+    for (int r = 0; r < kScanItems; ++r) {
+        const uint32_t i = blockIdx.x * kScanTile + r * kScanThreads + threadIdx.x;
+        const uint32_t b = i < n ? bins[i] : 0u;
+        const uint32_t c = bin_count(b);
+        const uint32_t o = carry + block_excl_scan(c, &total);
+        if (c) emit_splat_pairs(b, order[i], o, o + c, rec, tiles_x, ptile, pval);
+        carry += total;
+    }
+}
+
+size_t bin_scan_blocks(size_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+int bin_scan_sums(const uint32_t *bins, uint32_t n, uint32_t *sums, cudaStream_t st) {
+    if (n == 0) return 0;
+    const uint32_t nb = (uint32_t)bin_scan_blocks(n);
+    k_scan_reduce<1><<<nb, kScanThreads, 0, st>>>(bins, n, sums);
+    k_scan_spine<<<1, kScanThreads, 0, st>>>(sums, nb);
+    return 2;
+}
+
+int launch_emit_pairs_scan(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
+                           const uint32_t *sums, const float4 *rec, int tiles_x, uint16_t *ptile, uint32_t *pval,
+                           cudaStream_t st) {
+    if (n_splats == 0) return 0;
+    k_emit_pairs_scan<<<(uint32_t)bin_scan_blocks(n_splats), kScanThreads, 0, st>>>(n_splats, order, bins_sorted,
+                                                                                    sums, rec, tiles_x, ptile, pval);
+    return 1;
 }
 
 int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
