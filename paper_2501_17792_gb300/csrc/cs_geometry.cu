@@ -625,22 +625,16 @@ __device__ __forceinline__ void project_chunk(
             const float u = cam.fx * tx * iz + cam.cx;
             const float v = cam.fy * ty * iz + cam.cy;
             // pixels with centre inside the support box, clipped to the image
-            int px0, px1, py0, py1;
-            box_range(u, r, cam.W, px0, px1);
-            box_range(v, r, cam.H, py0, py1);
-            live = r > 0.0f && px0 <= px1 && py0 <= py1 && isfinite(u) && isfinite(v) &&
-                   isfinite(r) && isfinite(cA) && isfinite(cB) && isfinite(cC);
-            int ax0 = 0, ax1 = -1, ay0 = 0, ay1 = -1;
             const float fcut = splat_fcut(mo.w);
-            if (live && fcut >= 0.0f) {
-                // pixel range where alpha can reach 1/255 (ellipse extent),
-                // inside the support box
-                box_range(u, ellipse_reach(fcut, a), cam.W, ax0, ax1);
-                box_range(v, ellipse_reach(fcut, c), cam.H, ay0, ay1);
-                ax0 = max(ax0, px0);
-                ax1 = min(ax1, px1);
-                ay0 = max(ay0, py0);
-                ay1 = min(ay1, py1);
+            live = r > 0.0f && fcut >= 0.0f && isfinite(u) && isfinite(v) && isfinite(r) && isfinite(cA) &&
+                   isfinite(cB) && isfinite(cC);
+            int ax0 = 0, ax1 = -1, ay0 = 0, ay1 = -1;
+            if (live) {
+                // pixel range where alpha can reach 1/255 (ellipse extent)
+                // inside the support box: both are centred on the mean, so
+                // their intersection is the box of the smaller half-width
+                box_range(u, fminf(ellipse_reach(fcut, a), r), cam.W, ax0, ax1);
+                box_range(v, fminf(ellipse_reach(fcut, c), r), cam.H, ay0, ay1);
                 // the tiles the reach box meets: a 3x3 window of them is kept
                 // as a mask (bin word), larger boxes as a count
                 if (ax0 <= ax1 && ay0 <= ay1) {
