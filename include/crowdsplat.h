@@ -213,9 +213,13 @@ int cs_render(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats
 int cs_render_contrib(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, float *contrib_out,
                       cs_frame_stats *stats);
 
-/* cs_render into an internal device buffer followed by a device->host copy
- * of the image into rgba_host (HOST memory, pinned for full speed); returns
- * after the copy completes.  Same errors as cs_render. */
+/* cs_render with the image delivered to rgba_host (HOST memory, H*W*4
+ * floats, layout as cs_render's output); returns once the image is there.
+ * When rgba_host is page-locked host memory mapped into the device's
+ * address space (cudaHostAlloc / cudaHostRegister, e.g. a pinned torch
+ * tensor) and 16-byte aligned, the compositing kernels write the image
+ * straight into it; otherwise the frame is rendered into an internal device
+ * buffer followed by one device->host copy.  Same errors as cs_render. */
 int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_frame_stats *stats);
 
 /* cs_render without any device allocation, for callers that may not

@@ -1124,6 +1124,20 @@ int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_fr
     if (cam->width < 1 || cam->height < 1 || cam->width > CS_MAX_IMAGE_SIDE || cam->height > CS_MAX_IMAGE_SIDE)
         return fail(ctx, CS_ERR_ARG, "image size %dx%d outside 1..%d", cam->width, cam->height, CS_MAX_IMAGE_SIDE);
     CS_CUDA(cudaSetDevice(ctx->device));
+    // page-locked host memory mapped into the device's address space: the
+    // compositing kernels write the image straight into it (the stores cross
+    // the host link while the frame is composited; no separate copy)
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, rgba_host) != cudaSuccess) {
+        cudaGetLastError();  // not a CUDA-known pointer: plain pageable memory
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer &&
+        (reinterpret_cast<uintptr_t>(at.devicePointer) & 15u) == 0) {
+        CS_TRY(render_impl(ctx, cam, reinterpret_cast<float4 *>(at.devicePointer), stats));
+        CS_CUDA(cudaStreamSynchronize(ctx->stream));
+        return CS_OK;
+    }
     const size_t npix = (size_t)cam->width * cam->height;
     CS_TRY(ensure(ctx, ctx->img, npix, "image"));
     CS_TRY(render_impl(ctx, cam, ctx->img.p, stats));

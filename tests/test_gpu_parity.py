@@ -200,8 +200,12 @@ def test_deterministic_and_host_output():
     a = render(r, sc)
     b = render(r, sc)
     assert np.array_equal(a, b)
-    c = r.render_to_host(sc.camera)
+    c = r.render_to_host(sc.camera)  # pageable numpy buffer: rendered on the device, then copied
     assert np.array_equal(a, c)
+    # pinned host buffer: the compositing kernels write into it directly
+    pinned = torch.full((sc.camera.height, sc.camera.width, 4), float("nan"), dtype=torch.float32).pin_memory()
+    d = r.render_to_host(sc.camera, out=pinned.numpy())
+    assert np.array_equal(a, d) and np.array_equal(a, pinned.numpy())
 
 
 # ---------------------------------------------------------------------------
