@@ -5,12 +5,14 @@
 // support box touches and sorts the (tile, depth) keys so that each tile
 // can composite its splats front to back.  Here the order is reached in two
 // stable stages instead of one 64-bit sort:
-//   1. a stable LSD radix sort of the splats by 32-bit depth (4 passes);
+//   1. a stable LSD radix sort of the splats by depth key (as many bits as
+//      the frame's depth range needs, digits of at most 9 bits);
 //   2. pairs are emitted in that depth order (prefix sum of tile counts),
-//      then a stable LSD radix sort by tile index (ceil(bits/8) passes, 16-bit
-//      keys) leaves every tile's pairs in (depth, splat id) order.
-// Each radix pass is reduce-then-scan (histogram, exclusive scan,
-// scatter): no inter-block waits, and the order is deterministic.
+//      then a stable LSD radix sort by tile index (16-bit keys, 13 bits at
+//      1080p as 7 + 6) leaves every tile's pairs in (depth, splat id) order.
+// Each radix pass is reduce-then-scan (histogram of each digit per block,
+// one CTA per digit scanning its row of block counts, scatter): no
+// inter-block waits, and the order is deterministic.
 #include "cs_internal.cuh"
 
 namespace cs {
@@ -163,11 +165,42 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const K *__restric
     }
 }
 
+// Exclusive scan of each digit's row of the (digit, block) count matrix
+// (digit-major), one CTA per digit: offs[d][b] = counts of digit d in blocks
+// before b; tot[d] = the digit's total.  The scatter adds the digit's base
+// (an exclusive scan of tot it computes itself).
+__global__ void __launch_bounds__(kScanThreads) k_radix_rowscan(const uint32_t *__restrict__ hist, uint32_t nb,
+                                                                uint32_t *__restrict__ offs,
+                                                                uint32_t *__restrict__ tot) {
+    __shared__ uint32_t total;
+    const uint32_t *row = hist + (size_t)blockIdx.x * nb;
+    uint32_t *orow = offs + (size_t)blockIdx.x * nb;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nb; base += kScanTile) {
+        const uint32_t i0 = base + threadIdx.x * kScanItems;
+        uint32_t v[kScanItems], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            v[k] = i0 + k < nb ? row[i0 + k] : 0u;
+            sum += v[k];
+        }
+        uint32_t ex = block_excl_scan(sum, &total) + carry;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (i0 + k < nb) orow[i0 + k] = ex;
+            ex += v[k];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
+}
+
 template <typename K, int kBits>
 __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, uint32_t n, int shift, const uint32_t *__restrict__ offs,
-    uint32_t nblocks, const uint32_t *__restrict__ gsrc, uint32_t *__restrict__ gdst) {
+    const uint32_t *__restrict__ dtot_g, uint32_t nblocks, const uint32_t *__restrict__ gsrc,
+    uint32_t *__restrict__ gdst) {
     constexpr uint32_t kDigits = 1u << kBits;
     constexpr int kPer = kDigits > (uint32_t)kRadixThreads ? (int)kDigits / kRadixThreads : 1;  // digits per thread
     __shared__ uint32_t wcnt[kRadixWarps][kDigits];  // running counts, then warp offsets
@@ -216,12 +249,14 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
     }
     __syncthreads();
     // per digit (thread t: digits t kPer .. t kPer + kPer - 1): exclusive
-    // prefix over warps, and the digit's block total
-    uint32_t tot = 0, dtot[kPer];
+    // prefix over warps, and the digit's block total; the digit's global
+    // total for the digit bases
+    uint32_t tot = 0, dtot[kPer], gtot = 0, gt[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const int d = threadIdx.x * kPer + j;
         dtot[j] = 0;
+        gt[j] = 0;
         if (d < (int)kDigits) {
             uint32_t run = 0;
 #pragma unroll
@@ -232,16 +267,23 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
             }
             dtot[j] = run;
             tot += run;
-            gbase[d] = offs[(size_t)d * nblocks + blockIdx.x];
+            gt[j] = dtot_g[d];
+            gtot += gt[j];
         }
     }
     // block-local digit starts
     uint32_t ex = block_excl_scan(tot, &total);
+    // global digit bases: exclusive scan of the digit totals
+    uint32_t gex = block_excl_scan(gtot, &total);
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const int d = threadIdx.x * kPer + j;
-        if (d < (int)kDigits) dstart[d] = ex;
+        if (d < (int)kDigits) {
+            dstart[d] = ex;
+            gbase[d] = gex + offs[(size_t)d * nblocks + blockIdx.x];
+        }
         ex += dtot[j];
+        gex += gt[j];
     }
     __syncthreads();
     // block-local sort in shared memory
@@ -273,7 +315,7 @@ size_t radix_scratch_words(size_t n) {
     size_t nb = (n + kRadixTile - 1) / kRadixTile;
     if (nb == 0) nb = 1;
     size_t hist = (size_t)kRadixDigits * nb;
-    return 2 * hist + 1 + scan_scratch_words(hist);
+    return 2 * hist + kRadixDigits;
 }
 
 // one pass over digit bits [shift, shift + kBits)
@@ -283,7 +325,7 @@ static int radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, uint
     const uint32_t hn = (1u << kBits) * nb;
     uint32_t *hist = scratch;
     uint32_t *offs = scratch + hn;
-    uint32_t *sc = scratch + 2 * hn + 1;
+    uint32_t *dtot = scratch + 2 * hn;
     constexpr int kDyn = kRadixTile * (int)(sizeof(uint32_t) + sizeof(K));
     static int configured_device = -1;
     int dev = 0;
@@ -293,9 +335,10 @@ static int radix_pass(const K *ki, const uint32_t *vi, K *ko, uint32_t *vo, uint
         configured_device = dev;
     }
     k_radix_hist<K, kBits><<<nb, kRadixThreads, 0, st>>>(ki, n, shift, hist, nb);
-    int launched = 1 + exclusive_scan(hist, nullptr, offs, hn, sc, st);
-    k_radix_scatter<K, kBits><<<nb, kRadixThreads, kDyn, st>>>(ki, vi, ko, vo, n, shift, offs, nb, gsrc, gdst);
-    return launched + 1;
+    k_radix_rowscan<<<1u << kBits, kScanThreads, 0, st>>>(hist, nb, offs, dtot);
+    k_radix_scatter<K, kBits><<<nb, kRadixThreads, kDyn, st>>>(ki, vi, ko, vo, n, shift, offs, dtot, nb, gsrc,
+                                                              gdst);
+    return 3;
 }
 
 template <typename K>
