@@ -112,7 +112,8 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes per stage (per frame), see the design doc
+# algorithmic bytes per stage (per frame): the bytes each stage must move at
+# least, from the frame statistics (splats, live splats, pairs, passes)
 # ---------------------------------------------------------------------------
 
 def stage_bytes(st, n_inst, tpl_bytes, pixels):
