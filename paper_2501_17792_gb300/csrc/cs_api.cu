@@ -872,9 +872,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     const TemplateArrays ta = template_arrays(ctx);
     if (S > 0)
         launched += launch_project(proj_blocks, ctx->groups.p, ctx->h_groups, ctx->n_groups, ctx->tpl_host.data(),
-                                   ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
-                       ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
-                       ctx->rec.p, ctx->key.p, ctx->bins.p, st);
+                                   ctx->vis.p, ctx->B.p, ctx->V.p, ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod,
+                                   ctx->skin_mode, ctx->sh_frame, ctx->rec.p, ctx->key.p, ctx->bins.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[3], st));
     // 4. depth sort of the splats (stable, ties by splat id)
     int ob = 0;
@@ -1401,9 +1400,8 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     const TemplateArrays ta = template_arrays(ctx);
     if (S > 0)
         launched += launch_project(proj_blocks, ctx->groups.p, ctx->h_groups, n_groups, ctx->tpl_host.data(),
-                                   ctx->vis.p, ctx->B.p, ctx->V.p, ctx->Cloc.p,
-                                   ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod, ctx->skin_mode, ctx->sh_frame,
-                                   rec, key, bins, st);
+                                   ctx->vis.p, ctx->B.p, ctx->V.p, ctx->root.p, ta, ctx->d_tpl, cp, ctx->lod,
+                                   ctx->skin_mode, ctx->sh_frame, rec, key, bins, st);
     if (radix_scratch_words((size_t)std::max<int64_t>(S, 1)) > kStaticScratchWords ||
         scan_scratch_words((size_t)S + 1) > kStaticScratchWords)
         return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: scratch too small for %lld splats", (long long)S);

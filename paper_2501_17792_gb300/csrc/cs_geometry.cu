@@ -491,9 +491,8 @@ template <int kStore>
 __device__ __forceinline__ void project_chunk(
     const ProjGroup &G, int islot, int chunk, int inst, const float4 *__restrict__ sB,
     const float4 *__restrict__ sV, unsigned char *s_tc,
-    const float *__restrict__ Vm, const float *__restrict__ Cloc, const float *__restrict__ root,
-    const TemplateArrays &ta, const TemplateInfo *__restrict__ tpls, const CamParams &cam, const LodParams &lod,
-    int skin_mode, int sh_frame, float4 *__restrict__ rec, uint32_t *__restrict__ key,
+    const float *__restrict__ Vm, const float *__restrict__ root, const TemplateArrays &ta,
+    const TemplateInfo *__restrict__ tpls, const CamParams &cam, const LodParams &lod, int skin_mode, int sh_frame, float4 *__restrict__ rec, uint32_t *__restrict__ key,
     uint32_t *__restrict__ bin) {
     const int gg = chunk * kProjThreads + threadIdx.x;
     const bool valid = gg < G.ng;
@@ -706,8 +705,7 @@ __device__ __forceinline__ void project_chunk(
 template <int kStore, int kChunks>
 __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     const Group *__restrict__ groups, int n_groups, int n_vblocks, const int32_t *__restrict__ vis,
-    const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ Cloc,
-    const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,
+    const float *__restrict__ Bm, const float *__restrict__ Vm, const float *__restrict__ root, TemplateArrays ta, const TemplateInfo *__restrict__ tpls,
     CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
     uint32_t *__restrict__ key, uint32_t *__restrict__ bin, const __grid_constant__ ProjGroups pg) {
     static_assert(kStore == kStoreFp32 || kChunks == 1, "the BF16 blend needs one chunk per CTA");
@@ -762,7 +760,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
             __syncthreads();
             staged = inst;
         }
-        project_chunk<kStore>(G, islot, chunk, inst, sB, sV, s_tc, Vm, Cloc, root, ta, tpls, cam, lod, skin_mode,
+        project_chunk<kStore>(G, islot, chunk, inst, sB, sV, s_tc, Vm, root, ta, tpls, cam, lod, skin_mode,
                               sh_frame, rec, key, bin);
     }
 }
@@ -771,7 +769,7 @@ constexpr int kProjChunksFp32 = 8;
 
 int launch_project(int n_blocks, const Group *groups, const Group *groups_host, int n_groups,
                    const TemplateInfo *tpl_host, const int32_t *vis, const float *B, const float *V,
-                   const float *Cloc, const float *root, const TemplateArrays &ta, const TemplateInfo *tpls,
+                   const float *root, const TemplateArrays &ta, const TemplateInfo *tpls,
                    const CamParams &cam, const LodParams &lod, int skin_mode, int sh_frame, float4 *rec,
                    uint32_t *key, uint32_t *bin, cudaStream_t st) {
     if (n_blocks <= 0 || n_groups <= 0 || n_groups > kMaxGroups) return 0;
@@ -793,13 +791,13 @@ int launch_project(int n_blocks, const Group *groups, const Group *groups_host, 
         P.sh_off = T.sh_off;
     }
     if (ta.storage == kStoreBf16) {
-        k_project<kStoreBf16, 1><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, n_blocks, vis, B, V, Cloc, root,
-                                                                   ta, tpls, cam, lod, skin_mode, sh_frame, rec,
+        k_project<kStoreBf16, 1><<<n_blocks, kProjThreads, 0, st>>>(groups, n_groups, n_blocks, vis, B, V, root, ta,
+                                                                   tpls, cam, lod, skin_mode, sh_frame, rec,
                                                                    key, bin, pg);
     } else {
         const int grid = (n_blocks + kProjChunksFp32 - 1) / kProjChunksFp32;
         k_project<kStoreFp32, kProjChunksFp32><<<grid, kProjThreads, 0, st>>>(
-            groups, n_groups, n_blocks, vis, B, V, Cloc, root, ta, tpls, cam, lod, skin_mode, sh_frame, rec, key,
+            groups, n_groups, n_blocks, vis, B, V, root, ta, tpls, cam, lod, skin_mode, sh_frame, rec, key,
             bin, pg);
     }
     return 1;

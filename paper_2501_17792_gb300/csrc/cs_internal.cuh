@@ -249,7 +249,7 @@ int launch_cull_group(int n_inst, int n_tpl, const int32_t *tid, const float *ro
                        int32_t *meta, cudaStream_t st);
 int launch_project(int n_blocks, const Group *groups, const Group *groups_host, int n_groups,
                    const TemplateInfo *tpl_host, const int32_t *vis, const float *B, const float *V,
-                   const float *Cloc, const float *root, const TemplateArrays &ta, const TemplateInfo *tpls,
+                   const float *root, const TemplateArrays &ta, const TemplateInfo *tpls,
                    const CamParams &cam, const LodParams &lod, int skin_mode, int sh_frame, float4 *rec,
                    uint32_t *key, uint32_t *bin, cudaStream_t st);
 // Tile rectangle of each splat's support box (debug view; recomputed from the
