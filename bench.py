@@ -151,6 +151,34 @@ def workload_name(sc):
             f"{sc.camera.width}x{sc.camera.height}_lod{len(sc.lod.fractions)}_animated")
 
 
+def bench_config(sc, args, world=1):
+    """The config object of both arms' JSON lines (same keys)."""
+    return {"workload": workload_name(sc), "templates": len(sc.templates),
+            "gaussians_per_template": int(sc.templates[0].n), "sh_degree": int(sc.templates[0].sh_degree),
+            "instances": int(sc.instances.n), "width": sc.camera.width, "height": sc.camera.height,
+            "lod": {"thresholds_m": [float(x) for x in sc.lod.thresholds],
+                    "fractions": [round(float(x), 4) for x in sc.lod.fractions]},
+            "l2": "inputs larger than L2 (templates 231 MB, splat records > 1 GB per frame)",
+            "parallelism": f"replicas{world}" if world > 1 else "single",
+            "template_storage": args.storage}
+
+
+def project_survey_bytes(st, tpl_bytes):
+    """Algorithmic bytes of the fused skinning + projection kernel as the
+    hot-path scope table counts them: the shared templates read once, the
+    24 skinning transforms (48 B each) of every visible instance, and one
+    40-byte splat record written per Gaussian-instance."""
+    return tpl_bytes + st["instances_visible"] * 24 * 48 + st["splats"] * 40
+
+
+def profile_figures():
+    """Per-kernel figures taken from the committed ncu summaries (DRAM
+    traffic per launch, pipe utilisation); an entry is null once its kernel
+    has changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "ncu_metrics.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
 def template_bytes(sc, storage="fp32"):
     """Device bytes of the uploaded templates (the library's layout)."""
     tot = 0
@@ -167,50 +195,58 @@ def template_bytes(sc, storage="fp32"):
 # oracle on the host cores (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 
-def oracle_frame_time(sc, stride=16):
-    """Seconds for one full frame of the oracle, from two bounded runs: a
-    single-pixel lattice (all projection work, no compositing) and a lattice
-    of every `stride`-th pixel in both directions (adds 1/stride^2 of the
-    compositing).  Full frame = project + stride^2 x (lattice - project)."""
+def oracle_sample(os_, sc, stride=16, offset=(0, 0)):
+    """One bounded sample of the oracle's frame: the FP64 projection of
+    every instance (a one-pixel render) and the composite of every
+    `stride`-th pixel in x and y from `offset` (1/stride^2 of the pixels).
+    Returns (seconds the sample took, full-frame seconds extrapolated as
+    projection + stride^2 x the lattice's compositing time, details)."""
     import oracle
-    os_ = oracle.OracleScene(sc)
     W, H = sc.camera.width, sc.camera.height
     t0 = time.perf_counter()
     oracle.render(os_, lattice=(W // 2, H // 2, 1, 1, 1, 1))
     t_proj = time.perf_counter() - t0
-    nx, ny = (W + stride - 1) // stride, (H + stride - 1) // stride
+    ox, oy = offset
+    nx, ny = (W - ox + stride - 1) // stride, (H - oy + stride - 1) // stride
     t0 = time.perf_counter()
-    oracle.render(os_, lattice=(0, 0, stride, stride, nx, ny))
+    oracle.render(os_, lattice=(ox, oy, stride, stride, nx, ny))
     t_lat = time.perf_counter() - t0
-    t_pix = max(t_lat - t_proj, 0.0)
-    full = t_proj + t_pix * (W * H) / (nx * ny)
-    return full, dict(project_s=round(t_proj, 3), lattice_s=round(t_lat, 3), stride=stride,
-                      lattice_px=nx * ny, cores=oracle.num_threads())
+    full = t_proj + max(t_lat - t_proj, 0.0) * (W * H) / (nx * ny)
+    return t_proj + t_lat, full, dict(project_s=round(t_proj, 3), lattice_s=round(t_lat, 3), stride=stride,
+                                      lattice_px=nx * ny, cores=oracle.num_threads())
 
 
 def run_reference(args, sc, rank, world):
+    """The reference arm: the FP64 CPU oracle (there is no reference code;
+    the reference is the paper's text).  Each step is one bounded sample of
+    the frame (projection of all instances + one 1/256 pixel lattice, the
+    lattice offset moving from step to step); ms_per_step is the measured
+    wall time of a step, value the median full-frame rate the samples
+    extrapolate to.  Rank 0 only."""
     if rank != 0:
         return
     import oracle
     oracle.build()
-    times = []
-    info = {}
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm state; warm-up steps are not run
-    for step in range(args.steps):
-        full, info = oracle_frame_time(sc, stride=args.oracle_stride)
-        times.append(full)
-    med = statistics.median(times)
-    fps = 1.0 / med
-    sample = (f"every {info['stride']}th pixel in x and y ({info['lattice_px']} px) composited after "
-              f"projecting all {sc.instances.n} instances in FP64; full-frame time extrapolated as "
-              f"project + {info['stride']}^2 x composite")
+    os_ = oracle.OracleScene(sc)
+    st = args.oracle_stride
+    for w in range(min(args.warmup, 1)):  # the oracle has no warm state: one untimed sample
+        oracle_sample(os_, sc, st, (w % st, w % st))
+    wall, full, info = [], [], {}
+    for k in range(args.steps):
+        wt, ft, info = oracle_sample(os_, sc, st, ((5 * k) % st, (11 * k) % st))
+        wall.append(wt)
+        full.append(ft)
+    fps = 1.0 / statistics.median(full)
+    sample = (f"per step: FP64 projection of all {sc.instances.n} instances + every {st}th pixel in x and y "
+              f"({info['lattice_px']} px, offset moving per step); full frame = projection + {st}^2 x lattice "
+              f"compositing time (median over steps {statistics.median(full):.1f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": med * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(wall) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(sc)},
+            "data": "synthetic", "config": bench_config(sc, args, world),
             "cpu_baseline": {"value": fps, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-                             "sample": sample, **{k: info[k] for k in ("project_s", "lattice_s")}},
+                             "sample": sample, "frame_s_extrapolated": round(statistics.median(full), 2),
+                             "sample_s": round(statistics.mean(wall), 3)},
             "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -302,55 +338,82 @@ def run_ours(args, sc, rank, world, local_rank):
     d2h = sc.camera.width * sc.camera.height * 16
 
     if rank != 0:
+        r.close()
         return
     pk = peaks()
     pixels = sc.camera.width * sc.camera.height
-    sb = stage_bytes(st0, n, template_bytes(sc, args.storage), pixels)
+    tpl_b = template_bytes(sc, args.storage)
+    sb = stage_bytes(st0, n, tpl_b, pixels)
+    prof = profile_figures()
     stages = {}
     for name, ms in stage_ms.items():
+        if name not in sb:
+            stages[name] = {"ms": round(ms, 4)}
+            continue
         gbs = sb[name] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
         stages[name] = {"ms": round(ms, 4), "algo_bytes": int(sb[name]), "GB/s": round(gbs, 1),
-                        "frac": round(gbs / pk["hbm_gbs"], 4)}
-    # the roofline kernel: k_project, the largest single kernel of the frame
-    # (the blend stage is five kernels, bound by latency, not DRAM)
-    top = "skin_project"
-    prof = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))) if os.path.exists(
-        os.path.join(ROOT, "profiles", "traffic.json")) else {}
-    traffic = prof.get(top)
-    achieved = stages[top]["GB/s"]
+                        "frac_of_measured_hbm": round(gbs / pk["hbm_gbs"], 4)}
+    if "blend" in stages:
+        # compositing is bound by FP32 issue and the exp unit, not DRAM: its
+        # fraction is the FMA-pipe utilisation of the committed capture
+        bl = prof.get("k_blend", {})
+        stages["blend"] = {"ms": stages["blend"]["ms"], "bound": "fp32 issue",
+                           "fp32_pipe_frac": bl.get("fma_pipe_frac"), "source": bl.get("source")}
+    # the roofline kernel: k_project, the largest single kernel of the frame,
+    # with the scope table's algorithmic bytes (templates once, transforms,
+    # 40 B per splat record); its measured DRAM traffic is the committed
+    # one-pass capture's, null once the kernel has changed since
+    top_ms = stage_ms["skin_project"]
+    algo = project_survey_bytes(st0, tpl_b)
+    achieved = algo / (top_ms * 1e-3) / 1e9
+    kp = prof.get("k_project", {})
+    traffic = kp.get("dram_bytes_per_launch")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.storage == "fp32" else "f32 compute, bf16/fp16 template storage", "data": "synthetic",
-        "config": {"workload": workload_name(sc), "templates": len(sc.templates), "gaussians_per_template": int(sc.templates[0].n),
-                   "sh_degree": int(sc.templates[0].sh_degree), "instances": n, "width": sc.camera.width,
-                   "height": sc.camera.height, "lod": {"thresholds_m": [10, 30], "fractions": [1, 0.25, 0.06]},
-                   "l2": "inputs larger than L2 (templates 231 MB, splat records > 1 GB per frame)",
-                   "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "template_storage": args.storage},
+        "config": bench_config(sc, args, world),
         "frame": {"visible_instances": st0["instances_visible"], "per_level": st0["instances_per_level"][:3],
                   "splats": st0["splats"], "pairs": st0["pairs"],
                   "gaussians_per_s": st0["splats"] * value},
         "stages": stages,
-        "roofline": {"bound": "hbm", "kernel": "k_project", "achieved": achieved, "peak": pk["hbm_gbs"],
+        "roofline": {"bound": "hbm", "kernel": "k_project", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
                      "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
-                     "peak_source": f"{pk['src']} (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured" else "fallback"},
+                     "algorithmic_bytes": int(algo),
+                     "traffic_over_algorithmic": round(traffic / algo, 3) if traffic else None,
+                     "ms": round(top_ms, 4),
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured" else "fallback"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(st0["kernel_launches"]) * args.steps,
         "clocks": clocks,
         "paper_context": {"fps": PAPER_FPS, "hardware": "RTX4090 + i9-13900", "note": "different workload, context only"},
     }
+    r.close()
+    del poses, out
+    torch.cuda.empty_cache()
+    if not args.no_learned_lod:
+        line["learned_lod"] = learned_lod_summary(learned_lod_eval(args, reduced=True))
     if not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        full, info = oracle_frame_time(sc, stride=args.oracle_stride)
-        line["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
-                                "sample": (f"every {info['stride']}th pixel in x and y ({info['lattice_px']} px) "
-                                           f"after FP64 projection of all {n} instances; full frame extrapolated "
-                                           f"(project {info['project_s']} s, lattice {info['lattice_s']} s)")}
+        os_ = oracle.OracleScene(sc)
+        wall, full, t0, k = [], [], time.perf_counter(), 0
+        st = args.oracle_stride
+        while k < 3 or (time.perf_counter() - t0 < args.cpu_baseline_s and k < st * st):
+            wt, ft, info = oracle_sample(os_, sc, st, ((5 * k) % st, (11 * k) % st))
+            wall.append(wt)
+            full.append(ft)
+            k += 1
+        line["cpu_baseline"] = {"value": 1.0 / statistics.median(full), "unit": UNIT, "cores": info["cores"],
+                                "kind": "oracle",
+                                "sample": (f"{k} samples, each the FP64 projection of all {n} instances + every "
+                                           f"{st}th pixel in x and y ({info['lattice_px']} px, offset moving per "
+                                           f"sample); full frame = projection + {st}^2 x lattice compositing time "
+                                           f"(median {statistics.median(full):.1f} s); {sum(wall):.1f} s of CPU "
+                                           f"wall time"),
+                                "frame_s_extrapolated": round(statistics.median(full), 2)}
     print(json.dumps(line), flush=True)
-    r.close()
 
 
 # ---------------------------------------------------------------------------
@@ -443,11 +506,12 @@ def _fps(r, cam, tid, root, poses, out, warmup, steps):
     return steps / (e0.elapsed_time(e1) / 1e3)
 
 
-def run_learned_lod(args):
+def learned_lod_eval(args, reduced=False):
     """Ranked (learned) LoD against the distance LoD with prefix subsets, at
-    10,000 instances and 3840x2160: PSNR against the full-detail frame at the
-    same Gaussian budget, and FPS of the learned ranking at the smallest
-    budget that matches the distance LoD's PSNR."""
+    10,000 instances and 3840x2160.  PSNR against the full-detail frame is
+    the mean over `frames` animated frames (different poses); the learned
+    ranking is timed at the smallest budget whose mean PSNR matches the
+    distance LoD's.  Returns the JSON object of the comparison."""
     import numpy as np
     import torch
     from paper_2501_17792_gb300 import binding, build
@@ -459,25 +523,29 @@ def run_learned_lod(args):
     cols, rows = (30, 30) if small else (100, 100)
     n_tpl, n_g = (4, 16384) if small else (14, 65536)
     views = 8 if small else 34
+    frames = 5
+    t_all = time.time()
     tpls = [S.make_template(1000 + t, n_g, 3) for t in range(n_tpl)]
     cam = S.look_camera((0.0, 1.6, 0.0), 10.0, W, H)
     r = binding.Renderer(device=0)
     r.upload_templates(tpls)
     sizes = r.template_sizes
     # 1. training data: contributions of every Gaussian per distance band
+    torch.cuda.synchronize()
     t0 = time.time()
     feat = r.lod_features()
     contrib = LOD.collect_contributions(r, n_tpl, cam, views_per_band=views, instances_per_view=100, seed=5)
-    t_collect = time.time() - t0
     targets = r.lod_targets(contrib)
+    torch.cuda.synchronize()
+    t_collect = time.time() - t0
     # 2. the ranking MLP
     t0 = time.time()
     mlp = binding.Mlp(device=0, seed=1)
     hist = LOD.train_ranker(mlp, feat, targets, steps=args.lod_steps, log_every=max(1, args.lod_steps // 5))
+    scores = LOD.band_scores(mlp, feat, 3)
     torch.cuda.synchronize()
     t_train = time.time() - t0
-    scores = LOD.band_scores(mlp, feat, 3)
-    # rank correlation of predicted and measured order, per band (Spearman, host)
+
     def spearman(a, b):
         ra = np.argsort(np.argsort(a)).astype(np.float64)
         rb = np.argsort(np.argsort(b)).astype(np.float64)
@@ -494,74 +562,77 @@ def run_learned_lod(args):
         return S.LodConfig(thresholds=base.thresholds, fractions=fr.astype(np.float32),
                            scale_mult=(fr ** -expo).astype(np.float32)), fr
 
-    def frame_images(inst, poses_dev, configs):
-        """Images of frame 0 for each (name, lod, subsets-or-None)."""
+    def apply(lod, subs):
+        LOD.clear_subsets(r, n_tpl)
+        r.set_lod(lod)
+        if subs is not None:
+            LOD.apply_subsets(r, subs)
+
+    def mean_psnr(inst, pose_list, configs):
+        """{name: (mean PSNR vs full detail over the frames, splats of frame 0)}."""
         tid = torch.from_numpy(inst.template_id).cuda()
         root = torch.from_numpy(inst.root.reshape(-1, 12)).cuda()
-        out = {}
-        for name, lod, subs in configs:
-            LOD.clear_subsets(r, n_tpl)
-            r.set_lod(lod)
-            if subs is not None:
-                LOD.apply_subsets(r, subs)
-            r.set_instances(tid, root, poses_dev[0])
-            img, st = r.render(cam, stats=True)
-            out[name] = (img, st)
-        return out
+        acc = {name: [] for name, _, _ in configs}
+        splats = {}
+        ref = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        img = torch.empty_like(ref)
+        for k, pose in enumerate(pose_list):
+            apply(S.single_lod(), None)
+            r.set_instances(tid, root, pose)
+            _, st = r.render(cam, out=ref, stats=True)
+            splats.setdefault("full", st["splats"])
+            for name, lod, subs in configs:
+                apply(lod, subs)
+                r.set_instances(tid, root, pose)
+                _, st = r.render(cam, out=img, stats=True)
+                acc[name].append(LOD.psnr(img, ref))
+                splats.setdefault(name, st["splats"])
+        return {k: (float(np.mean(v)), int(splats[k])) for k, v in acc.items()}, int(splats["full"])
 
     # 3. scale-multiplier exponent, tuned on a training crowd (other layout
     # and poses) for both methods
     tr_inst = S.crowd_instances(n_tpl, cols, rows, layout_seed=8, pose_seed=300)
-    tr_poses = [torch.from_numpy(tr_inst.pose).cuda()]
     expos = (0.0, 0.25, 0.5)
-    cfgs = [("full", S.single_lod(), None)]
+    cfgs = []
     for e in expos:
         lod, fr = lod_cfg(1.0, e)
         cfgs.append((f"plain_{e}", lod, None))
         cfgs.append((f"learned_{e}", lod, LOD.ranked_subsets(r, scores, fr, sizes, levels=(1, 2))))
-    imgs = frame_images(tr_inst, tr_poses, cfgs)
-    ref = imgs["full"][0]
-    tune = {k: LOD.psnr(v[0], ref) for k, v in imgs.items() if k != "full"}
-    e_plain = max(expos, key=lambda e: tune[f"plain_{e}"])
-    e_learn = max(expos, key=lambda e: tune[f"learned_{e}"])
-    del imgs, ref
+    tune, _ = mean_psnr(tr_inst, [torch.from_numpy(tr_inst.pose).cuda()], cfgs)
+    e_plain = max(expos, key=lambda e: tune[f"plain_{e}"][0])
+    e_learn = max(expos, key=lambda e: tune[f"learned_{e}"][0])
 
-    # 4. evaluation crowd: PSNR vs full detail, budgets, FPS
+    # 4. evaluation crowd: PSNR vs full detail (mean over frames), budgets, FPS
     inst = S.crowd_instances(n_tpl, cols, rows, layout_seed=7, pose_seed=100)
     n = inst.n
-    poses = [torch.from_numpy(S.random_poses(100 + k, n)).cuda() for k in range(args.warmup + args.steps)]
+    poses = [torch.from_numpy(S.random_poses(100 + k, n)).cuda() for k in range(max(frames, args.warmup + args.steps))]
     tid = torch.from_numpy(inst.template_id).cuda()
     root = torch.from_numpy(inst.root.reshape(n, 12)).cuda()
     lod_plain, _ = lod_cfg(1.0, 0.5)
     lod_plain_t, _ = lod_cfg(1.0, e_plain)
-    scales = (1.0, 0.7, 0.5, 0.35, 0.25, 0.18, 0.12, 0.08, 0.05, 0.03, 0.02)
-    cfgs = [("full", S.single_lod(), None), ("plain", lod_plain, None), ("plain_tuned", lod_plain_t, None)]
-    direct = LOD.ranked_subsets(r, contrib, lod_cfg(1.0)[1], sizes, levels=(1, 2))
-    cfgs.append(("direct", lod_cfg(1.0, e_learn)[0], direct))
+    scales = ((1.0, 0.5, 0.25, 0.18, 0.12, 0.08, 0.05, 0.03) if reduced else
+              (1.0, 0.7, 0.5, 0.35, 0.25, 0.18, 0.12, 0.08, 0.05, 0.03, 0.02))
+    cfgs = [("plain", lod_plain, None), ("plain_tuned", lod_plain_t, None)]
     learned_subs = {}
     for s_ in scales:
         lod, fr = lod_cfg(s_, e_learn)
         learned_subs[s_] = (lod, LOD.ranked_subsets(r, scores, fr, sizes, levels=(1, 2)))
         cfgs.append((f"learned_{s_}", lod, learned_subs[s_][1]))
-    imgs = frame_images(inst, poses, cfgs)
-    ref = imgs["full"][0]
-    res = {k: dict(psnr=round(LOD.psnr(v[0], ref), 3), splats=int(v[1]["splats"]), pairs=int(v[1]["pairs"]))
-           for k, v in imgs.items() if k != "full"}
-    full_splats = int(imgs["full"][1]["splats"])
-    del imgs, ref
+    if not reduced:
+        cfgs.append(("direct", lod_cfg(1.0, e_learn)[0],
+                     LOD.ranked_subsets(r, contrib, lod_cfg(1.0)[1], sizes, levels=(1, 2))))
+    res, full_splats = mean_psnr(inst, poses[:frames], cfgs)
+
     def equal_budget(target_psnr):
-        eq = [s_ for s_ in scales if res[f"learned_{s_}"]["psnr"] >= target_psnr]
+        eq = [s_ for s_ in scales if res[f"learned_{s_}"][0] >= target_psnr]
         return min(eq) if eq else None
 
-    s_eq = equal_budget(res["plain"]["psnr"])
-    s_eq_t = equal_budget(res["plain_tuned"]["psnr"])
+    s_eq = equal_budget(res["plain"][0])
+    s_eq_t = equal_budget(res["plain_tuned"][0])
     out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
 
     def fps_of(lod, subs):
-        LOD.clear_subsets(r, n_tpl)
-        r.set_lod(lod)
-        if subs is not None:
-            LOD.apply_subsets(r, subs)
+        apply(lod, subs)
         return _fps(r, cam, tid, root, poses, out, args.warmup, args.steps)
 
     fps_full = fps_of(S.single_lod(), None)
@@ -570,34 +641,59 @@ def run_learned_lod(args):
     fps_same = fps_of(*learned_subs[1.0])
     fps_eq = fps_of(*learned_subs[s_eq]) if s_eq is not None else None
     fps_eq_t = fps_of(*learned_subs[s_eq_t]) if s_eq_t is not None else None
+    r.close()
+    mlp.close()
+    rd = lambda x: round(x, 3)  # noqa: E731
     line = {
         "metric": "learned vs distance LoD: FPS at equal PSNR vs full detail",
         "value": round(fps_eq, 2) if fps_eq else None, "unit": "frames/s",
         "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "dtype": "f32 render, bf16 MLP", "data": "synthetic",
         "config": {"workload": f"crowd_{n_tpl}x{n_g}g_sh3_{n}inst_{W}x{H}_lod3_animated",
-                   "bands_m": [10, 30], "fractions": [1.0, 0.25, 0.06]},
-        "distance_lod": {"fps": round(fps_plain, 2), "psnr_db": res["plain"]["psnr"],
-                         "splats": res["plain"]["splats"], "scale_mult_exponent": 0.5,
-                         "psnr_db_tuned_exponent": res["plain_tuned"]["psnr"], "tuned_exponent": e_plain},
-        "learned_lod_same_budget": {"fps": round(fps_same, 2), "psnr_db": res["learned_1.0"]["psnr"],
-                                    "splats": res["learned_1.0"]["splats"], "scale_mult_exponent": e_learn},
-        "learned_lod_equal_psnr": {"budget_scale": s_eq, "psnr_db": res[f"learned_{s_eq}"]["psnr"] if s_eq else None,
-                                   "splats": res[f"learned_{s_eq}"]["splats"] if s_eq else None},
+                   "bands_m": [10, 30], "fractions": [1.0, 0.25, 0.06],
+                   "psnr": f"mean over {frames} animated frames (poses from seeds 100..{99 + frames}) "
+                           "against the full-detail frame of the same poses"},
+        "distance_lod": {"fps": round(fps_plain, 2), "psnr_db": rd(res["plain"][0]),
+                         "splats": res["plain"][1], "scale_mult_exponent": 0.5},
+        "learned_lod_equal_psnr": {"budget_scale": s_eq, "fps": round(fps_eq, 2) if fps_eq else None,
+                                   "psnr_db": rd(res[f"learned_{s_eq}"][0]) if s_eq else None,
+                                   "splats": res[f"learned_{s_eq}"][1] if s_eq else None},
         "speedup_at_equal_psnr": round(fps_eq / fps_plain, 3) if fps_eq else None,
-        "vs_tuned_distance_lod": {"fps": round(fps_plain_t, 2), "psnr_db": res["plain_tuned"]["psnr"],
-                                  "splats": res["plain_tuned"]["splats"], "learned_budget_scale": s_eq_t,
+        "learned_lod_same_budget": {"fps": round(fps_same, 2), "psnr_db": rd(res["learned_1.0"][0]),
+                                    "splats": res["learned_1.0"][1], "scale_mult_exponent": e_learn},
+        "vs_tuned_distance_lod": {"fps": round(fps_plain_t, 2), "psnr_db": rd(res["plain_tuned"][0]),
+                                  "splats": res["plain_tuned"][1], "tuned_exponent": e_plain,
+                                  "learned_budget_scale": s_eq_t,
                                   "learned_fps": round(fps_eq_t, 2) if fps_eq_t else None,
                                   "speedup": round(fps_eq_t / fps_plain_t, 3) if fps_eq_t else None},
-        "direct_contribution_ranking_psnr_db": res["direct"]["psnr"],
-        "learned_psnr_by_budget": {str(s_): res[f"learned_{s_}"]["psnr"] for s_ in scales},
-        "learned_splats_by_budget": {str(s_): res[f"learned_{s_}"]["splats"] for s_ in scales},
+        "learned_psnr_by_budget": {str(s_): rd(res[f"learned_{s_}"][0]) for s_ in scales},
+        "learned_splats_by_budget": {str(s_): res[f"learned_{s_}"][1] for s_ in scales},
         "full_detail": {"fps": round(fps_full, 2), "splats": full_splats},
         "training": {"instance_views": 3 * views * 100, "rows": int(targets.numel()), "steps": args.lod_steps,
                      "loss": [(int(a), round(b, 4)) for a, b in hist], "spearman_by_band": rho,
-                     "collect_s": round(t_collect, 2), "train_s": round(t_train, 2)},
-        "tuning_psnr_db": {k: round(v, 3) for k, v in tune.items()},
+                     "collect_s": round(t_collect, 2), "train_s": round(t_train, 2),
+                     "cost_s": round(t_collect + t_train, 2)},
+        "tuning_psnr_db": {k: rd(v[0]) for k, v in tune.items()},
+        "wall_s": round(time.time() - t_all, 1),
     }
+    if "direct" in res:
+        line["direct_contribution_ranking_psnr_db"] = rd(res["direct"][0])
+    return line
+
+
+def learned_lod_summary(d):
+    """The part of the learned-LoD comparison the default bench line carries."""
+    keys = ("config", "distance_lod", "learned_lod_equal_psnr", "speedup_at_equal_psnr",
+            "learned_lod_same_budget", "vs_tuned_distance_lod", "full_detail", "wall_s")
+    out = {k: d[k] for k in keys}
+    out["training_cost_s"] = d["training"]["cost_s"]
+    out["training"] = {k: d["training"][k] for k in ("instance_views", "rows", "steps", "spearman_by_band",
+                                                     "collect_s", "train_s")}
+    return out
+
+
+def run_learned_lod(args):
+    line = learned_lod_eval(args, reduced=False)
     print(json.dumps(line), flush=True)
     return line
 
@@ -673,6 +769,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--oracle-stride", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-s", type=float, default=12.0,
+                    help="seconds of oracle samples for cpu_baseline (at least 3 samples)")
+    ap.add_argument("--no-learned-lod", action="store_true",
+                    help="skip the learned-vs-distance LoD comparison of the default run")
     ap.add_argument("--small", action="store_true", help="small crowd (debugging)")
     ap.add_argument("--sweep", action="store_true",
                     help="paper Table 1/2 sweep at 1280x720 (one JSON line per cell)")

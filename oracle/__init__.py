@@ -343,5 +343,58 @@ def tile_lists(os_: OracleScene, tile: int = 16) -> dict:
     return out
 
 
+def tile_lists_window(os_: OracleScene, tx0: int, ty0: int, ntx: int, nty: int, tile: int = 16,
+                      instances=None) -> tuple[dict, dict]:
+    """``tile_lists`` restricted to the tiles [tx0, tx0 + ntx) x [ty0, ty0 + nty)
+    (same membership rule and order: a splat belongs to every tile holding a
+    pixel centre of its support box clipped to the image; each list ordered
+    by view depth, then instance, then Gaussian), computed with array
+    operations over the given instances (default: all).  Returns (lists,
+    info): lists as in ``tile_lists``; info maps every listed key to its
+    projection (u, v, radius, r_exact, A, B, C, opacity, depth)."""
+    W, H = os_.width, os_.height
+    tw = (W + tile - 1) // tile
+    insts = range(int(os_.template_id.shape[0])) if instances is None else instances
+    T_, K_, D_, info = [], [], [], {}
+    for inst in insts:
+        p = project_instance(os_, int(inst))
+        g = np.nonzero(p["valid"])[0]
+        if g.size == 0:
+            continue
+        u, v, r = p["uv"][g, 0], p["uv"][g, 1], p["radius"][g].astype(np.float64)
+        i0 = np.maximum(0, np.ceil(u - r - 0.5)).astype(np.int64)
+        i1 = np.minimum(W - 1, np.floor(u + r - 0.5)).astype(np.int64)
+        j0 = np.maximum(0, np.ceil(v - r - 0.5)).astype(np.int64)
+        j1 = np.minimum(H - 1, np.floor(v + r - 0.5)).astype(np.int64)
+        a0 = np.maximum(i0 // tile, tx0); a1 = np.minimum(i1 // tile, tx0 + ntx - 1)
+        b0 = np.maximum(j0 // tile, ty0); b1 = np.minimum(j1 // tile, ty0 + nty - 1)
+        keep = (i0 <= i1) & (j0 <= j1) & (a0 <= a1) & (b0 <= b1)
+        if not keep.any():
+            continue
+        g, a0, a1, b0, b1 = g[keep], a0[keep], a1[keep], b0[keep], b1[keep]
+        nx, ny = a1 - a0 + 1, b1 - b0 + 1
+        cnt = nx * ny
+        rep = np.repeat(np.arange(g.size), cnt)
+        k = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        tiles = (b0[rep] + k // nx[rep]) * tw + a0[rep] + k % nx[rep]
+        keys = (np.int64(inst) << 32) | g[rep].astype(np.int64)
+        T_.append(tiles)
+        K_.append(keys)
+        D_.append(p["depth"][g][rep])
+        for m, gg in enumerate(g.tolist()):
+            info[(int(inst) << 32) | gg] = (p["uv"][gg, 0], p["uv"][gg, 1], int(p["radius"][gg]), p["r_exact"][gg],
+                                            p["conic"][gg, 0], p["conic"][gg, 1], p["conic"][gg, 2],
+                                            p["opacity"][gg], p["depth"][gg])
+    out = {}
+    if T_:
+        tiles, keys, depth = np.concatenate(T_), np.concatenate(K_), np.concatenate(D_)
+        order = np.lexsort((keys, depth, tiles))
+        tiles, keys = tiles[order], keys[order]
+        bounds = np.nonzero(np.diff(tiles))[0] + 1
+        for seg_t, seg_k in zip(np.split(tiles, bounds), np.split(keys, bounds)):
+            out[int(seg_t[0])] = seg_k
+    return out, info
+
+
 def num_threads() -> int:
     return int(lib().orc_num_threads())

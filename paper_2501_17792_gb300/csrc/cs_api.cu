@@ -1335,6 +1335,9 @@ extern "C" {
 
 int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats) {
     if (!ctx) return CS_ERR_ARG;
+    // this call rewrites the context's skinning, visibility and group
+    // buffers that a training frame's backward reads: that frame is gone
+    ctx->train_valid = false;
     float4 *out = reinterpret_cast<float4 *>(rgba_out);
     if (!cam || !out) return fail(ctx, CS_ERR_ARG, "NULL camera or output");
     if (reinterpret_cast<uintptr_t>(out) & 15u) return fail(ctx, CS_ERR_ARG, "rgba_out must be 16-byte aligned");

@@ -66,7 +66,7 @@ def gpu_live(r, S):
     return live
 
 
-def compare_splats(r, sc, os_=None, max_instances=None):
+def compare_splats(r, sc, os_=None, max_instances=None, instances=None):
     """Per-splat errors of the GPU records against the oracle, over GPU
     splats whose instance the oracle also projects.  Returns a dict of
     maxima and the per-splat arrays used for the tile-list checks."""
@@ -79,6 +79,8 @@ def compare_splats(r, sc, os_=None, max_instances=None):
                live_mismatch=0, n=0, culled_unreachable=0)
     W, H = sc.camera.width, sc.camera.height
     insts = np.unique(inst)
+    if instances is not None:
+        insts = np.intersect1d(insts, np.asarray(list(instances), np.int64))
     if max_instances is not None:
         insts = insts[:max_instances]
     ref = {}
@@ -162,3 +164,94 @@ def tile_lists_gpu(r, inst, gau):
             s = vals[a:b]
             out[t] = (inst[s] << 32) | gau[s]
     return out
+
+
+def support_entries_per_row(os_, n_instances, W, H):
+    """Per image row, the oracle's (pixel, splat) support-box entries: the
+    widths of the clipped support boxes of every valid splat that covers the
+    row (memory planning of banded full-frame renders)."""
+    rows = np.zeros(H + 1, np.int64)
+    for i in range(n_instances):
+        p = oracle.project_instance(os_, i)
+        g = np.nonzero(p["valid"])[0]
+        if g.size == 0:
+            continue
+        u, v, r = p["uv"][g, 0], p["uv"][g, 1], p["radius"][g].astype(np.float64) + 1.0
+        x0 = np.maximum(0, np.ceil(u - r - 0.5)); x1 = np.minimum(W - 1, np.floor(u + r - 0.5))
+        y0 = np.maximum(0, np.ceil(v - r - 0.5)).astype(np.int64)
+        y1 = np.minimum(H - 1, np.floor(v + r - 0.5)).astype(np.int64)
+        ok = (x0 <= x1) & (y0 <= y1)
+        w = (x1 - x0 + 1)[ok].astype(np.int64)
+        np.add.at(rows, y0[ok], w)
+        np.add.at(rows, y1[ok] + 1, -w)
+    return np.cumsum(rows)[:H]
+
+
+def render_banded(os_, eps, entries_per_row, budget=12_000_000):
+    """oracle.render of the whole image in bands of rows, each holding at
+    most about `budget` support-box entries; a single row over the budget
+    is split into column ranges.  Stitched into one result."""
+    W, H = os_.width, os_.height
+    bands, y = [], 0
+    while y < H:
+        y1, acc = y, 0
+        while y1 < H and (y1 == y or acc + entries_per_row[y1] <= budget):
+            acc += int(entries_per_row[y1])
+            y1 += 1
+        parts = []
+        nc = max(1, -(-acc // budget)) if y1 == y + 1 else 1
+        for c in range(nc):
+            x0, x1 = W * c // nc, W * (c + 1) // nc
+            parts.append(oracle.render(os_, eps, lattice=(x0, y, 1, 1, x1 - x0, y1 - y)))
+        bands.append({k: np.concatenate([p[k] for p in parts], 1) for k in parts[0]})
+        y = y1
+    return {k: np.concatenate([b_[k] for b_ in bands], 0) for k in bands[0]}
+
+
+def compare_tile_lists(gl, ol, info, eps, W, H, tiles_x, tiles=None):
+    """GPU tile lists `gl` against the oracle's `ol` (both {tile: keys in
+    order}), over `tiles` (default: every tile of either).  A listed splat
+    whose support-box edge lies within eps.px of a pixel centre, or whose
+    3 sqrt(lambda) lies within eps.radius of an integer, is a boundary splat
+    (it may be on one side only).  Pairs only the oracle lists must be
+    unreachable (alpha < 1/255 over the tile's part of the box, FP64), and
+    the common pairs must be in the same order except inside runs of
+    near-equal depth.  Returns counts; asserts the rules."""
+    n_pairs = n_dropped = perms = n_boundary = 0
+    tiles = sorted(set(gl) | set(ol)) if tiles is None else tiles
+    for t in tiles:
+        G = gl.get(t, np.zeros(0, np.int64)).tolist()
+        O = ol.get(t, np.zeros(0, np.int64)).tolist()
+        n_pairs += len(G)
+        sG, sO = set(G), set(O)
+
+        def boundary(k):
+            u, v, rr, rex = info[k][:4]
+            e = np.array([u - rr - 0.5, u + rr - 0.5, v - rr - 0.5, v + rr - 0.5])
+            return bool((np.abs(e - np.round(e)) < eps.px).any() or abs(rex - round(rex)) < eps.radius)
+
+        extra = [k for k in sG - sO if not (k in info and boundary(k))]
+        assert not extra, (t, extra[:5])
+        missing = [k for k in sO - sG if not boundary(k)]
+        n_boundary += len(sO ^ sG) - len(missing)
+        if missing:
+            a = np.array([info[k] for k in missing], np.float64)
+            u, v, rr, A, B, C, o = a[:, 0], a[:, 1], a[:, 2], a[:, 4], a[:, 5], a[:, 6], a[:, 7]
+            tx, ty = t % tiles_x, t // tiles_x
+            x0 = np.maximum(tx * 16, np.maximum(0, np.ceil(u - rr - 0.5)))
+            x1 = np.minimum(tx * 16 + 15, np.minimum(W - 1, np.floor(u + rr - 0.5)))
+            y0 = np.maximum(ty * 16, np.maximum(0, np.ceil(v - rr - 0.5)))
+            y1 = np.minimum(ty * 16 + 15, np.minimum(H - 1, np.floor(v + rr - 0.5)))
+            f = rect_fmin(u, v, A, B, C, x0, x1, y0, y1)
+            cut = 2 * np.log(255.0 * o)
+            assert (f > cut - 2e-3).all(), (t, np.array(missing)[f <= cut - 2e-3][:5])
+            n_dropped += len(missing)
+        common = sG & sO
+        Gc = [k for k in G if k in common]
+        Oc = [k for k in O if k in common]
+        if Gc != Oc:
+            perms += 1
+            d = np.array([info[k][8] for k in Gc])
+            # the GPU order may differ only inside runs of near-equal depth
+            assert (np.diff(d) >= -eps.depth_rel * np.maximum(1.0, d[1:]) * 4).all(), t
+    return dict(pairs=n_pairs, dropped_unreachable=n_dropped, boundary_pairs=n_boundary, tiles_with_tie_perms=perms)

@@ -803,3 +803,18 @@ def test_direct_covariance_matches_scales_and_rotation():
     d = oracle.render(oracle.OracleScene(U.scene_of([t4], U.instances(1, root, pose), cam, lod)))["rgba"]
     assert c[..., 3].max() > 0.3
     assert np.abs(c - d).max() < 1e-14
+
+
+def test_windowed_tile_lists_equal_the_full_lists_on_the_window():
+    """The array-operation form restricted to a tile window returns exactly
+    the lists of the plain per-splat loop for those tiles."""
+    sc = U.random_small_scene(21, n_gauss=120, n_inst=3, size=72, sh_degree=0)
+    os_ = oracle.OracleScene(sc)
+    full = oracle.tile_lists(os_, tile=16)
+    tw = (72 + 15) // 16
+    lists, info = oracle.tile_lists_window(os_, 1, 1, 3, 2)
+    want = {t: k for t, k in full.items() if 1 <= t % tw < 4 and 1 <= t // tw < 3}
+    assert set(lists) == set(want) and len(want) > 2
+    for t in want:
+        assert np.array_equal(lists[t], want[t])
+    assert all(k in info for ks in lists.values() for k in ks.tolist())

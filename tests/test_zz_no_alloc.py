@@ -73,3 +73,98 @@ def test_render_static_rejects_frames_over_its_limit():
     assert rc == binding.CS_ERR_CAPACITY
     assert b"static limit" in L.cs_last_error(r.h)
     r.close()
+
+
+def _layered_scene(seed=11, n=24000, size=16, f=30.0):
+    """Three templates of small faint Gaussians in front of an identity
+    camera, one instance of each at root depths 0, 0.6 and 1.2 m.  LoD bands
+    at 0.3 and 0.9 m give the instances levels 0, 1 and 2 (fractions 1, 0.5
+    and 0.25, scale multipliers f^-1/2), so the frame has 42,000 splats in
+    three (template, level) groups.  The 16x16 image is a single tile whose
+    list holds every splat: more than the 32,768 pairs the first compositing
+    pass takes, so the remaining chunks, their merge and the fix-ups of the
+    pixels that saturate inside a chunk all run from the static array."""
+    from paper_2501_17792_gb300 import scene as S
+    from tests import scene_util as U
+    rng = np.random.default_rng(seed)
+    tpls = []
+    for _ in range(3):
+        z = rng.uniform(2.0, 5.0, n)
+        px, py = rng.uniform(0, size, n), rng.uniform(0, size, n)
+        means = np.stack([(px - size / 2) * z / f, (py - size / 2) * z / f, z], 1)
+        scales = (0.8 * z / f)[:, None] * np.exp(rng.normal(0, 0.3, (n, 3)))
+        tpls.append(U.template_from(means, scales, rng.standard_normal((n, 4)), rng.uniform(0.006, 0.016, n),
+                                    0.3 * rng.standard_normal((n, 4, 3))))
+    roots = np.tile(np.eye(3, 4, dtype=np.float32), (3, 1, 1))
+    roots[:, 2, 3] = [0.0, 0.6, 1.2]
+    fr = np.array([1.0, 0.5, 0.25], np.float32)
+    lod = S.LodConfig(thresholds=np.array([0.3, 0.9], np.float32), fractions=fr,
+                      scale_mult=(fr ** -0.5).astype(np.float32))
+    return U.scene_of(tpls, U.instances(3, roots, template_id=[0, 1, 2]), U.identity_camera(size, size, f), lod)
+
+
+def test_render_static_long_list_three_levels_against_oracle():
+    import oracle
+    from paper_2501_17792_gb300 import binding
+    from tests import parity_util as PU
+    oracle.build()
+    sc = _layered_scene()
+    r = binding.Renderer(device=0)
+    r.upload_templates(sc.templates)
+    r.set_lod(sc.lod)
+    r.set_instances(sc.instances.template_id, sc.instances.root, sc.instances.pose)
+    ref_gpu, st_ref = r.render(sc.camera, stats=True)
+    ref_gpu = ref_gpu.cpu().numpy()
+    assert st_ref["instances_per_level"][:3] == [1, 1, 1] and st_ref["splats"] == 42000
+    counts = np.diff(r.debug("tile_ranges").astype(np.int64), axis=1)
+    assert counts.max() > 32768  # the list continues past the first pass
+    # per-splat errors of this frame give the oracle's boundary windows
+    os_ = oracle.OracleScene(sc)
+    errs = PU.compare_splats(r, sc, os_)
+    ref = oracle.render(os_, PU.eps_from(errs))
+    L = binding.load()
+    cam = binding.camera_struct(sc.camera)
+    out = torch.empty((sc.camera.height, sc.camera.width, 4), dtype=torch.float32, device="cuda")
+    for _ in range(2):  # the second call starts from the first call's array contents
+        out.fill_(float("nan"))
+        torch.cuda.synchronize()
+        st = binding.FrameStats()
+        rc = L.cs_render_static(r.h, C.byref(cam), C.c_void_p(out.data_ptr()), C.byref(st))
+        assert rc == binding.CS_OK, L.cs_last_error(r.h).decode()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert st.splats == 42000 and st.pairs == st_ref["pairs"]
+        assert np.abs(got - ref_gpu).max() <= TOL
+        rep = PU.compare_images(got, ref)
+        print(f"\n[static long list] pairs={st.pairs} max_abs={rep['max_abs']:.2e} psnr={rep['psnr']:.1f} "
+              f"boundary={rep['boundary_px']} vs cs_render {np.abs(got - ref_gpu).max():.1e}")
+        assert rep["max_abs"] <= PU.TOL_MAX_ABS and rep["psnr"] >= PU.TOL_PSNR_DB
+        assert rep["boundary_frac"] <= 0.2
+    A = ref["rgba"][..., 3]
+    assert (A > 0.9998).mean() > 0.2  # pixels saturate inside the list's later chunks
+    r.close()
+
+
+def test_render_static_ends_a_training_frame():
+    """The static call rewrites the context's per-frame instance buffers, so
+    a training frame rendered before it can no longer be differentiated."""
+    from paper_2501_17792_gb300 import binding
+    from paper_2501_17792_gb300 import scene as S
+    sc = S.single_avatar(n_gauss=2048, size=64)
+    r = binding.Renderer(device=0)
+    r.upload_templates(sc.templates)
+    r.set_instances(sc.instances.template_id, sc.instances.root, sc.instances.pose)
+    r.render_train(sc.camera)
+    dl = torch.ones((64, 64, 4), dtype=torch.float32, device="cuda")
+    r.backward(dl, 1)  # valid right after the training frame
+    r.render_train(sc.camera)
+    L = binding.load()
+    cam = binding.camera_struct(sc.camera)
+    out = torch.empty((64, 64, 4), dtype=torch.float32, device="cuda")
+    assert L.cs_render_static(r.h, C.byref(cam), C.c_void_p(out.data_ptr()), None) == binding.CS_OK
+    with pytest.raises(binding.CrowdSplatError) as e:
+        r.backward(dl, 1)
+    assert e.value.code == binding.CS_ERR_STATE
+    torch.cuda.synchronize()
+    r.close()
