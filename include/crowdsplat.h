@@ -244,8 +244,10 @@ int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_fr
 int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats);
 
 /* Per-stage milliseconds (needs stage_timing = 1), measured with CUDA events
- * on the context's stream: ms[0..n) = fk, cull+lod, skin+project, depth
- * sort, pair emit, tile sort, tile ranges, blend.  average = 0: the last
+ * on the context's stream: ms[0..n) = fk, cull+lod (with the host read of
+ * the frame's splat count), skin+project, depth sort, pair emit (with the
+ * host read of the pair count), tile sort, tile ranges, blend.  average = 0:
+ * the last
  * frame (waits for it); average = 1: the mean over every frame rendered
  * since the previous average call (waits for the last one), then restarts
  * the mean.  *frames_out (may be NULL) receives the number of frames
@@ -274,11 +276,22 @@ const char *cs_last_error(const cs_ctx *ctx);
                                 depth minus those of the frame's lower depth bound
                                 (from the instance cull), 0xFFFFFFFF = culled      */
 #define CS_DBG_RECTS 6       /* uint16 [S][4]: tile rect x0, y0, x1, y1 (inclusive)    */
-#define CS_DBG_DEPTH_ORDER 7 /* uint32 [S]: splat ids sorted by depth                  */
-#define CS_DBG_PAIR_TILES 8  /* uint16 [P]: tile of each pair, (tile, depth) order     */
-#define CS_DBG_PAIR_SPLATS 9 /* uint32 [P]: splat of each pair, (tile, depth) order    */
+#define CS_DBG_DEPTH_ORDER 7 /* uint32 [S]: splat ids sorted by (depth key, id)        */
+#define CS_DBG_PAIR_TILES 8  /* uint16 [P]: tile of each pair, (tile, depth, splat id)
+                                order                                              */
+#define CS_DBG_PAIR_SPLATS 9 /* uint32 [P]: splat of each pair, same order          */
 #define CS_DBG_TILE_RANGES 10 /* uint32 [T][2]: [start, end) of each tile's pairs      */
 int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size_t *size_out);
+
+/* Testing hook for the out-of-memory paths: after `after` more successful
+ * allocations of frame or instance buffers, every such allocation of the
+ * context fails with CS_ERR_OOM, exactly as a failed cudaMalloc would (the
+ * buffer being grown is released first), until the hook is called again
+ * with after < 0 (off, the default).  The failure is made on the host; no
+ * GPU call fails.  The context stays usable: once the hook is off, the next
+ * call allocates again.  The paper has no counterpart.  Returns CS_OK, or
+ * CS_ERR_ARG for a NULL context. */
+int cs_debug_fail_allocs(cs_ctx *ctx, int32_t after);
 
 /* Library version string. */
 const char *cs_version(void);

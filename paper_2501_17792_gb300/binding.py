@@ -90,6 +90,7 @@ SIGNATURES = {
     "cs_memory_stats": (C.c_int, [_P, C.POINTER(MemoryStats)]),
     "cs_last_error": (C.c_char_p, [_P]),
     "cs_debug_read": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "cs_debug_fail_allocs": (C.c_int, [_P, C.c_int32]),
     "cs_version": (C.c_char_p, []),
     # ranked LoD (include/crowdsplat_lod.h)
     "cs_lod_features": (C.c_int, [_P, _P]),

@@ -37,6 +37,9 @@ struct DevBuf {
 struct cs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    // allocation-failure injection (cs_debug_fail_allocs): -1 off, else the
+    // number of allocations that still succeed before every one fails
+    int fail_after = -1;
     int skin_mode = 0, sh_frame = 0, instance_cull = 1, stage_timing = 0;
     int storage = CS_STORE_FP32;  // template storage precision
     std::string err;
@@ -148,12 +151,14 @@ int ensure(cs_ctx *ctx, DevBuf<T> &b, size_t n, const char *what) {
         b.p = nullptr;
         b.cap = 0;
     }
-    cudaError_t e = cudaMalloc(&b.p, cap * sizeof(T));
+    const bool injected = ctx->fail_after == 0;
+    if (ctx->fail_after > 0) --ctx->fail_after;
+    cudaError_t e = injected ? cudaErrorMemoryAllocation : cudaMalloc(&b.p, cap * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
-        return fail(ctx, CS_ERR_OOM, "allocating %s (%zu bytes): %s", what, cap * sizeof(T),
-                    cudaGetErrorString(e));
+        return fail(ctx, CS_ERR_OOM, "allocating %s (%zu bytes): %s%s", what, cap * sizeof(T),
+                    cudaGetErrorString(e), injected ? " (injected failure)" : "");
     }
     b.cap = cap;
     return CS_OK;
@@ -1209,6 +1214,12 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
     out->instance_bytes = ib;
     out->frame_bytes = fb;
     out->total_bytes = tb + ib + fb;
+    return CS_OK;
+}
+
+int cs_debug_fail_allocs(cs_ctx *ctx, int32_t after) {
+    if (!ctx) return CS_ERR_ARG;
+    ctx->fail_after = after < 0 ? -1 : after;
     return CS_OK;
 }
 

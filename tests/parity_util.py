@@ -147,6 +147,8 @@ def compare_images(got, ref):
     mse = float(np.mean(d ** 2))
     rep = dict(max_abs=float(d[ok].max()) if ok.any() else 0.0,
                max_abs_all=float(d.max()),
+               # pixels (boundary or not) off by more than the per-pixel bound
+               over_tol_frac=float((d.max(-1) > TOL_MAX_ABS).mean()),
                psnr=float(10 * np.log10(1.0 / max(mse, 1e-30))),
                boundary_px=int(boundary.sum()), boundary_frac=float(boundary.mean()),
                covered_frac=float((ref["rgba"][..., 3] > 0).mean()),
