@@ -568,26 +568,52 @@ def learned_lod_eval(args, reduced=False):
         if subs is not None:
             LOD.apply_subsets(r, subs)
 
+    r2 = None  # a second renderer holding templates stored in learned order
+
+    def prefix_renderer(fr):
+        """r2 with every template re-uploaded in the nested learned order for
+        level fractions fr, so each level renders a prefix (no gather)."""
+        nonlocal r2
+        if r2 is None:
+            r2 = binding.Renderer(device=0)
+        orders = LOD.prefix_orders(scores, fr, sizes)
+        r2.upload_templates([LOD.permute_template(tp, o) for tp, o in zip(tpls, orders)])
+        return r2
+
+    def prepare(cfg):
+        """Renderer of a config (name, lod, subsets, prefix-order fractions)."""
+        name, lod, subs, pfr = cfg
+        rr = prefix_renderer(pfr) if pfr is not None else r
+        if pfr is None:
+            LOD.clear_subsets(rr, n_tpl)
+        rr.set_lod(lod)
+        if subs is not None:
+            LOD.apply_subsets(rr, subs)
+        return rr
+
     def mean_psnr(inst, pose_list, configs):
         """{name: (mean PSNR vs full detail over the frames, splats of frame 0)}."""
         tid = torch.from_numpy(inst.template_id).cuda()
         root = torch.from_numpy(inst.root.reshape(-1, 12)).cuda()
-        acc = {name: [] for name, _, _ in configs}
-        splats = {}
-        ref = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
-        img = torch.empty_like(ref)
-        for k, pose in enumerate(pose_list):
-            apply(S.single_lod(), None)
+        refs = []
+        apply(S.single_lod(), None)
+        for pose in pose_list:
             r.set_instances(tid, root, pose)
-            _, st = r.render(cam, out=ref, stats=True)
-            splats.setdefault("full", st["splats"])
-            for name, lod, subs in configs:
-                apply(lod, subs)
-                r.set_instances(tid, root, pose)
-                _, st = r.render(cam, out=img, stats=True)
-                acc[name].append(LOD.psnr(img, ref))
-                splats.setdefault(name, st["splats"])
-        return {k: (float(np.mean(v)), int(splats[k])) for k, v in acc.items()}, int(splats["full"])
+            img, st = r.render(cam, stats=True)
+            refs.append(img)
+        res = {}
+        img = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        for cfg in configs:
+            rr = prepare(cfg)
+            ps, spl = [], None
+            for pose, ref in zip(pose_list, refs):
+                rr.set_instances(tid, root, pose)
+                _, st2 = rr.render(cam, out=img, stats=True)
+                ps.append(LOD.psnr(img, ref))
+                spl = st2["splats"] if spl is None else spl
+            res[cfg[0]] = (float(np.mean(ps)), int(spl))
+        del refs
+        return res, int(st["splats"])
 
     # 3. scale-multiplier exponent, tuned on a training crowd (other layout
     # and poses) for both methods
@@ -596,8 +622,8 @@ def learned_lod_eval(args, reduced=False):
     cfgs = []
     for e in expos:
         lod, fr = lod_cfg(1.0, e)
-        cfgs.append((f"plain_{e}", lod, None))
-        cfgs.append((f"learned_{e}", lod, LOD.ranked_subsets(r, scores, fr, sizes, levels=(1, 2))))
+        cfgs.append((f"plain_{e}", lod, None, None))
+        cfgs.append((f"learned_{e}", lod, LOD.ranked_subsets(r, scores, fr, sizes, levels=(1, 2)), None))
     tune, _ = mean_psnr(tr_inst, [torch.from_numpy(tr_inst.pose).cuda()], cfgs)
     e_plain = max(expos, key=lambda e: tune[f"plain_{e}"][0])
     e_learn = max(expos, key=lambda e: tune[f"learned_{e}"][0])
@@ -612,36 +638,44 @@ def learned_lod_eval(args, reduced=False):
     lod_plain_t, _ = lod_cfg(1.0, e_plain)
     scales = ((1.0, 0.5, 0.25, 0.18, 0.12, 0.08, 0.05, 0.03) if reduced else
               (1.0, 0.7, 0.5, 0.35, 0.25, 0.18, 0.12, 0.08, 0.05, 0.03, 0.02))
-    cfgs = [("plain", lod_plain, None), ("plain_tuned", lod_plain_t, None)]
-    learned_subs = {}
+    cfgs = [("plain", lod_plain, None, None), ("plain_tuned", lod_plain_t, None, None)]
+    learned = {}
     for s_ in scales:
         lod, fr = lod_cfg(s_, e_learn)
-        learned_subs[s_] = (lod, LOD.ranked_subsets(r, scores, fr, sizes, levels=(1, 2)))
-        cfgs.append((f"learned_{s_}", lod, learned_subs[s_][1]))
+        learned[s_] = (f"learned_{s_}", lod, LOD.ranked_subsets(r, scores, fr, sizes, levels=(1, 2)), None)
+        cfgs.append(learned[s_])
+    # the same ranking with nested levels stored as template prefixes
+    prefix = {s_: (f"prefix_{s_}", lod_cfg(s_, e_learn)[0], None, lod_cfg(s_, e_learn)[1]) for s_ in scales}
+    cfgs.extend(prefix.values())
     if not reduced:
         cfgs.append(("direct", lod_cfg(1.0, e_learn)[0],
-                     LOD.ranked_subsets(r, contrib, lod_cfg(1.0)[1], sizes, levels=(1, 2))))
+                     LOD.ranked_subsets(r, contrib, lod_cfg(1.0)[1], sizes, levels=(1, 2)), None))
     res, full_splats = mean_psnr(inst, poses[:frames], cfgs)
 
-    def equal_budget(target_psnr):
-        eq = [s_ for s_ in scales if res[f"learned_{s_}"][0] >= target_psnr]
+    def equal_budget(kind, target_psnr):
+        eq = [s_ for s_ in scales if res[f"{kind}_{s_}"][0] >= target_psnr]
         return min(eq) if eq else None
 
-    s_eq = equal_budget(res["plain"][0])
-    s_eq_t = equal_budget(res["plain_tuned"][0])
+    s_eq = equal_budget("learned", res["plain"][0])
+    s_eq_t = equal_budget("learned", res["plain_tuned"][0])
+    p_eq = equal_budget("prefix", res["plain"][0])
     out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
 
-    def fps_of(lod, subs):
-        apply(lod, subs)
-        return _fps(r, cam, tid, root, poses, out, args.warmup, args.steps)
+    def fps_of(cfg):
+        rr = prepare(cfg)
+        return _fps(rr, cam, tid, root, poses, out, args.warmup, args.steps)
 
-    fps_full = fps_of(S.single_lod(), None)
-    fps_plain = fps_of(lod_plain, None)
-    fps_plain_t = fps_of(lod_plain_t, None)
-    fps_same = fps_of(*learned_subs[1.0])
-    fps_eq = fps_of(*learned_subs[s_eq]) if s_eq is not None else None
-    fps_eq_t = fps_of(*learned_subs[s_eq_t]) if s_eq_t is not None else None
+    fps_full = fps_of(("full", S.single_lod(), None, None))
+    fps_plain = fps_of(cfgs[0])
+    fps_plain_t = fps_of(cfgs[1])
+    fps_same = fps_of(learned[1.0])
+    fps_eq = fps_of(learned[s_eq]) if s_eq is not None else None
+    fps_eq_t = fps_of(learned[s_eq_t]) if s_eq_t is not None else None
+    fps_pre_same = fps_of(prefix[1.0])
+    fps_pre_eq = fps_of(prefix[p_eq]) if p_eq is not None else None
     r.close()
+    if r2 is not None:
+        r2.close()
     mlp.close()
     rd = lambda x: round(x, 3)  # noqa: E731
     line = {
@@ -659,6 +693,13 @@ def learned_lod_eval(args, reduced=False):
                                    "psnr_db": rd(res[f"learned_{s_eq}"][0]) if s_eq else None,
                                    "splats": res[f"learned_{s_eq}"][1] if s_eq else None},
         "speedup_at_equal_psnr": round(fps_eq / fps_plain, 3) if fps_eq else None,
+        "learned_prefix_equal_psnr": {"budget_scale": p_eq, "fps": round(fps_pre_eq, 2) if fps_pre_eq else None,
+                                      "psnr_db": rd(res[f"prefix_{p_eq}"][0]) if p_eq else None,
+                                      "splats": res[f"prefix_{p_eq}"][1] if p_eq else None,
+                                      "speedup": round(fps_pre_eq / fps_plain, 3) if fps_pre_eq else None,
+                                      "same_budget_fps": round(fps_pre_same, 2),
+                                      "same_budget_psnr_db": rd(res["prefix_1.0"][0]),
+                                      "note": "levels nested and re-uploaded as template prefixes (no gather)"},
         "learned_lod_same_budget": {"fps": round(fps_same, 2), "psnr_db": rd(res["learned_1.0"][0]),
                                     "splats": res["learned_1.0"][1], "scale_mult_exponent": e_learn},
         "vs_tuned_distance_lod": {"fps": round(fps_plain_t, 2), "psnr_db": rd(res["plain_tuned"][0]),
@@ -667,6 +708,7 @@ def learned_lod_eval(args, reduced=False):
                                   "learned_fps": round(fps_eq_t, 2) if fps_eq_t else None,
                                   "speedup": round(fps_eq_t / fps_plain_t, 3) if fps_eq_t else None},
         "learned_psnr_by_budget": {str(s_): rd(res[f"learned_{s_}"][0]) for s_ in scales},
+        "prefix_psnr_by_budget": {str(s_): rd(res[f"prefix_{s_}"][0]) for s_ in scales},
         "learned_splats_by_budget": {str(s_): res[f"learned_{s_}"][1] for s_ in scales},
         "full_detail": {"fps": round(fps_full, 2), "splats": full_splats},
         "training": {"instance_views": 3 * views * 100, "rows": int(targets.numel()), "steps": args.lod_steps,
@@ -683,7 +725,7 @@ def learned_lod_eval(args, reduced=False):
 
 def learned_lod_summary(d):
     """The part of the learned-LoD comparison the default bench line carries."""
-    keys = ("config", "distance_lod", "learned_lod_equal_psnr", "speedup_at_equal_psnr",
+    keys = ("config", "distance_lod", "learned_lod_equal_psnr", "speedup_at_equal_psnr", "learned_prefix_equal_psnr",
             "learned_lod_same_budget", "vs_tuned_distance_lod", "full_detail", "wall_s")
     out = {k: d[k] for k in keys}
     out["training_cost_s"] = d["training"]["cost_s"]

@@ -108,13 +108,26 @@ typedef struct {
 } cs_template_desc;
 
 /* Pinhole camera: x_cam = R x_world + t; u = fx x/z + cx, v = fy y/z + cy.
- * Splats with view depth z <= near_z are culled. */
+ * Splats with view depth z <= near_z are culled.
+ * Window: the output holds pixels [win_x0, win_x0 + width) x [win_y0,
+ * win_y0 + height) of a full image of full_width x full_height pixels
+ * (full_width = full_height = 0: no window, the full image is width x
+ * height and win_x0 = win_y0 = 0).  fx, fy, cx, cy are the full image's;
+ * the EWA clamp follows the full image's field of view and pixel centres
+ * stay at their full-image positions, so a window renders bit for bit the
+ * same pixels as the full frame.  The window's edges must lie on the full
+ * image's tile grid (multiples of CS_TILE) or on the full image's right and
+ * bottom edges, so every tile it holds has the full frame's list, and the
+ * window must lie inside the full image (CS_ERR_ARG otherwise).  Splitting a frame into row windows this way lets ranks
+ * render disjoint parts of one frame. */
 typedef struct {
     float R[9];
     float t[3];
     float fx, fy, cx, cy;
     int32_t width, height;
     float near_z;
+    int32_t win_x0, win_y0;
+    int32_t full_width, full_height;
 } cs_camera;
 
 typedef struct {
@@ -235,8 +248,10 @@ int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_fr
  * and a message naming the limit, leaving rgba_out unwritten.  The
  * instance buffers come from cs_set_instances, which allocates as usual.
  * The first call on a device looks the array's device address up (CUDA may
- * load the library's device code then): make that first call before any
- * stream capture.  All contexts of the process share the array and it
+ * load the library's device code then) and keeps it for the process: make
+ * that first call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) while the library is loaded, since the kept address
+ * would then be stale.  All contexts of the process share the array and it
  * keeps the previous call's contents, so calls that overlap on the GPU
  * (other streams, other contexts on the same device) race; serialise them.
  * No stage times are recorded, and cs_debug_read is unspecified after this

@@ -44,7 +44,8 @@ class TemplateDesc(C.Structure):
 class Camera(C.Structure):
     _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
                 ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
-                ("near_z", C.c_float)]
+                ("near_z", C.c_float), ("win_x0", C.c_int32), ("win_y0", C.c_int32),
+                ("full_width", C.c_int32), ("full_height", C.c_int32)]
 
 
 class FrameStats(C.Structure):
@@ -150,6 +151,8 @@ def camera_struct(cam) -> Camera:
     c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
     c.width, c.height = int(cam.width), int(cam.height)
     c.near_z = float(getattr(cam, "near", 0.2))
+    c.win_x0, c.win_y0 = int(getattr(cam, "win_x0", 0)), int(getattr(cam, "win_y0", 0))
+    c.full_width, c.full_height = int(getattr(cam, "full_width", 0)), int(getattr(cam, "full_height", 0))
     return c
 
 

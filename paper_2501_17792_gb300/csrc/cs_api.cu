@@ -97,7 +97,7 @@ struct cs_ctx {
 
     // last frame
     int64_t S = 0, P = 0;
-    int n_groups = 0, visible = 0, tiles_x = 0, tiles_y = 0, frame_w = 0, frame_h = 0;
+    int n_groups = 0, visible = 0, tiles_x = 0, tiles_y = 0, frame_w = 0, frame_h = 0, frame_ox = 0, frame_oy = 0;
     int order_buf = 0, pair_buf = 0;  // which ping-pong half holds the result
     int per_level[kMaxLevels] = {0, 0, 0, 0};
     int launches = 0;  // kernels launched by the last cs_render
@@ -285,6 +285,24 @@ int push_templates(cs_ctx *ctx) {
     return CS_OK;
 }
 
+// Full-image size of a camera (its own size when it has no window).
+void full_size(const cs_camera *cam, int &fw, int &fh) {
+    const bool win = cam->full_width != 0 || cam->full_height != 0;
+    fw = win ? cam->full_width : cam->width;
+    fh = win ? cam->full_height : cam->height;
+}
+
+// Window fields of a camera: origin on the tile grid, inside the full image.
+bool window_ok(const cs_camera *cam) {
+    int fw, fh;
+    full_size(cam, fw, fh);
+    if (cam->full_width == 0 && cam->full_height == 0) return cam->win_x0 == 0 && cam->win_y0 == 0;
+    const int x1 = cam->win_x0 + cam->width, y1 = cam->win_y0 + cam->height;
+    return fw >= 1 && fh >= 1 && fw <= CS_MAX_IMAGE_SIDE && fh <= CS_MAX_IMAGE_SIDE && cam->win_x0 >= 0 &&
+           cam->win_y0 >= 0 && cam->win_x0 % kTile == 0 && cam->win_y0 % kTile == 0 && x1 <= fw && y1 <= fh &&
+           (x1 % kTile == 0 || x1 == fw) && (y1 % kTile == 0 || y1 == fh);
+}
+
 void cam_params(const cs_ctx *c, const cs_camera *cam, CamParams &p) {
     for (int i = 0; i < 9; ++i) p.R[i] = cam->R[i];
     for (int i = 0; i < 3; ++i) p.t[i] = cam->t[i];
@@ -294,14 +312,19 @@ void cam_params(const cs_ctx *c, const cs_camera *cam, CamParams &p) {
     p.cy = cam->cy;
     p.W = cam->width;
     p.H = cam->height;
+    p.ox = cam->win_x0;
+    p.oy = cam->win_y0;
+    int fw, fh;
+    full_size(cam, fw, fh);
     p.near_z = cam->near_z;
     for (int i = 0; i < 3; ++i) {
         double s = 0.0;
         for (int k = 0; k < 3; ++k) s -= (double)cam->R[k * 3 + i] * (double)cam->t[k];
         p.center[i] = (float)s;
     }
-    p.limx = (float)(1.3 * (0.5 * cam->width) / (double)cam->fx);
-    p.limy = (float)(1.3 * (0.5 * cam->height) / (double)cam->fy);
+    // the EWA clamp follows the full image's field of view
+    p.limx = (float)(1.3 * (0.5 * fw) / (double)cam->fx);
+    p.limy = (float)(1.3 * (0.5 * fh) / (double)cam->fy);
     p.tiles_x = (cam->width + kTile - 1) / kTile;
     p.tiles_y = (cam->height + kTile - 1) / kTile;
     // Conservative instance cull.  A splat's support half-width is at most
@@ -316,10 +339,11 @@ void cam_params(const cs_ctx *c, const cs_camera *cam, CamParams &p) {
     // full-range depth keys until the cull has bounded the frame's depths
     p.key_lo = 0u;
     p.key_hi = 0xFFFFFFFEu;
-    const double tr = (cam->width - cam->cx + margin) / cam->fx;
-    const double tl = (cam->cx + margin) / cam->fx;
-    const double tb = (cam->height - cam->cy + margin) / cam->fy;
-    const double tt = (cam->cy + margin) / cam->fy;
+    // side planes of the rendered window
+    const double tr = (cam->win_x0 + cam->width - cam->cx + margin) / cam->fx;
+    const double tl = (cam->cx - cam->win_x0 + margin) / cam->fx;
+    const double tb = (cam->win_y0 + cam->height - cam->cy + margin) / cam->fy;
+    const double tt = (cam->cy - cam->win_y0 + margin) / cam->fy;
     const double planes[4][3] = {{1, 0, -tr}, {-1, 0, -tl}, {0, 1, -tb}, {0, -1, -tt}};
     for (int k = 0; k < 4; ++k) {
         double n = std::sqrt(planes[k][0] * planes[k][0] + planes[k][1] * planes[k][1] +
@@ -804,6 +828,10 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         return fail(ctx, CS_ERR_ARG, "image size %dx%d outside 1..%d", cam->width, cam->height, CS_MAX_IMAGE_SIDE);
     if (!(cam->fx > 0.f && cam->fy > 0.f && cam->near_z > 0.f) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
         return fail(ctx, CS_ERR_ARG, "focal lengths and near plane must be positive and finite");
+    if (!window_ok(cam))
+        return fail(ctx, CS_ERR_ARG, "window (%d, %d) + %dx%d of a %dx%d image: its edges must be on the %d-pixel "
+                    "tile grid (or the image edge) and the window inside the full image", cam->win_x0, cam->win_y0,
+                    cam->width, cam->height, cam->full_width, cam->full_height, kTile);
     for (int i = 0; i < 9; ++i)
         if (!std::isfinite(cam->R[i])) return fail(ctx, CS_ERR_ARG, "camera rotation not finite");
     for (int i = 0; i < 3; ++i)
@@ -818,6 +846,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     ctx->tiles_x = cp.tiles_x;
     ctx->frame_w = cam->width;
     ctx->frame_h = cam->height;
+    ctx->frame_ox = cp.ox;
+    ctx->frame_oy = cp.oy;
     ctx->tiles_y = cp.tiles_y;
     ctx->timed = false;
     int launched = 0;
@@ -940,6 +970,8 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
                  ctx->bw_meta.p, ctx->bw_stop.p, nullptr};
     bw.pp_tile = ctx->bw_pp.p;
     bw.chunk_slot = ctx->bw_cslot.p;
+    bw.ox = cp.ox;
+    bw.oy = cp.oy;
     if (contrib_tmpl) {
         CS_TRY(ensure(ctx, ctx->contrib_s, Sa, "splat contributions"));
         CS_CUDA(cudaMemsetAsync(ctx->contrib_s.p, 0, Sa * sizeof(float), st));
@@ -1052,6 +1084,8 @@ int cs_lod_rank(cs_ctx *ctx, const float *score, uint32_t *order_out) {
 
 int cs_render_train(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats) {
     if (!ctx) return CS_ERR_ARG;
+    if (cam && (cam->full_width != 0 || cam->full_height != 0))
+        return fail(ctx, CS_ERR_ARG, "training frames render the full image (no window)");
     if (ctx->storage != CS_STORE_FP32) return fail(ctx, CS_ERR_STATE, "gradients need FP32 template storage");
     return render_impl(ctx, cam, reinterpret_cast<float4 *>(rgba_out), stats, nullptr, true);
 }
@@ -1239,8 +1273,8 @@ int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size
             // recomputed from the records of the last frame
             if (ctx->S > 0) {
                 CS_TRY(ensure(ctx, ctx->rect, (size_t)ctx->S, "tile rects"));
-                launch_debug_rects((int)ctx->S, ctx->rec.p, ctx->bins.p, ctx->frame_w, ctx->frame_h, ctx->rect.p,
-                                   ctx->stream);
+                launch_debug_rects((int)ctx->S, ctx->rec.p, ctx->bins.p, ctx->frame_w, ctx->frame_h, ctx->frame_ox,
+                                   ctx->frame_oy, ctx->rect.p, ctx->stream);
                 CS_CUDA(cudaGetLastError());
             }
             src = ctx->rect.p;
@@ -1357,6 +1391,10 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
         return fail(ctx, CS_ERR_ARG, "image size %dx%d outside 1..%d", cam->width, cam->height, CS_MAX_IMAGE_SIDE);
     if (!(cam->fx > 0.f && cam->fy > 0.f && cam->near_z > 0.f) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
         return fail(ctx, CS_ERR_ARG, "focal lengths and near plane must be positive and finite");
+    if (!window_ok(cam))
+        return fail(ctx, CS_ERR_ARG, "window (%d, %d) + %dx%d of a %dx%d image: its edges must be on the %d-pixel "
+                    "tile grid (or the image edge) and the window inside the full image", cam->win_x0, cam->win_y0,
+                    cam->width, cam->height, cam->full_width, cam->full_height, kTile);
     for (int i = 0; i < 9; ++i)
         if (!std::isfinite(cam->R[i])) return fail(ctx, CS_ERR_ARG, "camera rotation not finite");
     for (int i = 0; i < 3; ++i)
@@ -1451,6 +1489,8 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
                  reinterpret_cast<int32_t *>(base + kOffBwMeta), reinterpret_cast<int32_t *>(base + kOffBwStop)};
     bw.pp_tile = reinterpret_cast<int32_t *>(base + kOffBwPp);
     bw.chunk_slot = reinterpret_cast<int32_t *>(base + kOffBwCslot);
+    bw.ox = cp.ox;
+    bw.oy = cp.oy;
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ranges, pval, rec, out, bw,
                              (uint32_t)P, st);
     CS_CUDA(cudaGetLastError());

@@ -185,7 +185,7 @@ struct TileGeom {
 
 // Pixel of the calling thread: warp w of the tile (w0 = the CTA's first)
 // covers the 8x4 block at column w % 2, row w / 2.
-__device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int H, int w0 = 0) {
+__device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int H, int ox, int oy, int w0 = 0) {
     TileGeom g;
     const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
     const int warp = w0 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -194,8 +194,8 @@ __device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int 
     g.px = g.tx0 + (warp & 1) * kBlockW + (lane & (kBlockW - 1));
     g.py = g.ty0 + (warp >> 1) * kBlockH + (lane / kBlockW);
     g.inside = g.px < W && g.py < H;
-    g.fpx = (float)g.px + 0.5f;
-    g.fpy = (float)g.py + 0.5f;
+    g.fpx = (float)(g.px + ox) + 0.5f;
+    g.fpy = (float)(g.py + oy) + 0.5f;
     return g;
 }
 
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
     constexpr int kParts = kBlendThreads / kT;
     const int tile = blockIdx.x / kParts, part = blockIdx.x % kParts;
     const int w0 = part * (kT / 32);  // first warp block of this CTA
-    const TileGeom g = tile_geom(tile, tiles_x, W, H, w0);
+    const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy, w0);
     const uint2 rg = ranges[tile];
     Pixel px{1.0f, 0.0f, 0.0f, 0.0f, rg.x, !g.inside, false};
     const uint32_t end1 = rg.y - rg.x > kBudget && kMode == 0 ? rg.x + kBudget : rg.y;
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
         const int bx0 = txi * kTile + (blk & 1) * kBlockW, by0 = tyi * kTile + (blk >> 1) * kBlockH;
         const int px = bx0 + (lane & (kBlockW - 1)), py = by0 + lane / kBlockW;
         const bool inside = px < W && py < H;
-        const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+        const float fpx = (float)(px + work.ox) + 0.5f, fpy = (float)(py + work.oy) + 0.5f;
         const uint2 rg = ranges[tile];
         const uint32_t end1 = rg.y - rg.x > kBudget ? rg.x + kBudget : rg.y;
         // the block's chained state (warp 0)
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_chunks(int tiles_x, int
     const int slot = work.chunk_slot[w];
     if (work.cand_done[slot]) return;
     const int tile = work.cand_tile[slot];
-    const TileGeom g = tile_geom(tile, tiles_x, W, H);
+    const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
     const uint2 rg = ranges[tile];
     const uint32_t c = w - work.cand_chunk0[slot];
     const uint32_t start = rg.x + kBudget + c * kChunk;
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_merge(int tiles_x, int 
     const int slot = blockIdx.x;
     if (slot >= work.meta[0] || work.cand_done[slot]) return;
     const int tile = work.cand_tile[slot];
-    const TileGeom g = tile_geom(tile, tiles_x, W, H);
+    const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
     const size_t pix = (size_t)slot * kBlendThreads + threadIdx.x;
     const float4 s1 = work.state[pix];
     float T = fabsf(s1.w), r = s1.x, gg = s1.y, b = s1.z;
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W,
     const bool mine = work.stop[pix] == (int32_t)w;
     if (__syncthreads_count(mine) == 0) return;
     const int tile = work.cand_tile[slot];
-    const TileGeom g = tile_geom(tile, tiles_x, W, H);
+    const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
     const uint2 rg = ranges[tile];
     const float4 sb = mine ? work.state[pix] : make_float4(0.f, 0.f, 0.f, 1.f);
     Pixel px{sb.w, sb.x, sb.y, sb.z, 0u, !mine, false};

@@ -484,16 +484,29 @@ __device__ void skin_blend_tc(const float4 *__restrict__ sB, const float w_in[4]
     for (int e = 0; e < 12; ++e) M[e] = sM[t * kTcMld + e] * iw;
 }
 
+// The FP32 path stages joint j's transform (12 floats) at word j * kSbwLd
+// of shared memory: 13 is odd, so the joints of a warp's 32 lanes fall in
+// distinct banks and every 4-byte load of the blend is conflict free (16-byte
+// loads of 3 rows per joint would put up to 9 joints in one bank group).
+constexpr int kSbwLd = 13;
+
+// Records of a 256-splat chunk staged in shared memory as four planes
+// (plane k holds float4 k of every splat; rows padded by two float4 so that
+// the transposing reads hit every bank group equally), then written out as
+// one contiguous block: each warp store covers 512 consecutive bytes instead
+// of one 16-byte piece of 32 different records.
+constexpr int kSrecLd = kProjThreads + 2;
+
 // Gaussians chunk * 256 + t of one visible instance (thread t), with the
 // instance's 24 skinning transforms staged in shared memory (sB).  Splat ids
 // are dense, grouped by (template, level), instance-major within a group.
 template <int kStore>
 __device__ __forceinline__ void project_chunk(
-    const ProjGroup &G, int islot, int chunk, int inst, const float4 *__restrict__ sB,
+    const ProjGroup &G, int islot, int chunk, int inst, const float4 *__restrict__ sB, const float *__restrict__ sBw,
     const float4 *__restrict__ sV, unsigned char *s_tc,
     const float *__restrict__ Vm, const float *__restrict__ root, const TemplateArrays &ta,
     const TemplateInfo *__restrict__ tpls, const CamParams &cam, const LodParams &lod, int skin_mode, int sh_frame, float4 *__restrict__ rec, uint32_t *__restrict__ key,
-    uint32_t *__restrict__ bin) {
+    uint32_t *__restrict__ bin, float4 *srec, uint8_t *slive) {
     const int gg = chunk * kProjThreads + threadIdx.x;
     const bool valid = gg < G.ng;
     // the tensor-core blend needs every thread of the CTA
@@ -530,11 +543,11 @@ __device__ __forceinline__ void project_chunk(
         for (int e = 0; e < 12; ++e) M[e] = 0.0f;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int j = (packed >> (8 * k)) & 0xFF;
-            const float4 b0 = sB[j * 3 + 0], b1 = sB[j * 3 + 1], b2 = sB[j * 3 + 2];
-            M[0] += wk[k] * b0.x; M[1] += wk[k] * b0.y; M[2] += wk[k] * b0.z; M[3] += wk[k] * b0.w;
-            M[4] += wk[k] * b1.x; M[5] += wk[k] * b1.y; M[6] += wk[k] * b1.z; M[7] += wk[k] * b1.w;
-            M[8] += wk[k] * b2.x; M[9] += wk[k] * b2.y; M[10] += wk[k] * b2.z; M[11] += wk[k] * b2.w;
+            // joint j's 12 entries at word j * kSbwLd: the 32 lanes of one
+            // load read 32 different banks (or the same word)
+            const float *b = sBw + ((packed >> (8 * k)) & 0xFF) * kSbwLd;
+#pragma unroll
+            for (int e = 0; e < 12; ++e) M[e] += wk[k] * b[e];
         }
         mo = __ldg(ta.mean_op + gi);
         // the covariance is loaded with the other attributes (one round of
@@ -632,8 +645,8 @@ __device__ __forceinline__ void project_chunk(
                 // pixel range where alpha can reach 1/255 (ellipse extent)
                 // inside the support box: both are centred on the mean, so
                 // their intersection is the box of the smaller half-width
-                box_range(u, fminf(ellipse_reach(fcut, a), r), cam.W, ax0, ax1);
-                box_range(v, fminf(ellipse_reach(fcut, c), r), cam.H, ay0, ay1);
+                box_range(u, fminf(ellipse_reach(fcut, a), r), cam.ox, cam.W, ax0, ax1);
+                box_range(v, fminf(ellipse_reach(fcut, c), r), cam.oy, cam.H, ay0, ay1);
                 // the tiles the reach box meets: a 3x3 window of them is kept
                 // as a mask (bin word), larger boxes as a count
                 if (ax0 <= ax1 && ay0 <= ay1) {
@@ -683,13 +696,27 @@ __device__ __forceinline__ void project_chunk(
                         default: sh_colour<3>(ta.sh, base, G.n, ddx, ddy, ddz, rgb); break;
                     }
                 }
-                float4 *ro = rec + (size_t)s * kRecVec;
-                ro[0] = make_float4(u, v, cA, cB);
-                ro[1] = make_float4(cC, mo.w, r, tz);
-                ro[2] = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
-                ro[3] = make_float4(__uint_as_float((uint32_t)ax0 | ((uint32_t)ax1 << 16)),
-                                    __uint_as_float((uint32_t)ay0 | ((uint32_t)ay1 << 16)), fcut,
-                                    __log2f(mo.w));
+                const float4 r0 = make_float4(u, v, cA, cB);
+                const float4 r1 = make_float4(cC, mo.w, r, tz);
+                const float4 r2 = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
+                const float4 r3 = make_float4(__uint_as_float((uint32_t)ax0 | ((uint32_t)ax1 << 16)),
+                                              __uint_as_float((uint32_t)ay0 | ((uint32_t)ay1 << 16)), fcut,
+                                              __log2f(mo.w));
+                if (srec) {
+                    // staged: the CTA writes the chunk's records out coalesced
+                    const int t = threadIdx.x;
+                    srec[0 * kSrecLd + t] = r0;
+                    srec[1 * kSrecLd + t] = r1;
+                    srec[2 * kSrecLd + t] = r2;
+                    srec[3 * kSrecLd + t] = r3;
+                    slive[t] = 1;
+                } else {
+                    float4 *ro = rec + (size_t)s * kRecVec;
+                    ro[0] = r0;
+                    ro[1] = r1;
+                    ro[2] = r2;
+                    ro[3] = r3;
+                }
             }
         }
     }
@@ -709,10 +736,13 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     CamParams cam, LodParams lod, int skin_mode, int sh_frame, float4 *__restrict__ rec,
     uint32_t *__restrict__ key, uint32_t *__restrict__ bin, const __grid_constant__ ProjGroups pg) {
     static_assert(kStore == kStoreFp32 || kChunks == 1, "the BF16 blend needs one chunk per CTA");
-    __shared__ float4 sB[kJoints * 3];  // skinning transforms (FP32 storage: V_R B_j)
+    __shared__ float4 sB[kStore == kStoreBf16 ? kJoints * 3 : 1];         // skinning transforms B_j (BF16 storage)
+    __shared__ float sBw[kStore == kStoreFp32 ? kJoints * kSbwLd : 1];   // V_R B_j (FP32 storage)
     __shared__ float4 sV[3];            // V = camera o root, rows
     __shared__ int s_group[kChunks];
     __shared__ __align__(16) unsigned char s_tc[kStore == kStoreBf16 ? kSkinTcBytes : 16];
+    __shared__ float4 s_rec[kStore == kStoreFp32 ? 4 * kSrecLd : 1];
+    __shared__ uint8_t s_live[kStore == kStoreFp32 ? kProjThreads : 1];
     if (threadIdx.x < 32) {
         // group of each virtual block: the last group with block0 <= vb
         // (block0 ascends from 0), counted by ballots
@@ -750,8 +780,11 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
                 const int jj = t / 3, r = t - 3 * jj;
                 const float4 vr = __ldg(Vi + r);
                 const float4 b0 = __ldg(Bi + jj * 3), b1 = __ldg(Bi + jj * 3 + 1), b2 = __ldg(Bi + jj * 3 + 2);
-                sB[t] = make_float4(vr.x * b0.x + vr.y * b1.x + vr.z * b2.x, vr.x * b0.y + vr.y * b1.y + vr.z * b2.y,
-                                    vr.x * b0.z + vr.y * b1.z + vr.z * b2.z, vr.x * b0.w + vr.y * b1.w + vr.z * b2.w);
+                float *o = sBw + jj * kSbwLd + 4 * r;
+                o[0] = vr.x * b0.x + vr.y * b1.x + vr.z * b2.x;
+                o[1] = vr.x * b0.y + vr.y * b1.y + vr.z * b2.y;
+                o[2] = vr.x * b0.z + vr.y * b1.z + vr.z * b2.z;
+                o[3] = vr.x * b0.w + vr.y * b1.w + vr.z * b2.w;
             } else if (kStore == kStoreBf16 && t < kJoints * 3) {
                 sB[t] = __ldg(Bi + t);
             } else if (t >= kJoints * 3 && t < kJoints * 3 + 3) {
@@ -760,8 +793,26 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
             __syncthreads();
             staged = inst;
         }
-        project_chunk<kStore>(G, islot, chunk, inst, sB, sV, s_tc, Vm, root, ta, tpls, cam, lod, skin_mode,
-                              sh_frame, rec, key, bin);
+        if (kStore == kStoreFp32) {
+            s_live[threadIdx.x] = 0;
+            project_chunk<kStore>(G, islot, chunk, inst, sB, sBw, sV, s_tc, Vm, root, ta, tpls, cam, lod,
+                                  skin_mode, sh_frame, rec, key, bin, s_rec, s_live);
+            __syncthreads();
+            // the chunk's records (live splats only), 16-byte piece o of the
+            // block at o (splat o / 4, piece o % 4), consecutive threads on
+            // consecutive pieces
+            const size_t s0 = (size_t)G.splat0 + (size_t)islot * G.ng + (size_t)chunk * kProjThreads;
+#pragma unroll
+            for (int i = 0; i < kRecVec; ++i) {
+                const int o = (int)threadIdx.x + i * kProjThreads;
+                const int sl = o >> 2, k = o & 3;
+                if (s_live[sl]) rec[s0 * kRecVec + o] = s_rec[k * kSrecLd + sl];
+            }
+            __syncthreads();  // the staging buffers are reused by the next chunk
+        } else {
+            project_chunk<kStore>(G, islot, chunk, inst, sB, sBw, sV, s_tc, Vm, root, ta, tpls, cam, lod,
+                                  skin_mode, sh_frame, rec, key, bin, nullptr, nullptr);
+        }
     }
 }
 
@@ -804,26 +855,26 @@ int launch_project(int n_blocks, const Group *groups, const Group *groups_host, 
 }
 
 __global__ void __launch_bounds__(256) k_debug_rects(int n, const float4 *__restrict__ rec,
-                                                     const uint32_t *__restrict__ bins, int W, int H,
-                                                     uint2 *__restrict__ rect) {
+                                                     const uint32_t *__restrict__ bins, int W, int H, int ox,
+                                                     int oy, uint2 *__restrict__ rect) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint2 rc = make_uint2(0u, 0u);
     if (bins[s] != 0u) {
         const float4 r0 = rec[(size_t)s * kRecVec], r1 = rec[(size_t)s * kRecVec + 1];
         int px0, px1, py0, py1;
-        box_range(r0.x, r1.z, W, px0, px1);
-        box_range(r0.y, r1.z, H, py0, py1);
+        box_range(r0.x, r1.z, ox, W, px0, px1);
+        box_range(r0.y, r1.z, oy, H, py0, py1);
         rc = make_uint2((uint32_t)(px0 >> 4) | ((uint32_t)(py0 >> 4) << 16),
                         (uint32_t)(px1 >> 4) | ((uint32_t)(py1 >> 4) << 16));
     }
     rect[s] = rc;
 }
 
-int launch_debug_rects(int n_splats, const float4 *rec, const uint32_t *bins, int W, int H, uint2 *rect,
-                       cudaStream_t st) {
+int launch_debug_rects(int n_splats, const float4 *rec, const uint32_t *bins, int W, int H, int ox, int oy,
+                       uint2 *rect, cudaStream_t st) {
     if (n_splats <= 0) return 0;
-    k_debug_rects<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, rec, bins, W, H, rect);
+    k_debug_rects<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, rec, bins, W, H, ox, oy, rect);
     return 1;
 }
 

@@ -92,8 +92,9 @@ struct ProjGroups {
 
 struct CamParams {
     float R[9], t[3];
-    float fx, fy, cx, cy;
-    int32_t W, H;
+    float fx, fy, cx, cy;  // of the full image
+    int32_t W, H;          // of the rendered window
+    int32_t ox, oy;        // window origin in the full image (multiples of the tile size)
     float near_z;
     float center[3];       // camera centre in world coordinates
     float limx, limy;      // EWA clamp of x/z, y/z (1.3 x half field of view)
@@ -171,10 +172,13 @@ __device__ __forceinline__ float splat_fcut(float opacity) {
 }
 
 // Pixel range [lo, hi] of a splat's support box on one axis (centres within
-// r of the mean), clipped to [0, size - 1]; lo > hi when empty.
-__device__ __forceinline__ void box_range(float c, float r, int size, int &lo, int &hi) {
-    const float l = fmaxf(ceilf(__fsub_rn(__fsub_rn(c, r), 0.5f)), 0.0f);
-    const float h = fminf(floorf(__fsub_rn(__fadd_rn(c, r), 0.5f)), (float)(size - 1));
+// r of the mean c, a full-image coordinate), in the coordinates of a window
+// starting at full-image pixel o, clipped to [0, size - 1]; lo > hi when
+// empty.  The integer shift by o is exact, so a window's ranges are the full
+// image's, shifted.
+__device__ __forceinline__ void box_range(float c, float r, int o, int size, int &lo, int &hi) {
+    const float l = fmaxf(ceilf(__fsub_rn(__fsub_rn(c, r), 0.5f)) - (float)o, 0.0f);
+    const float h = fminf(floorf(__fsub_rn(__fadd_rn(c, r), 0.5f)) - (float)o, (float)(size - 1));
     lo = (int)l;
     hi = (l <= h) ? (int)h : (int)l - 1;
 }
@@ -254,8 +258,8 @@ int launch_project(int n_blocks, const Group *groups, const Group *groups_host, 
                    uint32_t *key, uint32_t *bin, cudaStream_t st);
 // Tile rectangle of each splat's support box (debug view; recomputed from the
 // records: x0 | y0 << 16, x1 | y1 << 16; zero for splats without pairs).
-int launch_debug_rects(int n_splats, const float4 *rec, const uint32_t *bins, int W, int H, uint2 *rect,
-                       cudaStream_t st);
+int launch_debug_rects(int n_splats, const float4 *rec, const uint32_t *bins, int W, int H, int ox, int oy,
+                       uint2 *rect, cudaStream_t st);
 
 // ---- sort and binning (cs_sort.cu) ----
 // scratch words needed by exclusive_scan / radix_sort for n elements
@@ -324,6 +328,7 @@ struct BlendWork {
     float *px_T;
     int32_t *pp_tile;     // [tiles]
     int32_t *chunk_slot;  // [chunks]: the slot of each pass-2 chunk
+    int32_t ox, oy;       // window origin: pixel (i, j) has its centre at (ox + i + 0.5, oy + j + 0.5)
 };
 constexpr int kBlendMetaWords = 8;
 constexpr int kBlendBlockW = 8, kBlendBlockH = 4;  // pixels of one warp in a 16x16 tile

@@ -125,3 +125,43 @@ def psnr(a, b) -> float:
     else:
         d = float(np.mean((np.asarray(a, np.float64)[..., :3] - np.asarray(b, np.float64)[..., :3]) ** 2))
     return float(10 * math.log10(1.0 / max(d, 1e-30)))
+
+
+def prefix_orders(scores, fractions, template_sizes):
+    """Per template, a storage order whose prefixes are ranked levels: the
+    top round(f_L N) Gaussians of the coarsest band's score first, then the
+    next best of each finer band's score among those not yet placed, up to
+    that level's size, then the rest by the finest band's score.  Levels are
+    nested by construction (each coarser level is a prefix of the finer
+    ones), so a template re-uploaded in this order renders its levels as
+    plain prefixes, with no per-level index list to gather through.
+    scores: [n_levels, n_total] (CUDA tensor or array); fractions: one per
+    level, finest first.  Returns a list of int64 permutations (storage
+    position -> original index)."""
+    sc = scores.cpu().numpy() if hasattr(scores, "cpu") else np.asarray(scores)
+    out, off = [], 0
+    L = len(fractions)
+    for n in template_sizes:
+        s = sc[:, off:off + n].astype(np.float64)
+        placed = np.zeros(n, bool)
+        order = []
+        for l in range(L - 1, -1, -1):
+            k = n if l == 0 else min(n, max(1, int(math.floor(float(np.float32(fractions[l])) * n + 0.5))))
+            need = k - len(order)
+            if need <= 0:
+                continue
+            cand = np.nonzero(~placed)[0]
+            # highest score first; ties by index (stable)
+            pick = cand[np.argsort(-s[min(l, s.shape[0] - 1), cand], kind="stable")[:need]]
+            order.extend(pick.tolist())
+            placed[pick] = True
+        out.append(np.asarray(order, np.int64))
+        off += n
+    return out
+
+
+def permute_template(tpl, perm):
+    """The template with its Gaussians stored in the order `perm`."""
+    return dataclasses.replace(tpl, means=tpl.means[perm], scales=tpl.scales[perm], quats=tpl.quats[perm],
+                               opacity=tpl.opacity[perm], sh=tpl.sh[perm], skin_idx=tpl.skin_idx[perm],
+                               skin_w=tpl.skin_w[perm])

@@ -137,6 +137,13 @@ class Camera:
     width: int
     height: int
     near: float = 0.2
+    # window of a larger image (0 = no window): this camera renders pixels
+    # [win_x0, win_x0 + width) x [win_y0, win_y0 + height) of a full_width x
+    # full_height image whose principal point is (cx, cy)
+    win_x0: int = 0
+    win_y0: int = 0
+    full_width: int = 0
+    full_height: int = 0
 
     @property
     def center(self) -> np.ndarray:

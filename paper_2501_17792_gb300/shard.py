@@ -27,11 +27,14 @@ def row_ranges(height: int, world: int, tile: int = 16):
     return out
 
 
-def sub_camera(cam, row0: int, row1: int):
-    """Camera that renders rows [row0, row1) of `cam`'s image: same pose and
-    focal lengths, principal point moved up by row0, height row1 - row0.
-    Pixel centres of the sub-image coincide with those rows of the full one
-    (values agree up to FP32 rounding of the shifted principal point)."""
+def sub_camera(cam, row0: int, row1: int, tile: int = 16):
+    """Camera that renders rows [row0, row1) of `cam`'s image as a window of
+    the full image: same pose, focal lengths and principal point, the full
+    image's size and field of view (the EWA clamp depends on it), and pixel
+    centres at their full-image positions.  With row0 on the tile grid the
+    window's pixels are bit for bit the full frame's rows."""
     if not (0 <= row0 < row1 <= cam.height):
         raise ValueError("row range outside the image")
-    return replace(cam, cy=cam.cy - row0, height=row1 - row0)
+    if row0 % tile:
+        raise ValueError(f"row0 must be a multiple of the tile size {tile}")
+    return replace(cam, height=row1 - row0, win_x0=0, win_y0=row0, full_width=cam.width, full_height=cam.height)

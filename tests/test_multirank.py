@@ -99,6 +99,9 @@ def test_sub_camera_maps_rows():
     from paper_2501_17792_gb300 import scene as S, shard
     cam = S.look_camera((0.0, 1.6, 0.0), 10.0, 64, 48)
     sub = shard.sub_camera(cam, 16, 32)
-    assert sub.height == 16 and sub.cy == cam.cy - 16 and sub.width == 64
+    assert sub.height == 16 and sub.width == 64 and sub.cy == cam.cy and sub.cx == cam.cx
+    assert (sub.win_x0, sub.win_y0, sub.full_width, sub.full_height) == (0, 16, 64, 48)
     with pytest.raises(ValueError):
         shard.sub_camera(cam, 40, 60)
+    with pytest.raises(ValueError):
+        shard.sub_camera(cam, 8, 24)  # not on the tile grid
