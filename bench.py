@@ -128,9 +128,9 @@ def stage_bytes(st, n_inst, tpl_bytes, pixels):
         "fk": n_inst * (4 + 72 * 4 + 24 * 48),
         "cull_lod": n_inst * (4 + 48 + 48 + 16 + 4),
         # template attributes once (shared, L2-resident across a group) +
-        # per-instance transforms + per-splat key and bin word + the 64 B
+        # per-instance transforms + per-splat key and bin word + the 48 B
         # record of every live splat
-        "skin_project": tpl_bytes + V * (24 * 48 + 64) + S * (4 + 4) + live * 64,
+        "skin_project": tpl_bytes + V * (24 * 48 + 64) + S * (4 + 4) + live * 48,
         # per pass: keys read by the histogram, key+value read and written;
         # the first pass reads no values (they are the indices), the last
         # writes the bin words in depth order (gathered)
@@ -140,8 +140,8 @@ def stage_bytes(st, n_inst, tpl_bytes, pixels):
         "pair_emit": S * (4 + 4 + 4) + P * 6,
         "tile_sort": P * passes_tile * (2 + 6 + 6),
         "tile_ranges": P * 2 * 2,
-        # each pair: splat id + 64 B record; each pixel: 16 B written
-        "blend": P * (4 + 64) + pixels * 16,
+        # each pair: splat id + 48 B record; each pixel: 16 B written
+        "blend": P * (4 + 48) + pixels * 16,
     }
 
 

@@ -242,7 +242,7 @@ int cs_render_to_host(cs_ctx *ctx, const cs_camera *cam, float *rgba_host, cs_fr
  * front.  CrowdSplat has no counterpart of this call; it renders exactly
  * what cs_render renders, with the per-frame scratch (splat records, sort
  * buffers, pair lists, tile ranges) taken from one static device array of
- * about 11.6 MB that every GPU loading the library holds until the process
+ * about 9.9 MB that every GPU loading the library holds until the process
  * exits.  Limits per frame: 65,536 splats, 262,144 (tile, splat) pairs,
  * 16,384 tiles (e.g. 2048 x 2048); larger frames fail with CS_ERR_CAPACITY
  * and a message naming the limit, leaving rgba_out unwritten.  The
@@ -286,7 +286,10 @@ const char *cs_last_error(const cs_ctx *ctx);
                                 gaussians per slot, first splat, first projection CTA  */
 #define CS_DBG_RECORDS 4     /* float [S][16]: u, v, conic A, B, C, opacity, radius,
                                 depth, r, g, b, 0, reach x, reach y (pixel ranges lo | hi
-                                << 16 as float bits), fcut, log2 opacity              */
+                                << 16 as float bits), fcut, log2 opacity: the 48-byte
+                                splat records expanded for this view (opacity from
+                                its logarithm, depth from the depth key); culled
+                                splats read as zeros                               */
 #define CS_DBG_DEPTH_KEYS 5  /* uint32 [S]: depth keys in depth order: float bits of the
                                 depth minus those of the frame's lower depth bound
                                 (from the instance cull), 0xFFFFFFFF = culled      */

@@ -82,6 +82,8 @@ struct cs_ctx {
     DevBuf<uint2> rect, ranges;
     DevBuf<uint16_t> ptile, ptile2;
     DevBuf<float4> img;  // for cs_render_to_host
+    DevBuf<float4> dbg_rec;  // expanded records (debug view)
+    uint32_t key_lo = 0;     // the last frame's depth-key offset
     DevBuf<float> contrib_s;  // per-splat compositing weight sums (cs_render_contrib)
     // training frame (cs_render_train / cs_backward)
     DevBuf<uint32_t> px_end;
@@ -444,7 +446,7 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->rec); release(ctx->key); release(ctx->ids); release(ctx->key2); release(ctx->ids2);
     release(ctx->bins); release(ctx->bins_sorted); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
     release(ctx->scratch); release(ctx->rect); release(ctx->ranges); release(ctx->ptile);
-    release(ctx->ptile2); release(ctx->img); release(ctx->contrib_s);
+    release(ctx->ptile2); release(ctx->img); release(ctx->contrib_s); release(ctx->dbg_rec);
     release(ctx->px_end); release(ctx->px_T); release(ctx->dsplat); release(ctx->g_cov); release(ctx->g_B);
     release(ctx->g_dummy);
     release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_pp); release(ctx->bw_cslot); release(ctx->bw_chunk0);
@@ -883,6 +885,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         ctx->visible = ctx->h_meta[kMetaVisible];
         ctx->n_groups = ctx->h_meta[kMetaGroups];
         set_depth_key_range(cp, ctx->h_meta);
+        ctx->key_lo = cp.key_lo;
         S = ctx->h_meta[kMetaSplats];
         proj_blocks = ctx->h_meta[kMetaBlocks];
         for (int l = 0; l < kMaxLevels; ++l) ctx->per_level[l] = ctx->h_meta[kMetaLevel0 + l];
@@ -1267,7 +1270,19 @@ int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size
         case CS_DBG_SKIN_B: src = ctx->B.p; size = (size_t)ctx->n_inst * kJoints * 12 * sizeof(float); break;
         case CS_DBG_VISIBLE: src = ctx->vis.p; size = (size_t)ctx->visible * sizeof(int32_t); break;
         case CS_DBG_GROUPS: src = ctx->groups.p; size = (size_t)ctx->n_groups * sizeof(Group); break;
-        case CS_DBG_RECORDS: src = ctx->rec.p; size = (size_t)ctx->S * kRecVec * sizeof(float4); break;
+        case CS_DBG_RECORDS:
+            // the 48-byte records expanded to the 16-float view
+            if (ctx->S > 0) {
+                CS_TRY(ensure(ctx, ctx->dbg_rec, (size_t)ctx->S * 4, "debug records"));
+                CS_CUDA(cudaMemsetAsync(ctx->dbg_rec.p, 0, (size_t)ctx->S * 4 * sizeof(float4), ctx->stream));
+                launch_debug_records((int)ctx->S, ctx->rec.p, ctx->order_buf ? ctx->key2.p : ctx->key.p,
+                                     ctx->order_buf ? ctx->ids2.p : ctx->ids.p, ctx->key_lo, ctx->dbg_rec.p,
+                                     ctx->stream);
+                CS_CUDA(cudaGetLastError());
+            }
+            src = ctx->dbg_rec.p;
+            size = (size_t)ctx->S * 4 * sizeof(float4);
+            break;
         case CS_DBG_DEPTH_KEYS: src = ctx->order_buf ? ctx->key2.p : ctx->key.p; size = (size_t)ctx->S * 4; break;
         case CS_DBG_RECTS:
             // recomputed from the records of the last frame
@@ -1341,7 +1356,8 @@ constexpr size_t kOffBwPart = kOffBwState + a256(kStaticSlots * 256 * sizeof(flo
 constexpr size_t kOffBwStop = kOffBwPart + a256(kStaticChunks * 256 * sizeof(float4));
 constexpr size_t kOffBwPp = kOffBwStop + a256(kStaticSlots * 256 * 4);
 constexpr size_t kOffBwCslot = kOffBwPp + a256(kStaticTiles * 4);
-constexpr size_t kStaticBytes = kOffBwCslot + a256(kStaticChunks * 4);  // about 11.6 MB
+constexpr size_t kStaticBytes = kOffBwCslot + a256(kStaticChunks * 4);  // about 9.9 MB
+static_assert(kStaticBytes > 9800000 && kStaticBytes < 10000000, "the documented size of the static frame scratch");
 
 }  // namespace
 

@@ -100,11 +100,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_backward(
         if ((uint32_t)tid < nb) {
             const uint32_t s = __ldg(pval + lo + tid);
             const float4 *r = rec + (size_t)s * kRecVec;
-            const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), q = __ldg(r + 3);
+            const float4 q = __ldg(r), a = __ldg(r + 1), c = __ldg(r + 2);  // {rx, ry, log2 o, C}, {u, v, A, B}, {rgb, radius}
             sh.s0[tid] = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
-            sh.s1[tid] = make_float4(-0.5f * kLog2e * b.x, q.w, b.z, b.y);
+            // opacity from its logarithm (within an ulp): only gradients use it
+            sh.s1[tid] = make_float4(-0.5f * kLog2e * q.w, q.z, c.w, exp2f(q.z));
             sh.s2[tid] = c;
-            sh.s3[tid] = make_float4(a.z, a.w, b.x, 0.f);
+            sh.s3[tid] = make_float4(a.z, a.w, q.w, 0.f);
             sh.sid[tid] = s;
             const uint32_t rx = __float_as_uint(q.x), ry = __float_as_uint(q.y);
             const int x0 = (int)(rx & 0xFFFFu) - tx0, x1 = (int)(rx >> 16) - tx0;

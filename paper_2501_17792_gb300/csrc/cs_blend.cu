@@ -55,7 +55,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 struct StagedRecord {
-    float4 a, b, c, q;  // {u, v, A, B}, {C, o, r, depth}, {r, g, b, -}, {reach x, reach y, fcut, log2 o}
+    float4 q, a, c;  // {reach x, reach y, log2 o, C}, {u, v, A, B}, {r, g, b, radius}
     uint32_t s;         // splat id
     bool have;
 };
@@ -66,10 +66,9 @@ __device__ __forceinline__ void load_record(StagedRecord &r, const uint32_t *__r
     if (r.have) {
         r.s = __ldg(pval + idx);
         const float4 *p = rec + (size_t)r.s * kRecVec;
-        r.a = __ldg(p + 0);
-        r.b = __ldg(p + 1);
+        r.q = __ldg(p + 0);
+        r.a = __ldg(p + 1);
         r.c = __ldg(p + 2);
-        r.q = __ldg(p + 3);
     }
 }
 
@@ -118,7 +117,7 @@ __device__ __forceinline__ void composite_range(BlendShared<kT> &sh, uint32_t st
                 if (x0 <= bx + kBlockW - 1 && x1 >= bx && y0 <= by + kBlockH - 1 && y1 >= by) m |= 1u << w;
             }
             sh.s0[h][tid] = make_float4(r.a.x, r.a.y, -0.5f * kLog2e * r.a.z, -kLog2e * r.a.w);
-            sh.s1[h][tid] = make_float4(-0.5f * kLog2e * r.b.x, r.q.w, r.b.z, 0.0f);
+            sh.s1[h][tid] = make_float4(-0.5f * kLog2e * r.q.w, r.q.z, r.c.w, 0.0f);
             sh.s2[h][tid] = r.c;
             if (kMode == 1) sh.sid[h][tid] = r.s;
         }
@@ -329,14 +328,14 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
                 const float4 *p = rec + (size_t)s * kRecVec;
                 // the reach box first: the rest of the record only for
                 // splats whose reach box meets this block
-                const float4 rq = __ldg(p + 3);
+                const float4 rq = __ldg(p);  // reach x, reach y, log2 o, C
                 const uint32_t rx = __float_as_uint(rq.x), ry = __float_as_uint(rq.y);
                 mine = (int)(rx & 0xFFFFu) <= bx0 + kBlockW - 1 && (int)(rx >> 16) >= bx0 &&
                        (int)(ry & 0xFFFFu) <= by0 + kBlockH - 1 && (int)(ry >> 16) >= by0;
                 if (mine) {
-                    const float4 ra = __ldg(p), rb = __ldg(p + 1), rc = __ldg(p + 2);
+                    const float4 ra = __ldg(p + 1), rc = __ldg(p + 2);
                     sh.s0[warp][lane] = make_float4(ra.x, ra.y, -0.5f * kLog2e * ra.z, -kLog2e * ra.w);
-                    sh.s1[warp][lane] = make_float4(-0.5f * kLog2e * rb.x, rq.w, rb.z, 0.0f);
+                    sh.s1[warp][lane] = make_float4(-0.5f * kLog2e * rq.w, rq.z, rc.w, 0.0f);
                     sh.s2[warp][lane] = rc;
                 }
             }

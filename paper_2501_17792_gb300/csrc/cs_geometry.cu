@@ -696,26 +696,23 @@ __device__ __forceinline__ void project_chunk(
                         default: sh_colour<3>(ta.sh, base, G.n, ddx, ddy, ddz, rgb); break;
                     }
                 }
-                const float4 r0 = make_float4(u, v, cA, cB);
-                const float4 r1 = make_float4(cC, mo.w, r, tz);
-                const float4 r2 = make_float4(rgb[0], rgb[1], rgb[2], 0.0f);
-                const float4 r3 = make_float4(__uint_as_float((uint32_t)ax0 | ((uint32_t)ax1 << 16)),
-                                              __uint_as_float((uint32_t)ay0 | ((uint32_t)ay1 << 16)), fcut,
-                                              __log2f(mo.w));
+                const float4 r0 = make_float4(__uint_as_float((uint32_t)ax0 | ((uint32_t)ax1 << 16)),
+                                              __uint_as_float((uint32_t)ay0 | ((uint32_t)ay1 << 16)),
+                                              __log2f(mo.w), cC);
+                const float4 r1 = make_float4(u, v, cA, cB);
+                const float4 r2 = make_float4(rgb[0], rgb[1], rgb[2], r);
                 if (srec) {
                     // staged: the CTA writes the chunk's records out coalesced
                     const int t = threadIdx.x;
                     srec[0 * kSrecLd + t] = r0;
                     srec[1 * kSrecLd + t] = r1;
                     srec[2 * kSrecLd + t] = r2;
-                    srec[3 * kSrecLd + t] = r3;
                     slive[t] = 1;
                 } else {
                     float4 *ro = rec + (size_t)s * kRecVec;
                     ro[0] = r0;
                     ro[1] = r1;
                     ro[2] = r2;
-                    ro[3] = r3;
                 }
             }
         }
@@ -741,7 +738,7 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
     __shared__ float4 sV[3];            // V = camera o root, rows
     __shared__ int s_group[kChunks];
     __shared__ __align__(16) unsigned char s_tc[kStore == kStoreBf16 ? kSkinTcBytes : 16];
-    __shared__ float4 s_rec[kStore == kStoreFp32 ? 4 * kSrecLd : 1];
+    __shared__ float4 s_rec[kStore == kStoreFp32 ? kRecVec * kSrecLd : 1];
     __shared__ uint8_t s_live[kStore == kStoreFp32 ? kProjThreads : 1];
     if (threadIdx.x < 32) {
         // group of each virtual block: the last group with block0 <= vb
@@ -799,13 +796,13 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
                                   skin_mode, sh_frame, rec, key, bin, s_rec, s_live);
             __syncthreads();
             // the chunk's records (live splats only), 16-byte piece o of the
-            // block at o (splat o / 4, piece o % 4), consecutive threads on
-            // consecutive pieces
+            // block at o (splat o / kRecVec, piece o % kRecVec), consecutive
+            // threads on consecutive pieces
             const size_t s0 = (size_t)G.splat0 + (size_t)islot * G.ng + (size_t)chunk * kProjThreads;
 #pragma unroll
             for (int i = 0; i < kRecVec; ++i) {
                 const int o = (int)threadIdx.x + i * kProjThreads;
-                const int sl = o >> 2, k = o & 3;
+                const int sl = o / kRecVec, k = o - sl * kRecVec;
                 if (s_live[sl]) rec[s0 * kRecVec + o] = s_rec[k * kSrecLd + sl];
             }
             __syncthreads();  // the staging buffers are reused by the next chunk
@@ -861,14 +858,43 @@ __global__ void __launch_bounds__(256) k_debug_rects(int n, const float4 *__rest
     if (s >= n) return;
     uint2 rc = make_uint2(0u, 0u);
     if (bins[s] != 0u) {
-        const float4 r0 = rec[(size_t)s * kRecVec], r1 = rec[(size_t)s * kRecVec + 1];
+        const float4 r1 = rec[(size_t)s * kRecVec + 1], r2 = rec[(size_t)s * kRecVec + 2];
         int px0, px1, py0, py1;
-        box_range(r0.x, r1.z, ox, W, px0, px1);
-        box_range(r0.y, r1.z, oy, H, py0, py1);
+        box_range(r1.x, r2.w, ox, W, px0, px1);
+        box_range(r1.y, r2.w, oy, H, py0, py1);
         rc = make_uint2((uint32_t)(px0 >> 4) | ((uint32_t)(py0 >> 4) << 16),
                         (uint32_t)(px1 >> 4) | ((uint32_t)(py1 >> 4) << 16));
     }
     rect[s] = rc;
+}
+
+// Debug view of the records: per splat the 16 floats {u, v, A, B}, {C,
+// opacity, radius, depth}, {r, g, b, 0}, {reach x, reach y, fcut, log2
+// opacity}; opacity from its logarithm (within an ulp), the depth from the
+// depth key (exactly: float bits = key + key_lo), fcut as the projection
+// computes it.  Thread per position i of the depth order.
+__global__ void __launch_bounds__(256) k_debug_records(int n, const float4 *__restrict__ rec,
+                                                       const uint32_t *__restrict__ sorted_keys,
+                                                       const uint32_t *__restrict__ order, uint32_t key_lo,
+                                                       float4 *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t s = order[i], key = sorted_keys[i];
+    if (key == 0xFFFFFFFFu) return;  // culled: no record
+    const float4 q = rec[(size_t)s * kRecVec], a = rec[(size_t)s * kRecVec + 1], c = rec[(size_t)s * kRecVec + 2];
+    const float o = exp2f(q.z);
+    float4 *d = out + (size_t)s * 4;
+    d[0] = a;
+    d[1] = make_float4(q.w, o, c.w, __uint_as_float(key + key_lo));
+    d[2] = make_float4(c.x, c.y, c.z, 0.0f);
+    d[3] = make_float4(q.x, q.y, splat_fcut(o), q.z);
+}
+
+int launch_debug_records(int n_splats, const float4 *rec, const uint32_t *sorted_keys, const uint32_t *order,
+                         uint32_t key_lo, float4 *out, cudaStream_t st) {
+    if (n_splats <= 0) return 0;
+    k_debug_records<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, rec, sorted_keys, order, key_lo, out);
+    return 1;
 }
 
 int launch_debug_rects(int n_splats, const float4 *rec, const uint32_t *bins, int W, int H, int ox, int oy,

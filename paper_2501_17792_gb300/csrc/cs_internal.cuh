@@ -17,10 +17,11 @@
 // applied), V[i][12] = camera o root (3x4), C[i][4] = camera centre in the
 // instance root frame.
 // Per splat s (Gaussian-instance of a visible instance, dense ids grouped by
-// (template, level)): a 64-byte record rec[4s..4s+3] float4 = {u, v, A, B},
-// {C, opacity, radius, depth}, {r, g, b, 0}, {reach x, reach y, fcut,
-// log2 opacity} where reach x/y hold the inclusive pixel range (lo | hi << 16,
-// as float bits) in which alpha can reach 1/255 (see splat_reach_box);
+// (template, level)): a 48-byte record rec[3s..3s+2] float4 = {reach x,
+// reach y, log2 opacity, C}, {u, v, A, B}, {r, g, b, radius} where reach x/y
+// hold the inclusive pixel range (lo | hi << 16, as float bits) in which
+// alpha can reach 1/255 (see splat_reach_box); the compositing reads the
+// first word alone to test a splat against a pixel block;
 // key[s] depth bits (0xFFFFFFFF culled); rect[s] tile rectangle of the
 // support box (x0 | y0 << 16, x1 | y1 << 16), inclusive; bin[s] the tiles
 // holding a pixel the compositing uses (the pairs of the splat), as a bin
@@ -39,7 +40,7 @@ constexpr int kJoints = 24;
 constexpr int kMaxTemplates = 63;
 constexpr int kMaxLevels = 4;
 constexpr int kTile = 16;
-constexpr int kRecVec = 4;  // float4 per splat record
+constexpr int kRecVec = 3;  // float4 per splat record (48 bytes)
 constexpr uint32_t kBinLarge = 0x80000000u;
 
 // number of pairs (tiles) described by a bin word
@@ -260,6 +261,10 @@ int launch_project(int n_blocks, const Group *groups, const Group *groups_host, 
 // records: x0 | y0 << 16, x1 | y1 << 16; zero for splats without pairs).
 int launch_debug_rects(int n_splats, const float4 *rec, const uint32_t *bins, int W, int H, int ox, int oy,
                        uint2 *rect, cudaStream_t st);
+// The records of the last frame expanded to 16 floats per splat (debug
+// view; culled splats left unwritten).
+int launch_debug_records(int n_splats, const float4 *rec, const uint32_t *sorted_keys, const uint32_t *order,
+                         uint32_t key_lo, float4 *out, cudaStream_t st);
 
 // ---- sort and binning (cs_sort.cu) ----
 // scratch words needed by exclusive_scan / radix_sort for n elements

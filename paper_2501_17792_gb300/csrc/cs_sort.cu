@@ -413,7 +413,7 @@ __device__ __forceinline__ void emit_splat_pairs(uint32_t b, uint32_t s, uint32_
         }
         return;
     }
-    const float4 r3 = rec[(size_t)s * kRecVec + 3];  // reach x, reach y, fcut, log2 o
+    const float4 r3 = rec[(size_t)s * kRecVec];  // reach x, reach y, log2 o, C
     const uint32_t rx = __float_as_uint(r3.x), ry = __float_as_uint(r3.y);
     const int ax0 = (int)(rx & 0xFFFFu), ax1 = (int)(rx >> 16);
     const int ay0 = (int)(ry & 0xFFFFu), ay1 = (int)(ry >> 16);
