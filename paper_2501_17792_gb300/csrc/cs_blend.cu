@@ -11,8 +11,10 @@
 // tile size.
 //
 // Pass 1 of a plain frame (k_blend_pp) composites each 8x4 pixel block of
-// a tile with eight warps that split the block's depth-ordered pairs into
-// sub-ranges and chain their partial composites (described at the kernel).
+// a tile with a long list with eight warps that split the block's
+// depth-ordered pairs into sub-ranges and chain their partial composites,
+// and every tile with a short list with one CTA, one warp per block
+// (described at the kernel).
 //
 // The one-pass kernels (statistics and training frames) and the split passes
 // below take one CTA per tile, one thread per pixel, each warp an 8x4 block
@@ -245,30 +247,57 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
 // (only it needs the true T; the rest of the operator is associative).  A
 // block's dependency chain is one round per kPpRound pairs, split over
 // eight warps, instead of every pair in turn: a long list of large splats
-// no longer leaves the GPU waiting on a single CTA.  Persistent CTAs take
-// (tile, block) items from a list ordered by decreasing list length (so the
-// longest chains start first), then one item per empty tile (background).
+// no longer leaves the GPU waiting on a single CTA.
+//
+// A tile whose list is shorter (below 2^(kPpTileClass - 1) pairs) is one
+// item of its own instead: the CTA stages each batch of kPpRound pairs once
+// for the whole tile, with the blocks each reach box meets as one bit mask
+// per block, and warp w composites block w's pairs in depth order, as the
+// definition reads.  Eight block items would stage every pair eight times
+// and pay eight rounds of barriers and chaining; where lists are mid-length
+// and many (a 4K frame of a large crowd) the pass is bound by instruction
+// issue, and the tile items issue 17% fewer instructions there.
+//
+// Persistent CTAs take items in decreasing schedule key (blend_key: the
+// list length class, raised for tile items), so the longest dependency
+// chains start first; empty tiles (background) come last.
 // ---------------------------------------------------------------------------
 constexpr int kPpWarps = 8;
 constexpr int kPpThreads = 32 * kPpWarps;
 constexpr uint32_t kPpRound = 32 * kPpWarps;
 constexpr int kPpBlocks = kTile * kTile / 32;  // 8x4 blocks per tile
+constexpr int kPpTileClass = 13;               // lists of fewer than 4,096 pairs: tile items
+static_assert((1u << (kPpTileClass - 1)) <= kBlendBudget, "a tile item composites its whole list");
 
 struct PpShared {
     float4 s0[kPpWarps][32];  // u, v, a', b' (as staged by composite_range)
     float4 s1[kPpWarps][32];  // c', log2 o, radius, -
     float4 s2[kPpWarps][32];  // r, g, b, -
     float4 part[kPpWarps][32];
+    uint32_t wm[kPpBlocks][kPpWarps];  // tile items: bit l of wm[b][k]: pair 32 k + l meets block b
     uint32_t m[kPpWarps];  // pairs of each sub-range whose reach box meets the block
     uint32_t done;         // pixels of the block that are done
-    int item;
+    int tile, kind, blk;   // the current item: kind 0 empty tile, 1 tile item, 2 block item
+    int seg_item[kBlendKeys + 1], seg_tile[kBlendKeys + 1];  // first item and tile of each key, decreasing key
 };
 
 // alpha of a staged splat at a pixel centre; 0 when the splat does not
 // contribute there (outside its support box, q > 0, alpha < 1/255).  The
-// same arithmetic as composite_range.
+// same arithmetic as composite_range.  kBranchFree evaluates every test
+// without branches: a splat that does not contribute then leaves T and C
+// unchanged when composited with alpha = 0 (T (1 - 0) = T exactly), so the
+// caller needs no test either.  That pays where the pairs of a sub-range
+// are composited by many warps at once (no divergence); one warp walking a
+// block's pairs in turn is faster skipping early.
+template <bool kBranchFree>
 __device__ __forceinline__ float staged_alpha(const float4 &a, const float4 &b, float fpx, float fpy) {
     const float dx = fpx - a.x, dy = fpy - a.y;
+    if (kBranchFree) {
+        const float p = dx * (a.z * dx + a.w * dy) + b.x * dy * dy;
+        const float alpha = fminf(0.99f, ex2_approx(p + b.y));
+        const bool skip = fmaxf(fabsf(dx), fabsf(dy)) > b.z || p > 0.0f || alpha < (1.0f / 255.0f);
+        return skip ? 0.0f : alpha;
+    }
     if (fmaxf(fabsf(dx), fabsf(dy)) > b.z) return 0.0f;
     const float p = dx * (a.z * dx + a.w * dy) + b.x * dy * dy;
     if (p > 0.0f) return 0.0f;
@@ -282,26 +311,117 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
                                                          BlendWork work) {
     __shared__ PpShared sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_busy = work.meta[2];
-    const int n_busy_items = n_busy * kPpBlocks;
-    const int n_items = n_busy_items + work.meta[4];
-    for (;;) {
-        if (threadIdx.x == 0) sh.item = (int)atomicAdd(reinterpret_cast<unsigned *>(work.meta + 3), 1u);
-        __syncthreads();
-        const int item = sh.item;
-        if (item >= n_items) return;
-        if (item >= n_busy_items) {
-            // a tile without pairs: background (C = 0, T = 1)
-            const int tile = work.pp_tile[n_busy + (item - n_busy_items)];
-            const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
-            for (int q = threadIdx.x; q < kTile * kTile; q += kPpThreads) {
-                const int x = txi * kTile + (q & (kTile - 1)), y = tyi * kTile + q / kTile;
-                if (x < W && y < H) out[(size_t)y * W + x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            }
-            __syncthreads();  // sh.item is reused by the next item
-            continue;
+    // items in decreasing schedule key: per key, its tiles times kPpBlocks
+    // (odd keys: block items) or times 1
+    if (threadIdx.x == 0) {
+        int ri = 0, rt = 0;
+        for (int s = 0; s < kBlendKeys; ++s) {
+            const int key = kBlendKeys - 1 - s, cnt = work.meta[kBlendCountAt + key];
+            sh.seg_item[s] = ri;
+            sh.seg_tile[s] = rt;
+            ri += (key & 1) ? cnt * kPpBlocks : cnt;
+            rt += cnt;
         }
-        const int tile = work.pp_tile[item / kPpBlocks], blk = item % kPpBlocks;
+        sh.seg_item[kBlendKeys] = ri;
+        sh.seg_tile[kBlendKeys] = rt;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int item = (int)atomicAdd(reinterpret_cast<unsigned *>(work.meta + 3), 1u);
+            int seg = 0;
+            while (seg < kBlendKeys && item >= sh.seg_item[seg + 1]) ++seg;
+            int tile = -1, kind = 0, blk = 0;
+            if (seg < kBlendKeys) {
+                const int key = kBlendKeys - 1 - seg, off = item - sh.seg_item[seg];
+                const int per = (key & 1) ? kPpBlocks : 1;
+                tile = work.pp_tile[sh.seg_tile[seg] + off / per];
+                blk = off % per;
+                kind = key == 0 ? 0 : ((key & 1) ? 2 : 1);
+            }
+            sh.tile = tile;
+            sh.kind = kind;
+            sh.blk = blk;
+        }
+        __syncthreads();
+        const int tile = sh.tile, kind = sh.kind;
+        if (tile < 0) return;
+        if (kind != 2) {
+            const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
+            const int tx0 = txi * kTile, ty0 = tyi * kTile;
+            if (kind == 0) {
+                // a tile without pairs: background (C = 0, T = 1)
+                for (int q = threadIdx.x; q < kTile * kTile; q += kPpThreads) {
+                    const int x = tx0 + (q & (kTile - 1)), y = ty0 + q / kTile;
+                    if (x < W && y < H) out[(size_t)y * W + x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+                __syncthreads();  // the item fields are rewritten for the next item
+                continue;
+            }
+            // a short list: the whole tile, warp w compositing block w
+            const int px = tx0 + (warp & 1) * kBlockW + (lane & (kBlockW - 1));
+            const int py = ty0 + (warp >> 1) * kBlockH + lane / kBlockW;
+            const bool inside = px < W && py < H;
+            const float fpx = (float)(px + work.ox) + 0.5f, fpy = (float)(py + work.oy) + 0.5f;
+            const uint2 rg = ranges[tile];
+            float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+            bool done = !inside;
+            float4 *const f0 = &sh.s0[0][0], *const f1 = &sh.s1[0][0], *const f2 = &sh.s2[0][0];
+            for (uint32_t base = rg.x; base < rg.y; base += kPpRound) {
+                // stage pair base + tid with the blocks its reach box meets
+                const uint32_t i = base + threadIdx.x;
+                uint32_t bm = 0;
+                if (i < rg.y) {
+                    const uint32_t s = __ldg(pval + i);
+                    const float4 *p = rec + (size_t)s * kRecVec;
+                    const float4 rq = __ldg(p);  // reach x, reach y, log2 o, C
+                    const uint32_t rx = __float_as_uint(rq.x), ry = __float_as_uint(rq.y);
+                    const int x0 = (int)(rx & 0xFFFFu) - tx0, x1 = (int)(rx >> 16) - tx0;
+                    const int y0 = (int)(ry & 0xFFFFu) - ty0, y1 = (int)(ry >> 16) - ty0;
+#pragma unroll
+                    for (int b = 0; b < kPpBlocks; ++b) {
+                        const int bx = (b & 1) * kBlockW, by = (b >> 1) * kBlockH;
+                        if (x0 <= bx + kBlockW - 1 && x1 >= bx && y0 <= by + kBlockH - 1 && y1 >= by) bm |= 1u << b;
+                    }
+                    if (bm) {
+                        const float4 ra = __ldg(p + 1), rc = __ldg(p + 2);
+                        f0[threadIdx.x] = make_float4(ra.x, ra.y, -0.5f * kLog2e * ra.z, -kLog2e * ra.w);
+                        f1[threadIdx.x] = make_float4(-0.5f * kLog2e * rq.w, rq.z, rc.w, 0.0f);
+                        f2[threadIdx.x] = rc;
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < kPpBlocks; ++b) {
+                    const uint32_t word = __ballot_sync(0xffffffffu, (bm >> b) & 1u);
+                    if (lane == 0) sh.wm[b][warp] = word;
+                }
+                __syncthreads();
+                for (int k = 0; k < kPpWarps && !done; ++k) {
+                    uint32_t m = sh.wm[warp][k];
+                    while (m) {
+                        const int j = 32 * k + __ffs(m) - 1;
+                        m &= m - 1;
+                        const float alpha = staged_alpha<false>(f0[j], f1[j], fpx, fpy);
+                        if (alpha == 0.0f) continue;
+                        const float Tn = T * (1.0f - alpha);
+                        if (Tn < 1e-4f) {
+                            done = true;
+                            break;
+                        }
+                        const float4 col = f2[j];
+                        const float wgt = alpha * T;
+                        cr += col.x * wgt;
+                        cg += col.y * wgt;
+                        cb += col.z * wgt;
+                        T = Tn;
+                    }
+                }
+                // the staging buffers are refilled by the next batch
+                if (__syncthreads_count(done) == kPpThreads) break;
+            }
+            if (inside) out[(size_t)py * W + px] = make_float4(cr, cg, cb, 1.0f - T);
+            continue;  // the loop's barriers keep the item fields until every thread has read them
+        }
+        const int blk = sh.blk;
         const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
         const int bx0 = txi * kTile + (blk & 1) * kBlockW, by0 = tyi * kTile + (blk >> 1) * kBlockH;
         const int px = bx0 + (lane & (kBlockW - 1)), py = by0 + lane / kBlockW;
@@ -343,14 +463,12 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
             if (lane == 0) sh.m[warp] = m;
             __syncwarp();
             // the sub-range's partial composite from T = 1
-            const bool pdone = (dmask >> lane) & 1u;
             float Tk = 1.0f, kr = 0.0f, kg = 0.0f, kb = 0.0f;
             while (m) {
                 const int j = __ffs(m) - 1;
                 m &= m - 1;
-                if (pdone) continue;
-                const float alpha = staged_alpha(sh.s0[warp][j], sh.s1[warp][j], fpx, fpy);
-                if (alpha == 0.0f) continue;
+                // a done pixel's partial is computed and left unused
+                const float alpha = staged_alpha<true>(sh.s0[warp][j], sh.s1[warp][j], fpx, fpy);
                 const float4 col = sh.s2[warp][j];
                 const float wgt = alpha * Tk;
                 kr += col.x * wgt;
@@ -394,8 +512,7 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
                     while (mk) {
                         const int j = __ffs(mk) - 1;
                         mk &= mk - 1;
-                        const float alpha = staged_alpha(sh.s0[ks][j], sh.s1[ks][j], fpx, fpy);
-                        if (alpha == 0.0f) continue;
+                        const float alpha = staged_alpha<true>(sh.s0[ks][j], sh.s1[ks][j], fpx, fpy);
                         const float Tn = T * (1.0f - alpha);
                         if (Tn < 1e-4f) {
                             done = true;
@@ -426,7 +543,7 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
             }
             if (final_out && inside) out[(size_t)py * W + px] = make_float4(cr, cg, cb, 1.0f - T);
         }
-        __syncthreads();  // sh.item and the staging buffers are reused by the next item
+        __syncthreads();  // the item fields and the staging buffers are reused by the next item
     }
 }
 
@@ -460,6 +577,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_chunks(int tiles_x, int
 // state before that chunk (in work.state) and its index (work.stop) for the
 // fix-up pass; the others are final.
 __global__ void __launch_bounds__(kBlendThreads) k_blend_merge(int tiles_x, int W, int H,
+                                                               const uint2 *__restrict__ ranges,
                                                                float4 *__restrict__ out, BlendWork work) {
     const int slot = blockIdx.x;
     if (slot >= work.meta[0] || work.cand_done[slot]) return;
@@ -470,7 +588,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_merge(int tiles_x, int 
     float T = fabsf(s1.w), r = s1.x, gg = s1.y, b = s1.z;
     bool done = !g.inside || s1.w < 0.0f;
     int32_t stop = -1;
-    const uint32_t c0 = work.cand_chunk0[slot], c1 = work.cand_chunk0[slot + 1];
+    const uint2 rg = ranges[tile];
+    const uint32_t c0 = work.cand_chunk0[slot], c1 = c0 + (rg.y - rg.x - kBudget + kChunk - 1) / kChunk;
     // four chunks' partials loaded at a time (independent loads), applied in order
     for (uint32_t w0 = c0; w0 < c1 && !done; w0 += 4) {
         float4 pk[4];
@@ -525,73 +644,70 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W,
     if (mine && g.inside) out[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, 1.0f - px.T);
 }
 
-// Plan of the split: tiles with more than kBudget pairs get a slot and
-// ceil((n - kBudget) / kChunk) chunks (one block, deterministic scans).
-__global__ void __launch_bounds__(1024) k_blend_plan(int n_tiles, const uint2 *__restrict__ ranges,
-                                                     BlendWork work) {
-    __shared__ uint32_t tot_c, tot_k;
-    __shared__ uint32_t run_c, run_k;
+// Schedule key of a tile in pass 1 (larger first): its list length class
+// c = 1 + floor(log2 n), moved up by kPpTileShift for a tile item (one warp
+// composites each block's pairs in turn: a far longer dependency chain than
+// a block item's for the same n, and a CTA held for the whole tile); odd
+// keys are block items, even keys above 0 tile items, 0 empty tiles.
+// Longest chains first keeps the tail of the persistent grid short.  The
+// shift and the tile-item threshold were chosen by timing the 1080p
+// 3,500-instance frame (long lists) and the 4K 10,000-instance frame
+// (mostly mid-length lists).
+constexpr int kPpTileShift = 5;
+constexpr int kPpMaxClass = 23;
+static_assert(2 * kPpMaxClass + 1 < kBlendKeys && 2 * (kPpTileClass - 1 + kPpTileShift) < kBlendKeys, "schedule keys");
+__device__ __forceinline__ int blend_key(uint32_t n) {
+    if (n == 0u) return 0;
+    const int c = 1 + min(kPpMaxClass - 1, 31 - __clz((int)n));
+    return c >= kPpTileClass ? 2 * c + 1 : 2 * (c + kPpTileShift);
+}
+
+// Plan, part 1 (one thread per tile; meta zeroed before): tiles per
+// schedule key (warp-aggregated atomics), and a slot plus
+// ceil((n - kBudget) / kChunk) consecutive chunks for every tile with more
+// than kBudget pairs.  Slot and chunk numbers depend on the order of the
+// atomics; no result does (a tile's chunks are consecutive and merged in
+// order).
+__global__ void __launch_bounds__(256) k_blend_count(int n_tiles, const uint2 *__restrict__ ranges, BlendWork work) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    const uint32_t n = t < n_tiles ? ranges[t].y - ranges[t].x : 0u;
+    const int key = t < n_tiles ? blend_key(n) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(work.meta + kBlendCountAt + key, __popc(peers));
+    if (t >= n_tiles) return;
+    int slot = -1;
+    if (n > kBudget) {
+        const uint32_t nk = (n - kBudget + kChunk - 1) / kChunk;
+        slot = atomicAdd(work.meta + 0, 1);
+        const uint32_t c0 = atomicAdd(reinterpret_cast<unsigned *>(work.meta + 1), nk);
+        work.cand_tile[slot] = t;
+        work.cand_chunk0[slot] = c0;
+        work.cand_done[slot] = 1u;  // cleared by pass 1 unless every pixel is done
+        for (uint32_t c = 0; c < nk; ++c) work.chunk_slot[c0 + c] = slot;
+    }
+    work.cand_slot[t] = slot;
+}
+
+// Plan, part 2: pp_tile in decreasing schedule key (the order inside a key
+// is that of the atomics and affects no result).
+__global__ void __launch_bounds__(256) k_blend_order(int n_tiles, const uint2 *__restrict__ ranges, BlendWork work) {
+    __shared__ int first[kBlendKeys];
     if (threadIdx.x == 0) {
-        run_c = 0;
-        run_k = 0;
-    }
-    __syncthreads();
-    for (int base = 0; base < n_tiles; base += blockDim.x) {
-        const int t = base + threadIdx.x;
-        uint32_t n = 0;
-        if (t < n_tiles) n = ranges[t].y - ranges[t].x;
-        const uint32_t cand = n > kBudget ? 1u : 0u;
-        const uint32_t nk = cand ? (n - kBudget + kChunk - 1) / kChunk : 0u;
-        const uint32_t ec = block_exclusive_scan(cand, &tot_c);
-        const uint32_t ek = block_exclusive_scan(nk, &tot_k);
-        if (t < n_tiles) {
-            const int slot = cand ? (int)(run_c + ec) : -1;
-            work.cand_slot[t] = slot;
-            if (cand) {
-                work.cand_tile[slot] = t;
-                work.cand_chunk0[slot] = run_k + ek;
-                work.cand_done[slot] = 1u;  // cleared by pass 1 unless every pixel is done
-            }
+        int run = 0;
+        for (int k = kBlendKeys - 1; k >= 0; --k) {
+            first[k] = run;
+            run += work.meta[kBlendCountAt + k];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            run_c += tot_c;
-            run_k += tot_k;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        work.cand_chunk0[run_c] = run_k;
-        work.meta[0] = (int)run_c;
-        work.meta[1] = (int)run_k;
     }
     __syncthreads();
-    // slot of every chunk (the chunk kernels read it instead of searching)
-    for (uint32_t sl = threadIdx.x; sl < run_c; sl += blockDim.x)
-        for (uint32_t c = work.cand_chunk0[sl], c1 = work.cand_chunk0[sl + 1]; c < c1; ++c) work.chunk_slot[c] = (int)sl;
-    // pass-1 items, grouped by list length, longest first (the order inside
-    // a group does not affect any result): eight block items per tile with
-    // pairs, then one item per empty tile
-    constexpr int kClasses = 24;  // 0: empty; k >= 1: 2^(k-1) <= pairs < 2^k
-    __shared__ uint32_t ccount[kClasses], ccursor[kClasses];
-    if (threadIdx.x < kClasses) ccount[threadIdx.x] = 0u;
-    __syncthreads();
-    auto cls = [](uint32_t n) { return n == 0u ? 0 : 1 + min(kClasses - 2, 31 - __clz((int)n)); };
-    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&ccount[cls(ranges[t].y - ranges[t].x)], 1u);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int k = kClasses - 1; k >= 0; --k) {
-            ccursor[k] = run;
-            run += ccount[k];
-        }
-        work.meta[2] = (int)(run - ccount[0]);
-        work.meta[3] = 0;
-        work.meta[4] = (int)ccount[0];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
-        work.pp_tile[atomicAdd(&ccursor[cls(ranges[t].y - ranges[t].x)], 1u)] = t;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    const int key = t < n_tiles ? blend_key(ranges[t].y - ranges[t].x) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    int pos = 0;
+    if (key >= 0 && lane == leader) pos = atomicAdd(work.meta + kBlendCursorAt + key, __popc(peers));
+    pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & ((1u << lane) - 1u));
+    if (key >= 0) work.pp_tile[first[key] + pos] = t;
 }
 
 // Persistent grid of the pair-parallel pass: as many CTAs as fit on the
@@ -627,14 +743,17 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
         k_blend<2, kBlendThreads><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
         return 1;
     }
-    k_blend_plan<<<1, 1024, 0, st>>>(n, ranges, work);
-    // pass 1 of every tile: persistent CTAs, longest lists first
+    const unsigned tb = (unsigned)((n + 255) / 256);
+    if (cudaMemsetAsync(work.meta, 0, kBlendMetaWords * sizeof(int32_t), st) != cudaSuccess) return -1;
+    k_blend_count<<<tb, 256, 0, st>>>(n, ranges, work);
+    k_blend_order<<<tb, 256, 0, st>>>(n, ranges, work);
+    // pass 1 of every tile: persistent CTAs, longest chains first
     k_blend_pp<<<pp_grid(), kPpThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
-    const int launched = 2;
+    const int launched = 3;
     // no tile has pairs left after pass 1
     if (n_pairs <= kBudget) return launched;
     k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);
-    k_blend_merge<<<(unsigned)max_cand, kBlendThreads, 0, st>>>(tiles_x, W, H, out, work);
+    k_blend_merge<<<(unsigned)max_cand, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, out, work);
     k_blend_fix<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
     return launched + 3;
 }

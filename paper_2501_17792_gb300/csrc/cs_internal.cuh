@@ -311,10 +311,11 @@ int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cud
 // pixel state (r, g, b, T; T negated when saturated); per chunk, the chunk's
 // pixel composite (r, g, b, T; T negated when it met the stop rule); per
 // slot pixel, the chunk in which it meets the stop rule (-1 if none);
-// meta[0] = slots, meta[1] = chunks; pass 1 (plain frames): meta[2] =
-// tiles with pairs, meta[4] = empty tiles, meta[3] = the work counter of its
-// persistent CTAs; pp_tile lists the tiles with pairs, longest lists first
-// (by powers of two), then the empty ones.
+// meta[0] = slots, meta[1] = chunks, meta[3] = the work counter of the
+// persistent pass-1 CTAs (plain frames), meta[kBlendCountAt + k] = tiles of
+// schedule key k, meta[kBlendCursorAt + k] = their fill cursor (all zeroed
+// before the plan); pp_tile lists the tiles by decreasing schedule key, the
+// empty ones last.
 struct BlendWork {
     int32_t *cand_slot;
     int32_t *cand_tile;
@@ -335,7 +336,9 @@ struct BlendWork {
     int32_t *chunk_slot;  // [chunks]: the slot of each pass-2 chunk
     int32_t ox, oy;       // window origin: pixel (i, j) has its centre at (ox + i + 0.5, oy + j + 0.5)
 };
-constexpr int kBlendMetaWords = 8;
+constexpr int kBlendKeys = 64;  // schedule keys of pass 1 (see cs_blend.cu)
+constexpr int kBlendCountAt = 8, kBlendCursorAt = kBlendCountAt + kBlendKeys;
+constexpr int kBlendMetaWords = kBlendCursorAt + kBlendKeys;
 constexpr int kBlendBlockW = 8, kBlendBlockH = 4;  // pixels of one warp in a 16x16 tile
 constexpr uint32_t kBlendBudget = 32768;  // pairs composited by pass 1 per tile
 constexpr uint32_t kBlendChunk = 1024;   // pairs per pass-2 chunk
@@ -345,6 +348,8 @@ constexpr size_t blend_max_slots(size_t n_tiles, size_t n_pairs) {
 constexpr size_t blend_max_chunks(size_t n_tiles, size_t n_pairs) {
     return n_pairs / kBlendChunk + blend_max_slots(n_tiles, n_pairs) + 1;
 }
+// Returns the kernels launched, or -1 when the plan's counters could not be
+// cleared (the CUDA error is then cudaGetLastError's).
 int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, const uint32_t *pval,
                  const float4 *rec, float4 *out, const BlendWork &work, uint32_t n_pairs, cudaStream_t st);
 
