@@ -438,51 +438,65 @@ def run_sweep(args):
     duplicated to the paper's character counts on a 1.2 m grid starting 3 m
     from the camera, 1280x720, full detail (the paper's rows use a single
     template size).  Memory: the library always shares template attributes;
-    the unshared figure adds a template copy per extra character."""
+    the unshared figure adds a template copy per extra character.  One more
+    row per template size measures the plain (unshared) layout itself at the
+    largest character count the library can hold as separate templates
+    (CS_MAX_TEMPLATES = 63): every character its own uploaded copy."""
     import torch
     from paper_2501_17792_gb300 import binding, build
     from paper_2501_17792_gb300 import scene as S
     build.build()
     cam = S.look_camera((0.0, 1.6, 0.0), 10.0, 1280, 720)
     rows_out = []
+
+    def measure(tpls, tid, root, count):
+        r = binding.Renderer(device=0)
+        r.upload_templates(tpls)
+        out = torch.empty((720, 1280, 4), dtype=torch.float32, device="cuda")
+        fps = {}
+        dtid = torch.from_numpy(np.ascontiguousarray(tid, np.int32)).cuda()
+        droot = torch.from_numpy(np.ascontiguousarray(root.reshape(count, 12))).cuda()
+        for motion in (False, True):
+            poses = [torch.from_numpy(S.random_poses(100 + (f if motion else 0), count)).cuda()
+                     for f in range(args.steps + args.warmup)]
+            for f in range(args.warmup):
+                r.set_instances(dtid, droot, poses[f])
+                r.render(cam, out=out)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for f in range(args.warmup, args.warmup + args.steps):
+                r.set_instances(dtid, droot, poses[f])
+                r.render(cam, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            fps["motion" if motion else "static"] = args.steps / (e0.elapsed_time(e1) / 1e3)
+        _, st = r.render(cam, out=out, stats=True)
+        mem = r.memory_stats()
+        r.close()
+        return fps, st, (mem["total_bytes"] + out.numel() * 4) / 2 ** 20
+
     for n_gauss, cells in PAPER_TABLE2.items():
         tpl = S.make_template(1000, n_gauss, 3)
         tbytes = template_bytes(S.Scene([tpl], None, cam, S.single_lod(), ""))
-        for count in cells:
+        for count in list(cells) + [63]:
             cols = min(50, int(math.ceil(math.sqrt(count))))
             nrows = int(math.ceil(count / cols))
             inst = S.crowd_instances(1, cols, nrows)
             tid, root = inst.template_id[:count], inst.root[:count]
-            r = binding.Renderer(device=0)
-            r.upload_templates([tpl])
-            out = torch.empty((720, 1280, 4), dtype=torch.float32, device="cuda")
-            fps = {}
-            for motion in (False, True):
-                poses = [torch.from_numpy(S.random_poses(100 + (f if motion else 0), count)).cuda()
-                         for f in range(args.steps + args.warmup)]
-                dtid = torch.from_numpy(tid).cuda()
-                droot = torch.from_numpy(root.reshape(count, 12)).cuda()
-                for f in range(args.warmup):
-                    r.set_instances(dtid, droot, poses[f])
-                    r.render(cam, out=out)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for f in range(args.warmup, args.warmup + args.steps):
-                    r.set_instances(dtid, droot, poses[f])
-                    r.render(cam, out=out)
-                e1.record()
-                torch.cuda.synchronize()
-                fps["motion" if motion else "static"] = args.steps / (e0.elapsed_time(e1) / 1e3)
-            _, st = r.render(cam, out=out, stats=True)
-            mem = r.memory_stats()
-            r.close()
-            shared_mib = (mem["total_bytes"] + out.numel() * 4) / 2 ** 20
+            fps, st, shared_mib = measure([tpl], tid, root, count)
             row = dict(gaussians=n_gauss, characters=count, fps_static=round(fps["static"], 1),
                        fps_motion=round(fps["motion"], 1), splats=st["splats"], pairs=st["pairs"],
                        mem_shared_mib=round(shared_mib, 1),
                        mem_unshared_mib=round(shared_mib + (count - 1) * tbytes / 2 ** 20, 1),
                        paper_fps=PAPER_TABLE2[n_gauss].get(count), paper_mib=PAPER_TABLE1[n_gauss].get(count))
+            if count == 63:
+                # the plain layout measured: character k renders its own copy k
+                pfps, pst, plain_mib = measure([tpl] * count, np.arange(count, dtype=np.int32), root, count)
+                row.update(plain_measured=dict(fps_static=round(pfps["static"], 1),
+                                               fps_motion=round(pfps["motion"], 1),
+                                               mem_mib=round(plain_mib, 1), splats=pst["splats"],
+                                               pairs=pst["pairs"]))
             rows_out.append(row)
             print(json.dumps(row), flush=True)
     return rows_out
@@ -825,8 +839,10 @@ def main():
     ap.add_argument("--learned-lod", action="store_true",
                     help="learned vs distance LoD at 10,000 instances, 3840x2160 (one JSON line)")
     ap.add_argument("--lod-steps", type=int, default=1500, help="MLP training steps for --learned-lod")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="quarter crowd (875 instances, 960x540) for full ncu captures")
+    ap.add_argument("--profile-case", nargs="?", const="crowd540", default=None, choices=["crowd540", "lod4k"],
+                    help="frames for ncu captures: crowd540 (default) the quarter crowd, 875 instances at 960x540; "
+                         "lod4k the 10,000-instance 3840x2160 crowd at the learned LoD's equal-PSNR budget "
+                         "(levels 1 and 2 at 0.08 of their distance-LoD sizes)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.sweep:
@@ -844,8 +860,14 @@ def main():
     from paper_2501_17792_gb300 import scene as S
     if args.small:
         sc = S.crowd(n_templates=2, n_gauss=4096, cols=10, rows=10, width=640, height=360)
-    elif args.profile_case:
+    elif args.profile_case == "crowd540":
         sc = S.crowd(cols=25, rows=35, width=960, height=540)
+    elif args.profile_case == "lod4k":
+        base = S.paper_lod()
+        fr = np.asarray(base.fractions, np.float64) * np.array([1.0, 0.08, 0.08])
+        sc = S.crowd(cols=100, rows=100, width=3840, height=2160,
+                     lod=S.LodConfig(thresholds=base.thresholds, fractions=fr.astype(np.float32),
+                                     scale_mult=np.ones(3, np.float32)))
     else:
         sc = S.crowd()
     if args.impl == "reference":

@@ -311,6 +311,21 @@ int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size
  * CS_ERR_ARG for a NULL context. */
 int cs_debug_fail_allocs(cs_ctx *ctx, int32_t after);
 
+/* Testing hook for the compositing schedule of plain frames: mode
+ * CS_BLEND_ITEMS_AUTO (the default) composites every short tile list (under
+ * 4,096 pairs) as one work item of its own when the frame has many busy
+ * tiles (at least 8 per resident compositing CTA) and block by block
+ * otherwise; CS_BLEND_ITEMS_TILES and CS_BLEND_ITEMS_BLOCKS force one or the
+ * other for every frame of the context, so that small test frames exercise
+ * both.  The image is the same up to rounding order (both composite every
+ * pixel's pairs in depth order with the same stop rule).  The paper has no
+ * counterpart.  Returns CS_OK, or CS_ERR_ARG for a NULL context or an
+ * unknown mode. */
+#define CS_BLEND_ITEMS_AUTO 0
+#define CS_BLEND_ITEMS_TILES 1
+#define CS_BLEND_ITEMS_BLOCKS 2
+int cs_debug_blend_items(cs_ctx *ctx, int32_t mode);
+
 /* Library version string. */
 const char *cs_version(void);
 

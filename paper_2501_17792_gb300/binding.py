@@ -22,6 +22,7 @@ CS_OK, CS_ERR_ARG, CS_ERR_CUDA, CS_ERR_OOM, CS_ERR_CAPACITY, CS_ERR_TIMEOUT, CS_
 CS_SKIN_FULL, CS_SKIN_MEANS_ONLY = 0, 1
 CS_SH_ROOT_FRAME, CS_SH_WORLD_FRAME = 0, 1
 CS_STORE_FP32, CS_STORE_BF16 = 0, 1
+CS_BLEND_ITEMS_AUTO, CS_BLEND_ITEMS_TILES, CS_BLEND_ITEMS_BLOCKS = 0, 1, 2
 DBG = dict(skin_b=1, visible=2, groups=3, records=4, depth_keys=5, rects=6, depth_order=7,
            pair_tiles=8, pair_splats=9, tile_ranges=10)
 STAGES = ("fk", "cull_lod", "skin_project", "depth_sort", "pair_emit", "tile_sort", "tile_ranges",
@@ -92,6 +93,7 @@ SIGNATURES = {
     "cs_last_error": (C.c_char_p, [_P]),
     "cs_debug_read": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "cs_debug_fail_allocs": (C.c_int, [_P, C.c_int32]),
+    "cs_debug_blend_items": (C.c_int, [_P, C.c_int32]),
     "cs_version": (C.c_char_p, []),
     # ranked LoD (include/crowdsplat_lod.h)
     "cs_lod_features": (C.c_int, [_P, _P]),
@@ -377,6 +379,11 @@ class Renderer:
             raise ValueError(f"score has {s.shape[0]} entries, templates hold {self.n_gauss_total}")
         self._check(self.L.cs_lod_rank(self.h, s.data_ptr(), o.data_ptr()))
         return o
+
+    def debug_blend_items(self, mode: int) -> None:
+        """Testing hook: the compositing schedule of plain frames
+        (CS_BLEND_ITEMS_AUTO, _TILES or _BLOCKS; cs_debug_blend_items)."""
+        self._check(self.L.cs_debug_blend_items(self.h, int(mode)))
 
     def debug(self, which: str) -> np.ndarray:
         code = DBG[which]

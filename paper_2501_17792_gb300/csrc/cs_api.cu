@@ -40,6 +40,7 @@ struct cs_ctx {
     // allocation-failure injection (cs_debug_fail_allocs): -1 off, else the
     // number of allocations that still succeed before every one fails
     int fail_after = -1;
+    int blend_items = CS_BLEND_ITEMS_AUTO;  // cs_debug_blend_items
     int skin_mode = 0, sh_frame = 0, instance_cull = 1, stage_timing = 0;
     int storage = CS_STORE_FP32;  // template storage precision
     std::string err;
@@ -975,6 +976,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     bw.chunk_slot = ctx->bw_cslot.p;
     bw.ox = cp.ox;
     bw.oy = cp.oy;
+    bw.items = ctx->blend_items;
     if (contrib_tmpl) {
         CS_TRY(ensure(ctx, ctx->contrib_s, Sa, "splat contributions"));
         CS_CUDA(cudaMemsetAsync(ctx->contrib_s.p, 0, Sa * sizeof(float), st));
@@ -1260,6 +1262,14 @@ int cs_debug_fail_allocs(cs_ctx *ctx, int32_t after) {
     return CS_OK;
 }
 
+int cs_debug_blend_items(cs_ctx *ctx, int32_t mode) {
+    if (!ctx) return CS_ERR_ARG;
+    if (mode != CS_BLEND_ITEMS_AUTO && mode != CS_BLEND_ITEMS_TILES && mode != CS_BLEND_ITEMS_BLOCKS)
+        return fail(ctx, CS_ERR_ARG, "cs_debug_blend_items: unknown mode");
+    ctx->blend_items = mode;
+    return CS_OK;
+}
+
 int cs_debug_read(cs_ctx *ctx, int32_t which, void *host_dst, size_t bytes, size_t *size_out) {
     if (!ctx) return CS_ERR_ARG;
     CS_CUDA(cudaSetDevice(ctx->device));
@@ -1507,6 +1517,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     bw.chunk_slot = reinterpret_cast<int32_t *>(base + kOffBwCslot);
     bw.ox = cp.ox;
     bw.oy = cp.oy;
+    bw.items = ctx->blend_items;
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ranges, pval, rec, out, bw,
                              (uint32_t)P, st);
     CS_CUDA(cudaGetLastError());

@@ -39,6 +39,7 @@
 // their true T, so the stop rule holds exactly as in the definition.
 #include <algorithm>
 
+#include "crowdsplat.h"
 #include "cs_internal.cuh"
 
 namespace cs {
@@ -281,6 +282,73 @@ struct PpShared {
     int seg_item[kBlendKeys + 1], seg_tile[kBlendKeys + 1];  // first item and tile of each key, decreasing key
 };
 
+// List length class of a tile: 0 empty, else 1 + floor(log2 n) (capped).
+__device__ __forceinline__ int blend_class(uint32_t n) {
+    return n == 0u ? 0 : 1 + min(kBlendClasses - 2, 31 - __clz((int)n));
+}
+
+// Schedule key of a tile in pass 1 (larger first), from its class c: 2c + 1
+// for block items; for a tile item 2 (c + kPpTileShift), moved up because
+// one warp composites each block's pairs in turn (a far longer dependency
+// chain than a block item's for the same n, and a CTA held for the whole
+// tile); 0 for an empty tile.  Longest chains first keeps the tail of the
+// persistent grid short.  Tile items are used only in frames with at least
+// kPpTileItemsPerCta busy tiles per persistent CTA: with fewer, block items
+// keep more of the GPU busy and the frame is bound by its longest chains,
+// not by instruction issue.  The shift, the threshold class and the busy
+// tile count were chosen by timing the 1080p 3,500-instance frame (long
+// lists), the 4K 10,000-instance frame (mostly mid-length lists) and
+// 1280x720 frames of 1 to 5,000 characters.
+constexpr int kPpTileShift = 5;
+constexpr int kPpTileItemsPerCta = 8;
+static_assert(2 * (kBlendClasses - 1) + 1 < kBlendKeys && 2 * (kPpTileClass - 1 + kPpTileShift) < kBlendKeys,
+              "schedule keys");
+__device__ __forceinline__ int blend_key(int c, bool tiles) {
+    return c == 0 ? 0 : (tiles && c < kPpTileClass ? 2 * (c + kPpTileShift) : 2 * c + 1);
+}
+
+// Class of the tiles of schedule key k, or -1 when no class maps to it.
+__device__ __forceinline__ int key_class(int k, bool tiles) {
+    if (k == 0) return 0;
+    if (k & 1) {
+        const int c = (k - 1) >> 1;
+        return c >= 1 && c < kBlendClasses && (!tiles || c >= kPpTileClass) ? c : -1;
+    }
+    const int c = (k >> 1) - kPpTileShift;
+    return tiles && c >= 1 && c < kPpTileClass ? c : -1;
+}
+
+// Segments of the schedule in decreasing key, scanned by one warp (two keys
+// per lane): segment s = key kBlendKeys - 1 - s starts at tile seg_tile[s]
+// of pp_tile and at item seg_item[s] (kPpBlocks items per tile for odd keys,
+// block items; one otherwise); entry kBlendKeys holds the totals.  Returns
+// whether the frame uses tile items (the same answer in every CTA; forced
+// by `items` unless CS_BLEND_ITEMS_AUTO).
+static_assert(kBlendKeys == 64 && kBlendClasses <= 32, "one warp: two schedule keys, one class per lane");
+__device__ __forceinline__ bool key_segments(const int32_t *__restrict__ meta, int ctas, int items, int *seg_item,
+                                             int *seg_tile) {
+    const int lane = threadIdx.x & 31, s0 = 2 * lane, k0 = kBlendKeys - 1 - s0, k1 = k0 - 1;
+    int busy = lane >= 1 && lane < kBlendClasses ? meta[kBlendCountAt + lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) busy += __shfl_xor_sync(0xffffffffu, busy, o);
+    const bool tiles = items == CS_BLEND_ITEMS_TILES || (items == CS_BLEND_ITEMS_AUTO && busy >= kPpTileItemsPerCta * ctas);
+    const int q0 = key_class(k0, tiles), q1 = key_class(k1, tiles);
+    const int c0 = q0 >= 0 ? meta[kBlendCountAt + q0] : 0, c1 = q1 >= 0 ? meta[kBlendCountAt + q1] : 0;
+    const int i0 = (k0 & 1) ? c0 * kPpBlocks : c0, i1 = (k1 & 1) ? c1 * kPpBlocks : c1;
+    const int ii = (int)warp_inclusive_scan((uint32_t)(i0 + i1));
+    const int it = (int)warp_inclusive_scan((uint32_t)(c0 + c1));
+    if (seg_item) {
+        seg_item[s0] = ii - i0 - i1;
+        seg_item[s0 + 1] = ii - i1;
+        if (lane == 31) seg_item[kBlendKeys] = ii;
+    }
+    seg_tile[s0] = it - c0 - c1;
+    seg_tile[s0 + 1] = it - c1;
+    if (lane == 31) seg_tile[kBlendKeys] = it;
+    __syncwarp();
+    return tiles;
+}
+
 // alpha of a staged splat at a pixel centre; 0 when the splat does not
 // contribute there (outside its support box, q > 0, alpha < 1/255).  The
 // same arithmetic as composite_range.  kBranchFree evaluates every test
@@ -311,20 +379,8 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
                                                          BlendWork work) {
     __shared__ PpShared sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // items in decreasing schedule key: per key, its tiles times kPpBlocks
-    // (odd keys: block items) or times 1
-    if (threadIdx.x == 0) {
-        int ri = 0, rt = 0;
-        for (int s = 0; s < kBlendKeys; ++s) {
-            const int key = kBlendKeys - 1 - s, cnt = work.meta[kBlendCountAt + key];
-            sh.seg_item[s] = ri;
-            sh.seg_tile[s] = rt;
-            ri += (key & 1) ? cnt * kPpBlocks : cnt;
-            rt += cnt;
-        }
-        sh.seg_item[kBlendKeys] = ri;
-        sh.seg_tile[kBlendKeys] = rt;
-    }
+    // items in decreasing schedule key
+    if (warp == 0) key_segments(work.meta, gridDim.x, work.items, sh.seg_item, sh.seg_tile);
     for (;;) {
         if (threadIdx.x == 0) {
             const int item = (int)atomicAdd(reinterpret_cast<unsigned *>(work.meta + 3), 1u);
@@ -644,26 +700,8 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W,
     if (mine && g.inside) out[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, 1.0f - px.T);
 }
 
-// Schedule key of a tile in pass 1 (larger first): its list length class
-// c = 1 + floor(log2 n), moved up by kPpTileShift for a tile item (one warp
-// composites each block's pairs in turn: a far longer dependency chain than
-// a block item's for the same n, and a CTA held for the whole tile); odd
-// keys are block items, even keys above 0 tile items, 0 empty tiles.
-// Longest chains first keeps the tail of the persistent grid short.  The
-// shift and the tile-item threshold were chosen by timing the 1080p
-// 3,500-instance frame (long lists) and the 4K 10,000-instance frame
-// (mostly mid-length lists).
-constexpr int kPpTileShift = 5;
-constexpr int kPpMaxClass = 23;
-static_assert(2 * kPpMaxClass + 1 < kBlendKeys && 2 * (kPpTileClass - 1 + kPpTileShift) < kBlendKeys, "schedule keys");
-__device__ __forceinline__ int blend_key(uint32_t n) {
-    if (n == 0u) return 0;
-    const int c = 1 + min(kPpMaxClass - 1, 31 - __clz((int)n));
-    return c >= kPpTileClass ? 2 * c + 1 : 2 * (c + kPpTileShift);
-}
-
-// Plan, part 1 (one thread per tile; meta zeroed before): tiles per
-// schedule key (warp-aggregated atomics), and a slot plus
+// Plan, part 1 (one thread per tile; meta zeroed before): tiles per list
+// length class (warp-aggregated atomics), and a slot plus
 // ceil((n - kBudget) / kChunk) consecutive chunks for every tile with more
 // than kBudget pairs.  Slot and chunk numbers depend on the order of the
 // atomics; no result does (a tile's chunks are consecutive and merged in
@@ -671,9 +709,9 @@ __device__ __forceinline__ int blend_key(uint32_t n) {
 __global__ void __launch_bounds__(256) k_blend_count(int n_tiles, const uint2 *__restrict__ ranges, BlendWork work) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
     const uint32_t n = t < n_tiles ? ranges[t].y - ranges[t].x : 0u;
-    const int key = t < n_tiles ? blend_key(n) : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(work.meta + kBlendCountAt + key, __popc(peers));
+    const int cls = t < n_tiles ? blend_class(n) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, cls);
+    if (cls >= 0 && lane == __ffs(peers) - 1) atomicAdd(work.meta + kBlendCountAt + cls, __popc(peers));
     if (t >= n_tiles) return;
     int slot = -1;
     if (n > kBudget) {
@@ -690,24 +728,23 @@ __global__ void __launch_bounds__(256) k_blend_count(int n_tiles, const uint2 *_
 
 // Plan, part 2: pp_tile in decreasing schedule key (the order inside a key
 // is that of the atomics and affects no result).
-__global__ void __launch_bounds__(256) k_blend_order(int n_tiles, const uint2 *__restrict__ ranges, BlendWork work) {
-    __shared__ int first[kBlendKeys];
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int k = kBlendKeys - 1; k >= 0; --k) {
-            first[k] = run;
-            run += work.meta[kBlendCountAt + k];
-        }
+__global__ void __launch_bounds__(256) k_blend_order(int n_tiles, const uint2 *__restrict__ ranges, int pp_ctas,
+                                                     BlendWork work) {
+    __shared__ int seg_tile[kBlendKeys + 1];  // first tile of key kBlendKeys - 1 - s
+    __shared__ bool tiles;
+    if (threadIdx.x < 32) {
+        const bool t_ = key_segments(work.meta, pp_ctas, work.items, nullptr, seg_tile);
+        if (threadIdx.x == 0) tiles = t_;
     }
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-    const int key = t < n_tiles ? blend_key(ranges[t].y - ranges[t].x) : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int cls = t < n_tiles ? blend_class(ranges[t].y - ranges[t].x) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, cls);
     const int leader = __ffs(peers) - 1;
     int pos = 0;
-    if (key >= 0 && lane == leader) pos = atomicAdd(work.meta + kBlendCursorAt + key, __popc(peers));
+    if (cls >= 0 && lane == leader) pos = atomicAdd(work.meta + kBlendCursorAt + cls, __popc(peers));
     pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & ((1u << lane) - 1u));
-    if (key >= 0) work.pp_tile[first[key] + pos] = t;
+    if (cls >= 0) work.pp_tile[seg_tile[kBlendKeys - 1 - blend_key(cls, tiles)] + pos] = t;
 }
 
 // Persistent grid of the pair-parallel pass: as many CTAs as fit on the
@@ -746,9 +783,10 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
     const unsigned tb = (unsigned)((n + 255) / 256);
     if (cudaMemsetAsync(work.meta, 0, kBlendMetaWords * sizeof(int32_t), st) != cudaSuccess) return -1;
     k_blend_count<<<tb, 256, 0, st>>>(n, ranges, work);
-    k_blend_order<<<tb, 256, 0, st>>>(n, ranges, work);
+    const unsigned grid = pp_grid();
+    k_blend_order<<<tb, 256, 0, st>>>(n, ranges, (int)grid, work);
     // pass 1 of every tile: persistent CTAs, longest chains first
-    k_blend_pp<<<pp_grid(), kPpThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+    k_blend_pp<<<grid, kPpThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
     const int launched = 3;
     // no tile has pairs left after pass 1
     if (n_pairs <= kBudget) return launched;

@@ -312,10 +312,10 @@ int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cud
 // pixel composite (r, g, b, T; T negated when it met the stop rule); per
 // slot pixel, the chunk in which it meets the stop rule (-1 if none);
 // meta[0] = slots, meta[1] = chunks, meta[3] = the work counter of the
-// persistent pass-1 CTAs (plain frames), meta[kBlendCountAt + k] = tiles of
-// schedule key k, meta[kBlendCursorAt + k] = their fill cursor (all zeroed
-// before the plan); pp_tile lists the tiles by decreasing schedule key, the
-// empty ones last.
+// persistent pass-1 CTAs (plain frames), meta[kBlendCountAt + c] = tiles of
+// list length class c, meta[kBlendCursorAt + c] = their fill cursor (all
+// zeroed before the plan); pp_tile lists the tiles by decreasing schedule
+// key, the empty ones last.
 struct BlendWork {
     int32_t *cand_slot;
     int32_t *cand_tile;
@@ -335,10 +335,12 @@ struct BlendWork {
     int32_t *pp_tile;     // [tiles]
     int32_t *chunk_slot;  // [chunks]: the slot of each pass-2 chunk
     int32_t ox, oy;       // window origin: pixel (i, j) has its centre at (ox + i + 0.5, oy + j + 0.5)
+    int32_t items;        // pass-1 schedule: CS_BLEND_ITEMS_AUTO, _TILES or _BLOCKS
 };
-constexpr int kBlendKeys = 64;  // schedule keys of pass 1 (see cs_blend.cu)
-constexpr int kBlendCountAt = 8, kBlendCursorAt = kBlendCountAt + kBlendKeys;
-constexpr int kBlendMetaWords = kBlendCursorAt + kBlendKeys;
+constexpr int kBlendKeys = 64;     // schedule keys of pass 1 (see cs_blend.cu)
+constexpr int kBlendClasses = 24;  // list length classes: 0 empty, c: 2^(c-1) <= n < 2^c (last: n >= 2^22)
+constexpr int kBlendCountAt = 8, kBlendCursorAt = kBlendCountAt + kBlendClasses;
+constexpr int kBlendMetaWords = kBlendCursorAt + kBlendClasses;
 constexpr int kBlendBlockW = 8, kBlendBlockH = 4;  // pixels of one warp in a 16x16 tile
 constexpr uint32_t kBlendBudget = 32768;  // pairs composited by pass 1 per tile
 constexpr uint32_t kBlendChunk = 1024;   // pairs per pass-2 chunk

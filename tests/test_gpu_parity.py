@@ -49,10 +49,12 @@ def render(r, sc, stats=False):
     return out.cpu().numpy()
 
 
-def full_check(sc, *, skin_mode=0, sh_frame=0, label="", max_boundary=0.08, subsets=None, **kw):
+def full_check(sc, *, skin_mode=0, sh_frame=0, label="", max_boundary=0.08, subsets=None, blend_items=None, **kw):
     r = make(sc, skin_mode=skin_mode, sh_frame=sh_frame, **kw)
     for (t, l), idx in (subsets or {}).items():
         r.set_lod_subset(t, l, idx)
+    if blend_items is not None:
+        r.debug_blend_items(blend_items)
     img, st = render(r, sc, stats=True)
     os_ = oracle.OracleScene(sc, skin_mode=skin_mode, sh_frame=sh_frame, subsets=subsets)
     errs = PU.compare_splats(r, sc, os_)
@@ -310,6 +312,35 @@ def test_pair_parallel_pass_on_mid_length_lists():
     assert counts.min() > 1024 and counts.max() <= 32768, counts
     A = ref["rgba"][..., 3]
     assert (A < 0.999).mean() > 0.05 and (A > 0.9998).mean() > 0.3
+
+
+def test_tile_items_and_block_items_match_the_oracle():
+    """Plain-frame compositing with every short list (under 4,096 pairs) as
+    one whole-tile item (warp w walks block w's pairs in depth order), and
+    with every list block by block (eight sub-range partials chained per
+    round), each forced by the testing hook on a field whose density falls
+    from left to right: lists from a few pairs to past the tile-item limit,
+    ragged right and bottom tiles, pixels saturating at all depths.  Both
+    match the oracle, and each other up to rounding order."""
+    from paper_2501_17792_gb300 import binding
+    rng = np.random.default_rng(23)
+    n, w, h, f = 24000, 88, 40, 60.0
+    z = rng.uniform(2.0, 6.0, n)
+    px, py = w * rng.random(n) ** 3, rng.uniform(0, h, n)
+    s = (2.0 * z / f)[:, None] * np.exp(rng.normal(0, 0.3, (n, 3)))
+    tpl = U.template_from(np.stack([(px - w / 2) * z / f, (py - h / 2) * z / f, z], 1), s,
+                          rng.standard_normal((n, 4)), rng.uniform(0.01, 0.03, n), 0.3 * rng.standard_normal((n, 4, 3)))
+    sc = U.scene_of([tpl], U.instances(1), U.identity_camera(w, h, f))
+    imgs = {}
+    for mode in (binding.CS_BLEND_ITEMS_TILES, binding.CS_BLEND_ITEMS_BLOCKS):
+        r, imgs[mode], ref, errs, st = full_check(sc, label=f"schedule_{mode}", max_boundary=0.2, blend_items=mode)
+        rg = r.debug("tile_ranges").astype(np.int64)
+        counts = rg[:, 1] - rg[:, 0]
+        assert counts.min() < 1024 and ((counts >= 1024) & (counts < 4096)).sum() >= 8 and counts.max() >= 4096, counts
+    d = np.abs(imgs[binding.CS_BLEND_ITEMS_TILES] - imgs[binding.CS_BLEND_ITEMS_BLOCKS])
+    assert d.max() <= PU.TOL_MAX_ABS and np.median(d) <= 1e-6, (d.max(), np.median(d))
+    with pytest.raises(binding.CrowdSplatError):
+        r.debug_blend_items(7)
 
 
 @pytest.mark.parametrize("spread", [0.012, 0.0])
