@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
     extern __shared__ uint8_t grp[];  // [n_inst] group of each instance
     __shared__ int32_t gcount[kMaxTemplates * kMaxLevels];
     __shared__ int32_t gslot[kMaxTemplates * kMaxLevels];
+    __shared__ int32_t wcount[kCullThreads / 32][kMaxTemplates * kMaxLevels];  // per warp and group
     __shared__ uint32_t zlo_bits, zhi_bits;
     const int L = lod.n_levels;
     const int n_grp = n_tpl * L;
@@ -130,72 +131,84 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
     }
     __syncthreads();
 
-    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
-        const float *rt = root + (size_t)i * 12;
-        float Rr[9] = {rt[0], rt[1], rt[2], rt[4], rt[5], rt[6], rt[8], rt[9], rt[10]};
-        float tr[3] = {rt[3], rt[7], rt[11]};
-        // distance band: number of thresholds <= distance (CrowdSplat Sec. 2)
-        float dx = tr[0] - cam.center[0], dy = tr[1] - cam.center[1], dz = tr[2] - cam.center[2];
-        float d = sqrtf(dx * dx + dy * dy + dz * dz);
-        int lvl = 0;
-        for (int k = 0; k < L - 1; ++k) lvl += (d >= lod.thresh[k]) ? 1 : 0;
-        // V = camera o root
-        float Vm[12];
+    for (int i0 = 0; i0 < n_inst; i0 += blockDim.x) {
+        // every lane runs every round (the depth range is reduced per warp)
+        const int i = i0 + threadIdx.x;
+        uint32_t zl_bits = 0x7F7FFFFFu, zh_bits = 0u;
+        if (i < n_inst) {
+            const float *rt = root + (size_t)i * 12;
+            float Rr[9] = {rt[0], rt[1], rt[2], rt[4], rt[5], rt[6], rt[8], rt[9], rt[10]};
+            float tr[3] = {rt[3], rt[7], rt[11]};
+            // distance band: number of thresholds <= distance (CrowdSplat Sec. 2)
+            float dx = tr[0] - cam.center[0], dy = tr[1] - cam.center[1], dz = tr[2] - cam.center[2];
+            float d = sqrtf(dx * dx + dy * dy + dz * dz);
+            int lvl = 0;
+            for (int k = 0; k < L - 1; ++k) lvl += (d >= lod.thresh[k]) ? 1 : 0;
+            // V = camera o root
+            float Vm[12];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
+            for (int r = 0; r < 3; ++r) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                Vm[r * 4 + c] = cam.R[r * 3 + 0] * Rr[0 * 3 + c] + cam.R[r * 3 + 1] * Rr[1 * 3 + c] +
-                                cam.R[r * 3 + 2] * Rr[2 * 3 + c];
-            Vm[r * 4 + 3] = cam.R[r * 3 + 0] * tr[0] + cam.R[r * 3 + 1] * tr[1] +
-                            cam.R[r * 3 + 2] * tr[2] + cam.t[r];
-        }
-        float4 *vo = reinterpret_cast<float4 *>(V + (size_t)i * 12);
-        vo[0] = make_float4(Vm[0], Vm[1], Vm[2], Vm[3]);
-        vo[1] = make_float4(Vm[4], Vm[5], Vm[6], Vm[7]);
-        vo[2] = make_float4(Vm[8], Vm[9], Vm[10], Vm[11]);
-        // camera centre in the root frame: Rr^T (c - t)
-        float e0 = -dx, e1 = -dy, e2 = -dz;
-        reinterpret_cast<float4 *>(Cloc)[i] =
-            make_float4(Rr[0] * e0 + Rr[3] * e1 + Rr[6] * e2, Rr[1] * e0 + Rr[4] * e1 + Rr[7] * e2,
-                        Rr[2] * e0 + Rr[5] * e1 + Rr[8] * e2, 0.0f);
-        int t = tid[i];
-        bool visible = t >= 0 && t < n_tpl;  // out-of-range ids (device input) are hidden
-        if (do_cull && visible) {
-            const TemplateInfo &T = tpls[t];
-            // bounding sphere: centre = pelvis rest position (posed local
-            // means stay within reach of it), grown by the splat support
-            float px = T.rest[0], py = T.rest[1], pz = T.rest[2];
-            float cxs = Vm[0] * px + Vm[1] * py + Vm[2] * pz + Vm[3];
-            float cys = Vm[4] * px + Vm[5] * py + Vm[6] * pz + Vm[7];
-            float czs = Vm[8] * px + Vm[9] * py + Vm[10] * pz + Vm[11];
-            float reach = T.reach[lvl] * 1.0001f + 1e-4f;
-            float grow = reach + cam.cull_sigma_k * T.sigma_max[lvl] + 1e-3f;
-            if (czs + reach <= cam.near_z) visible = false;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                float s = cam.plane[p][0] * cxs + cam.plane[p][1] * cys + cam.plane[p][2] * czs;
-                if (s > grow) visible = false;
+                for (int c = 0; c < 3; ++c)
+                    Vm[r * 4 + c] = cam.R[r * 3 + 0] * Rr[0 * 3 + c] + cam.R[r * 3 + 1] * Rr[1 * 3 + c] +
+                                    cam.R[r * 3 + 2] * Rr[2 * 3 + c];
+                Vm[r * 4 + 3] = cam.R[r * 3 + 0] * tr[0] + cam.R[r * 3 + 1] * tr[1] +
+                                cam.R[r * 3 + 2] * tr[2] + cam.t[r];
             }
+            float4 *vo = reinterpret_cast<float4 *>(V + (size_t)i * 12);
+            vo[0] = make_float4(Vm[0], Vm[1], Vm[2], Vm[3]);
+            vo[1] = make_float4(Vm[4], Vm[5], Vm[6], Vm[7]);
+            vo[2] = make_float4(Vm[8], Vm[9], Vm[10], Vm[11]);
+            // camera centre in the root frame: Rr^T (c - t)
+            float e0 = -dx, e1 = -dy, e2 = -dz;
+            reinterpret_cast<float4 *>(Cloc)[i] =
+                make_float4(Rr[0] * e0 + Rr[3] * e1 + Rr[6] * e2, Rr[1] * e0 + Rr[4] * e1 + Rr[7] * e2,
+                            Rr[2] * e0 + Rr[5] * e1 + Rr[8] * e2, 0.0f);
+            int t = tid[i];
+            bool visible = t >= 0 && t < n_tpl;  // out-of-range ids (device input) are hidden
+            if (do_cull && visible) {
+                const TemplateInfo &T = tpls[t];
+                // bounding sphere: centre = pelvis rest position (posed local
+                // means stay within reach of it), grown by the splat support
+                float px = T.rest[0], py = T.rest[1], pz = T.rest[2];
+                float cxs = Vm[0] * px + Vm[1] * py + Vm[2] * pz + Vm[3];
+                float cys = Vm[4] * px + Vm[5] * py + Vm[6] * pz + Vm[7];
+                float czs = Vm[8] * px + Vm[9] * py + Vm[10] * pz + Vm[11];
+                float reach = T.reach[lvl] * 1.0001f + 1e-4f;
+                float grow = reach + cam.cull_sigma_k * T.sigma_max[lvl] + 1e-3f;
+                if (czs + reach <= cam.near_z) visible = false;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    float s = cam.plane[p][0] * cxs + cam.plane[p][1] * cys + cam.plane[p][2] * czs;
+                    if (s > grow) visible = false;
+                }
+            }
+            if (visible) {
+                // view-depth interval of the instance's splat means: a mean p
+                // lies within reach of the pelvis rest position c (instance
+                // frame), so its depth is within |v| reach of v.c + t_z, v the
+                // depth row of camera o root (Cauchy-Schwarz); widened for
+                // rounding and clipped below at the near plane
+                const TemplateInfo &T = tpls[t];
+                const float czs = Vm[8] * T.rest[0] + Vm[9] * T.rest[1] + Vm[10] * T.rest[2] + Vm[11];
+                const float vn = sqrtf(Vm[8] * Vm[8] + Vm[9] * Vm[9] + Vm[10] * Vm[10]);
+                const float ext = T.reach[lvl] * vn * 1.001f + 1e-3f;
+                const float zl = fmaxf(cam.near_z, (czs - ext) * 0.999f - 1e-3f);
+                const float zh = fmaxf(cam.near_z, (czs + ext) * 1.001f + 1e-3f);
+                zl_bits = __float_as_uint(zl);  // positive floats order as their bits
+                zh_bits = __float_as_uint(zh);
+            }
+            uint8_t g = visible ? (uint8_t)(t * L + lvl) : kHidden;
+            grp[i] = g;
+            if (visible) atomicAdd(&gcount[g], 1);
         }
-        if (visible) {
-            // view-depth interval of the instance's splat means: a mean p
-            // lies within reach of the pelvis rest position c (instance
-            // frame), so its depth is within |v| reach of v.c + t_z, v the
-            // depth row of camera o root (Cauchy-Schwarz); widened for
-            // rounding and clipped below at the near plane
-            const TemplateInfo &T = tpls[t];
-            const float czs = Vm[8] * T.rest[0] + Vm[9] * T.rest[1] + Vm[10] * T.rest[2] + Vm[11];
-            const float vn = sqrtf(Vm[8] * Vm[8] + Vm[9] * Vm[9] + Vm[10] * Vm[10]);
-            const float ext = T.reach[lvl] * vn * 1.001f + 1e-3f;
-            const float zl = fmaxf(cam.near_z, (czs - ext) * 0.999f - 1e-3f);
-            const float zh = fmaxf(cam.near_z, (czs + ext) * 1.001f + 1e-3f);
-            atomicMin(&zlo_bits, __float_as_uint(zl));  // positive floats order as their bits
-            atomicMax(&zhi_bits, __float_as_uint(zh));
+        // one shared atomic per warp instead of one per visible instance
+        zl_bits = __reduce_min_sync(0xffffffffu, zl_bits);
+        zh_bits = __reduce_max_sync(0xffffffffu, zh_bits);
+        if ((threadIdx.x & 31) == 0) {
+            if (zl_bits != 0x7F7FFFFFu) atomicMin(&zlo_bits, zl_bits);
+            if (zh_bits != 0u) atomicMax(&zhi_bits, zh_bits);
         }
-        uint8_t g = visible ? (uint8_t)(t * L + lvl) : kHidden;
-        grp[i] = g;
-        if (visible) atomicAdd(&gcount[g], 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -231,18 +244,32 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
         meta[kMetaZhi] = (int32_t)zhi_bits;
     }
     __syncthreads();
-    // stable placement: one warp per group sweeps the instances in order
+    // stable placement, one round of kCullThreads instances at a time: an
+    // instance goes to its group's slot plus the instances of its group in
+    // earlier rounds (gslot runs on), in earlier warps of the round (a scan
+    // of the per-warp counts) and in earlier lanes of its warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int g = warp; g < n_grp; g += kCullThreads / 32) {
-        if (gcount[g] == 0) continue;
-        int pos = gslot[g];
-        for (int base = 0; base < n_inst; base += 32) {
-            int i = base + lane;
-            bool hit = i < n_inst && grp[i] == g;
-            unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (hit) vis[pos + __popc(m & ((1u << lane) - 1u))] = i;
-            pos += __popc(m);
+    for (int i0 = 0; i0 < n_inst; i0 += kCullThreads) {
+        const int i = i0 + threadIdx.x;
+        const int g = i < n_inst ? grp[i] : kHidden;
+        const unsigned peers = __match_any_sync(0xffffffffu, g);
+        for (int k = lane; k < n_grp; k += 32) wcount[warp][k] = 0;
+        __syncwarp();
+        if (g != kHidden && lane == __ffs(peers) - 1) wcount[warp][g] = __popc(peers);
+        __syncthreads();
+        for (int k = threadIdx.x; k < n_grp; k += kCullThreads) {
+            int run = gslot[k];
+#pragma unroll 8
+            for (int w = 0; w < kCullThreads / 32; ++w) {
+                const int c = wcount[w][k];
+                wcount[w][k] = run;
+                run += c;
+            }
+            gslot[k] = run;
         }
+        __syncthreads();
+        if (g != kHidden) vis[wcount[warp][g] + __popc(peers & ((1u << lane) - 1u))] = i;
+        __syncthreads();  // wcount and gslot are rewritten by the next round
     }
 }
 
@@ -251,15 +278,14 @@ int launch_cull_group(int n_inst, int n_tpl, const int32_t *tid, const float *ro
                        int do_cull, float *V, float *Cloc, int32_t *vis, Group *groups,
                        int32_t *meta, cudaStream_t st) {
     size_t smem = (size_t)(n_inst > 0 ? n_inst : 1);
-    if (smem > 48 * 1024) {
-        static int configured_device = -1;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (configured_device != dev) {
-            cudaFuncSetAttribute(k_cull_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 CS_MAX_INSTANCES_BYTES);
-            configured_device = dev;
-        }
+    // the group bytes (dynamic) and the per-warp group counts (static,
+    // 32 KB) exceed the default 48 KB from about 14,000 instances on
+    static int configured_device = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_device != dev) {
+        cudaFuncSetAttribute(k_cull_group, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_MAX_INSTANCES_BYTES);
+        configured_device = dev;
     }
     k_cull_group<<<1, kCullThreads, smem, st>>>(n_inst, n_tpl, tid, root, tpls, cam, lod, do_cull,
                                                 V, Cloc, vis, groups, meta);

@@ -188,6 +188,43 @@ def test_means_only_and_world_frame_modes():
     full_check(sc, sh_frame=1, label="world_frame_sh")
 
 
+def test_grouping_is_stable_at_the_instance_limit():
+    """CS_MAX_INSTANCES instances of three templates at three LoD bands,
+    instance culling off: the visible list is every instance, grouped by
+    (template, level) in that order and ascending inside each group, and
+    each group's slots, sizes and first splat follow from the counts."""
+    from paper_2501_17792_gb300 import binding
+    n, L = 131072, 3
+    rng = np.random.default_rng(41)
+    tpls = [U.random_small_scene(50 + t, n_gauss=32, n_inst=1, sh_degree=0).templates[0] for t in range(3)]
+    tid = (rng.permutation(n) % 3).astype(np.int32)
+    z = np.array([3.0, 7.0, 14.0])[rng.integers(0, 3, n)]  # far from the 5 m and 10 m thresholds
+    roots = np.tile(np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], np.float32), (n, 1, 1))
+    roots[:, 0, 3] = rng.uniform(-0.4, 0.4, n) * z / 3.0
+    roots[:, 1, 3] = rng.uniform(-0.3, 0.3, n) * z / 3.0
+    roots[:, 2, 3] = z
+    lod = S.LodConfig(thresholds=np.array([5.0, 10.0], np.float32), fractions=np.array([1.0, 0.5, 0.25], np.float32),
+                      scale_mult=np.ones(3, np.float32))
+    sc = U.scene_of(tpls, U.instances(n, roots=roots, template_id=tid), U.identity_camera(96, 64, 60.0), lod=lod)
+    r = make(sc, instance_cull=False)
+    img, st = render(r, sc, stats=True)
+    assert np.isfinite(img).all() and st["instances_visible"] == n
+    lvl = np.searchsorted(np.array([5.0, 10.0]), z, side="right")
+    vis, groups = r.debug("visible"), r.debug("groups")
+    want, slot, splat, rows = [], 0, 0, []
+    for t in range(3):
+        for l in range(L):
+            ids = np.flatnonzero((tid == t) & (lvl == l))
+            if ids.size:
+                ng = int(round(32 * [1.0, 0.5, 0.25][l]))
+                rows.append((t, l, slot, ids.size, ng, splat))
+                want.append(ids)
+                slot += ids.size
+                splat += ids.size * ng
+    assert np.array_equal(vis, np.concatenate(want))
+    assert np.array_equal(groups[:, :6], np.array(rows)), (groups[:, :6], rows)
+
+
 def test_instance_cull_never_changes_the_image():
     sc = S.crowd(n_templates=4, n_gauss=2048, sh_degree=1, cols=50, rows=70, width=480, height=270)
     a, sa = render(make(sc, instance_cull=True), sc, stats=True)
