@@ -443,23 +443,57 @@ __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *
 // takes the kScanTile splats from b kScanTile in depth order, in kScanItems
 // rounds of kScanThreads consecutive splats (one per thread, coalesced); its
 // offset comes from the scanned block sums, each round is scanned in the
-// block, so no per-splat offset array is written or read.
+// block, so no per-splat offset array is written or read.  A splat whose
+// tiles fit a 3x3 window (at most nine pairs) is written by its thread; a
+// larger one is queued in shared memory and written by a whole warp, lane l
+// taking its tiles l, l + 32, ... in row-major order (coalesced stores, no
+// warp waiting on one lane's long loop): exactly the pairs emit_splat_pairs
+// writes.
 __global__ void __launch_bounds__(kScanThreads) k_emit_pairs_scan(uint32_t n, const uint32_t *__restrict__ order,
                                                                  const uint32_t *__restrict__ bins,
                                                                  const uint32_t *__restrict__ sums,
                                                                  const float4 *__restrict__ rec, int tiles_x,
                                                                  uint16_t *__restrict__ ptile,
                                                                  uint32_t *__restrict__ pval) {
-    __shared__ uint32_t total;
+    __shared__ uint32_t total, n_large;
+    __shared__ uint4 s_large[kScanThreads];  // splat id, first pair, tile x0 | y0 << 16, tiles per row
+    __shared__ uint32_t s_cnt[kScanThreads];  // its pairs
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     uint32_t carry = sums[blockIdx.x];
+    if (t == 0) n_large = 0u;
 #pragma unroll 1
     for (int r = 0; r < kScanItems; ++r) {
-        const uint32_t i = blockIdx.x * kScanTile + r * kScanThreads + threadIdx.x;
+        const uint32_t i = blockIdx.x * kScanTile + r * kScanThreads + t;
         const uint32_t b = i < n ? bins[i] : 0u;
         const uint32_t c = bin_count(b);
         const uint32_t o = carry + block_excl_scan(c, &total);
-        if (c) emit_splat_pairs(b, order[i], o, o + c, rec, tiles_x, ptile, pval);
+        if (c) {
+            const uint32_t s = order[i];
+            if (!(b & kBinLarge)) {
+                emit_splat_pairs(b, s, o, o + c, rec, tiles_x, ptile, pval);
+            } else {
+                const float4 r3 = rec[(size_t)s * kRecVec];  // reach x, reach y, log2 o, C
+                const uint32_t rx = __float_as_uint(r3.x), ry = __float_as_uint(r3.y);
+                const uint32_t tx0 = (rx & 0xFFFFu) >> 4, ty0 = (ry & 0xFFFFu) >> 4;
+                const uint32_t q = atomicAdd(&n_large, 1u);  // queue order: any (own output range)
+                s_large[q] = make_uint4(s, o, tx0 | (ty0 << 16), ((rx >> 16) >> 4) - tx0 + 1u);
+                s_cnt[q] = c;
+            }
+        }
         carry += total;
+        __syncthreads();
+        const uint32_t nl = n_large;
+        for (uint32_t q = warp; q < nl; q += kScanThreads / 32) {
+            const uint4 L = s_large[q];  // splat id, first pair, tile x0 | y0 << 16, tiles per row
+            const uint32_t cnt = s_cnt[q];
+            for (uint32_t k = lane; k < cnt; k += 32) {
+                const uint32_t row = k / L.w, col = k - row * L.w;
+                ptile[L.y + k] = (uint16_t)(((L.z >> 16) + row) * (uint32_t)tiles_x + (L.z & 0xFFFFu) + col);
+                pval[L.y + k] = L.x;
+            }
+        }
+        __syncthreads();  // the queue is refilled by the next round
+        if (t == 0) n_large = 0u;
     }
 }
 
