@@ -313,7 +313,7 @@ int cs_debug_fail_allocs(cs_ctx *ctx, int32_t after);
 
 /* Testing hook for the compositing schedule of plain frames: mode
  * CS_BLEND_ITEMS_AUTO (the default) composites every short tile list (under
- * 4,096 pairs) as one work item of its own when the frame has many busy
+ * 8,192 pairs) as one work item of its own when the frame has many busy
  * tiles (at least 8 per resident compositing CTA) and block by block
  * otherwise; CS_BLEND_ITEMS_TILES and CS_BLEND_ITEMS_BLOCKS force one or the
  * other for every frame of the context, so that small test frames exercise

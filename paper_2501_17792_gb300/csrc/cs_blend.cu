@@ -267,7 +267,7 @@ constexpr int kPpWarps = 8;
 constexpr int kPpThreads = 32 * kPpWarps;
 constexpr uint32_t kPpRound = 32 * kPpWarps;
 constexpr int kPpBlocks = kTile * kTile / 32;  // 8x4 blocks per tile
-constexpr int kPpTileClass = 13;               // lists of fewer than 4,096 pairs: tile items
+constexpr int kPpTileClass = 14;               // lists of fewer than 8,192 pairs: tile items
 static_assert((1u << (kPpTileClass - 1)) <= kBlendBudget, "a tile item composites its whole list");
 
 struct PpShared {
@@ -299,7 +299,7 @@ __device__ __forceinline__ int blend_class(uint32_t n) {
 // tile count were chosen by timing the 1080p 3,500-instance frame (long
 // lists), the 4K 10,000-instance frame (mostly mid-length lists) and
 // 1280x720 frames of 1 to 5,000 characters.
-constexpr int kPpTileShift = 5;
+constexpr int kPpTileShift = 4;
 constexpr int kPpTileItemsPerCta = 8;
 static_assert(2 * (kBlendClasses - 1) + 1 < kBlendKeys && 2 * (kPpTileClass - 1 + kPpTileShift) < kBlendKeys,
               "schedule keys");

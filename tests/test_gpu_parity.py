@@ -352,7 +352,7 @@ def test_pair_parallel_pass_on_mid_length_lists():
 
 
 def test_tile_items_and_block_items_match_the_oracle():
-    """Plain-frame compositing with every short list (under 4,096 pairs) as
+    """Plain-frame compositing with every short list (under 8,192 pairs) as
     one whole-tile item (warp w walks block w's pairs in depth order), and
     with every list block by block (eight sub-range partials chained per
     round), each forced by the testing hook on a field whose density falls
@@ -373,7 +373,7 @@ def test_tile_items_and_block_items_match_the_oracle():
         r, imgs[mode], ref, errs, st = full_check(sc, label=f"schedule_{mode}", max_boundary=0.2, blend_items=mode)
         rg = r.debug("tile_ranges").astype(np.int64)
         counts = rg[:, 1] - rg[:, 0]
-        assert counts.min() < 1024 and ((counts >= 1024) & (counts < 4096)).sum() >= 8 and counts.max() >= 4096, counts
+        assert counts.min() < 1024 and ((counts >= 1024) & (counts < 8192)).sum() >= 8 and counts.max() >= 8192, counts
     d = np.abs(imgs[binding.CS_BLEND_ITEMS_TILES] - imgs[binding.CS_BLEND_ITEMS_BLOCKS])
     assert d.max() <= PU.TOL_MAX_ABS and np.median(d) <= 1e-6, (d.max(), np.median(d))
     with pytest.raises(binding.CrowdSplatError):
