@@ -321,6 +321,20 @@ int cs_debug_fail_allocs(cs_ctx *ctx, int32_t after);
  * pixel's pairs in depth order with the same stop rule).  The paper has no
  * counterpart.  Returns CS_OK, or CS_ERR_ARG for a NULL context or an
  * unknown mode. */
+/* Bounds checks of the debug build (compiled with CS_CHECKS=1, the library
+ * libcrowdsplat_checks.so that build.build(checks=True) makes; the release
+ * library compiles them away): a kernel index outside its buffer (splat
+ * record, pair, tile, sort position, compositing slot) sets one bit of a
+ * device check word and the access is skipped.  Waits for the context's
+ * stream, then stores the word accumulated since the last call in *failed
+ * (0: every check passed; bits 1 record, 2 pair, 4 tile, 8 splat id,
+ * 16 sort, 32 slot) and clears it, and stores in *enabled whether this
+ * library was built with the checks (0 and *failed = 0 otherwise).  The
+ * word is per process and device, shared by every context.  The paper has
+ * no counterpart.  Returns CS_OK, CS_ERR_ARG for a NULL argument, or
+ * CS_ERR_CUDA. */
+int cs_debug_checks(cs_ctx *ctx, uint32_t *failed, int32_t *enabled);
+
 #define CS_BLEND_ITEMS_AUTO 0
 #define CS_BLEND_ITEMS_TILES 1
 #define CS_BLEND_ITEMS_BLOCKS 2

@@ -94,6 +94,7 @@ SIGNATURES = {
     "cs_debug_read": (C.c_int, [_P, C.c_int32, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "cs_debug_fail_allocs": (C.c_int, [_P, C.c_int32]),
     "cs_debug_blend_items": (C.c_int, [_P, C.c_int32]),
+    "cs_debug_checks": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_int32)]),
     "cs_version": (C.c_char_p, []),
     # ranked LoD (include/crowdsplat_lod.h)
     "cs_lod_features": (C.c_int, [_P, _P]),
@@ -115,11 +116,15 @@ SIGNATURES = {
 LOD_FEATURES, MLP_PARAMS = 32, 48 * 64 + 64 + 64 * 64 + 64 + 64 + 1
 
 
+_libs = {}
+
+
 def load(path: str | None = None):
-    """Load libcrowdsplat.so; raises RuntimeError if it has not been built."""
+    """Load libcrowdsplat.so (or the library at `path`, e.g. the bounds-checked
+    debug build); raises RuntimeError if it has not been built."""
     global _lib
-    if _lib is None:
-        p = path or LIB_PATH
+    p = os.path.abspath(path or LIB_PATH)
+    if p not in _libs:
         if not os.path.exists(p):
             raise RuntimeError(f"{p} is missing: build it first (python -m paper_2501_17792_gb300.build "
                                "or __graft_entry__.build()); there is no CPU fallback")
@@ -128,8 +133,10 @@ def load(path: str | None = None):
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = L
-    return _lib
+        _libs[p] = L
+    if path is None:
+        _lib = _libs[p]
+    return _libs[p]
 
 
 lib = load
@@ -172,10 +179,10 @@ class Renderer:
 
     def __init__(self, device: int = 0, stream=None, skin_mode: int = CS_SKIN_FULL,
                  sh_frame: int = CS_SH_ROOT_FRAME, instance_cull: bool = True,
-                 stage_timing: bool = False, template_storage: int = CS_STORE_FP32):
+                 stage_timing: bool = False, template_storage: int = CS_STORE_FP32, library: str | None = None):
         import torch
         self.torch = torch
-        self.L = load()
+        self.L = load(library)
         self.device = int(device)
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
@@ -379,6 +386,14 @@ class Renderer:
             raise ValueError(f"score has {s.shape[0]} entries, templates hold {self.n_gauss_total}")
         self._check(self.L.cs_lod_rank(self.h, s.data_ptr(), o.data_ptr()))
         return o
+
+    def debug_checks(self) -> tuple[int, bool]:
+        """Bounds-check word of the checked debug build since the last call
+        (read and cleared; 0 = every check passed) and whether the loaded
+        library was built with the checks (cs_debug_checks)."""
+        failed, enabled = C.c_uint32(), C.c_int32()
+        self._check(self.L.cs_debug_checks(self.h, C.byref(failed), C.byref(enabled)))
+        return int(failed.value), bool(enabled.value)
 
     def debug_blend_items(self, mode: int) -> None:
         """Testing hook: the compositing schedule of plain frames

@@ -307,6 +307,7 @@ bool window_ok(const cs_camera *cam) {
 }
 
 void cam_params(const cs_ctx *c, const cs_camera *cam, CamParams &p) {
+    p.n_splats = 0;  // set once the cull's counts are read
     for (int i = 0; i < 9; ++i) p.R[i] = cam->R[i];
     for (int i = 0; i < 3; ++i) p.t[i] = cam->t[i];
     p.fx = cam->fx;
@@ -888,6 +889,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         set_depth_key_range(cp, ctx->h_meta);
         ctx->key_lo = cp.key_lo;
         S = ctx->h_meta[kMetaSplats];
+        cp.n_splats = (uint32_t)S;
         proj_blocks = ctx->h_meta[kMetaBlocks];
         for (int l = 0; l < kMaxLevels; ++l) ctx->per_level[l] = ctx->h_meta[kMetaLevel0 + l];
         if (S >= 0x7fffffffLL) return fail(ctx, CS_ERR_CAPACITY, "more than 2^31 - 1 splats in a frame");
@@ -942,7 +944,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->pval2, Pa, "pair splats (ping-pong)"));
     CS_TRY(ensure(ctx, ctx->scratch, std::max(radix_scratch_words(Pa), radix_scratch_words(Sa)), "scratch"));
     if (P > 0) launched += launch_emit_pairs_scan((uint32_t)S, order, ctx->bins_sorted.p, ctx->pair_off.p, ctx->rec.p,
-                                                  cp.tiles_x, ctx->ptile.p, ctx->pval.p, st);
+                                                  cp.tiles_x, (uint32_t)T, ctx->ptile.p, ctx->pval.p, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[5], st));
     // 6. stable sort of the pairs by tile
     int pb = 0;
@@ -954,7 +956,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     if (timing) CS_CUDA(cudaEventRecord(ev[6], st));
     // 7. per-tile ranges
     CS_CUDA(cudaMemsetAsync(ctx->ranges.p, 0, sizeof(uint2) * T, st));
-    launched += launch_tile_ranges((uint32_t)P, ptile, ctx->ranges.p, st);
+    launched += launch_tile_ranges((uint32_t)P, ptile, ctx->ranges.p, (uint32_t)T, st);
     if (timing) CS_CUDA(cudaEventRecord(ev[7], st));
     // 8. compositing
     {
@@ -977,6 +979,9 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     bw.ox = cp.ox;
     bw.oy = cp.oy;
     bw.items = ctx->blend_items;
+    bw.n_pairs = (uint32_t)P;
+    bw.max_slots = (uint32_t)blend_max_slots((size_t)T, (size_t)P);
+    bw.max_chunks = (uint32_t)blend_max_chunks((size_t)T, (size_t)P);
     if (contrib_tmpl) {
         CS_TRY(ensure(ctx, ctx->contrib_s, Sa, "splat contributions"));
         CS_CUDA(cudaMemsetAsync(ctx->contrib_s.p, 0, Sa * sizeof(float), st));
@@ -1262,6 +1267,17 @@ int cs_debug_fail_allocs(cs_ctx *ctx, int32_t after) {
     return CS_OK;
 }
 
+int cs_debug_checks(cs_ctx *ctx, uint32_t *failed, int32_t *enabled) {
+    if (!ctx || !failed || !enabled) return ctx ? fail(ctx, CS_ERR_ARG, "cs_debug_checks: NULL output") : CS_ERR_ARG;
+    CS_CUDA(cudaSetDevice(ctx->device));
+    CS_CUDA(cudaStreamSynchronize(ctx->stream));
+    const uint32_t w = check_word_geometry() | check_word_sort() | check_word_blend();
+    if (w == 0xFFFFFFFFu) return fail(ctx, CS_ERR_CUDA, "cs_debug_checks: reading the check word failed");
+    *failed = w;
+    *enabled = CS_CHECKS ? 1 : 0;
+    return CS_OK;
+}
+
 int cs_debug_blend_items(cs_ctx *ctx, int32_t mode) {
     if (!ctx) return CS_ERR_ARG;
     if (mode != CS_BLEND_ITEMS_AUTO && mode != CS_BLEND_ITEMS_TILES && mode != CS_BLEND_ITEMS_BLOCKS)
@@ -1469,6 +1485,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
         n_groups = ctx->h_meta[kMetaGroups];
         set_depth_key_range(cp, ctx->h_meta);
         S = ctx->h_meta[kMetaSplats];
+        cp.n_splats = (uint32_t)S;
         proj_blocks = ctx->h_meta[kMetaBlocks];
         for (int l = 0; l < kMaxLevels; ++l) per_level[l] = ctx->h_meta[kMetaLevel0 + l];
     }
@@ -1500,7 +1517,9 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
                     (long long)P, kStaticPairs);
     if (radix_scratch_words((size_t)std::max<int64_t>(P, 1)) > kStaticScratchWords)
         return fail(ctx, CS_ERR_CAPACITY, "cs_render_static: scratch too small for %lld pairs", (long long)P);
-    if (P > 0) launched += launch_emit_pairs((uint32_t)S, order, bins_sorted, pair_off, rec, cp.tiles_x, ptile0, pval0, st);
+    if (P > 0)
+        launched += launch_emit_pairs((uint32_t)S, order, bins_sorted, pair_off, rec, cp.tiles_x, (uint32_t)T, ptile0,
+                                      pval0, st);
     int pb = 0;
     if (P > 0) launched += radix_sort_u16(ptile0, pval0, ptile1, pval1, (uint32_t)P, bits_for((uint32_t)T),
                                           scratch, st, &pb);
@@ -1508,7 +1527,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     uint32_t *pval = pb ? pval1 : pval0;
     // the array keeps the previous call's ranges: clear them
     CS_CUDA(cudaMemsetAsync(ranges, 0, sizeof(uint2) * T, st));
-    launched += launch_tile_ranges((uint32_t)P, ptile, ranges, st);
+    launched += launch_tile_ranges((uint32_t)P, ptile, ranges, (uint32_t)T, st);
     BlendWork bw{reinterpret_cast<int32_t *>(base + kOffBwSlot), reinterpret_cast<int32_t *>(base + kOffBwTile),
                  reinterpret_cast<uint32_t *>(base + kOffBwChunk0), reinterpret_cast<uint32_t *>(base + kOffBwDone),
                  reinterpret_cast<float4 *>(base + kOffBwState), reinterpret_cast<float4 *>(base + kOffBwPart),
@@ -1518,6 +1537,9 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     bw.ox = cp.ox;
     bw.oy = cp.oy;
     bw.items = ctx->blend_items;
+    bw.n_pairs = (uint32_t)P;
+    bw.max_slots = (uint32_t)blend_max_slots((size_t)T, (size_t)P);
+    bw.max_chunks = (uint32_t)blend_max_chunks((size_t)T, (size_t)P);
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ranges, pval, rec, out, bw,
                              (uint32_t)P, st);
     CS_CUDA(cudaGetLastError());

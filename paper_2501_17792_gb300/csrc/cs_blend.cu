@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
     const int tile = blockIdx.x / kParts, part = blockIdx.x % kParts;
     const int w0 = part * (kT / 32);  // first warp block of this CTA
     const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy, w0);
-    const uint2 rg = ranges[tile];
+    uint2 rg = ranges[tile];
+    if (!in_bounds(rg.x <= rg.y && rg.y <= work.n_pairs, kChkPair)) rg.y = rg.x;
     Pixel px{1.0f, 0.0f, 0.0f, 0.0f, rg.x, !g.inside, false};
     const uint32_t end1 = rg.y - rg.x > kBudget && kMode == 0 ? rg.x + kBudget : rg.y;
     composite_range<kMode, kT>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib, w0 / 2);
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
         work.px_end[(size_t)g.py * W + g.px] = px.last;
         work.px_T[(size_t)g.py * W + g.px] = px.T;
     }
-    if (end1 < rg.y) {
+    if (end1 < rg.y && in_bounds(work.cand_slot[tile] >= 0, kChkSlot)) {
         // pairs remain: record the pixel state for pass 2 and the merge (the
         // plan set cand_done to 1; every part clears it unless all its
         // pixels are done)
@@ -401,6 +402,10 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
         __syncthreads();
         const int tile = sh.tile, kind = sh.kind;
         if (tile < 0) return;
+        if (!in_bounds(tile < tiles_x * ((H + kTile - 1) / kTile), kChkTile)) {
+            __syncthreads();  // the item fields are rewritten for the next item
+            continue;
+        }
         if (kind != 2) {
             const int tyi = tile / tiles_x, txi = tile - tyi * tiles_x;
             const int tx0 = txi * kTile, ty0 = tyi * kTile;
@@ -418,7 +423,8 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
             const int py = ty0 + (warp >> 1) * kBlockH + lane / kBlockW;
             const bool inside = px < W && py < H;
             const float fpx = (float)(px + work.ox) + 0.5f, fpy = (float)(py + work.oy) + 0.5f;
-            const uint2 rg = ranges[tile];
+            uint2 rg = ranges[tile];
+            if (!in_bounds(rg.x <= rg.y && rg.y <= work.n_pairs, kChkPair)) rg.y = rg.x;
             float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
             bool done = !inside;
             float4 *const f0 = &sh.s0[0][0], *const f1 = &sh.s1[0][0], *const f2 = &sh.s2[0][0];
@@ -483,7 +489,8 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
         const int px = bx0 + (lane & (kBlockW - 1)), py = by0 + lane / kBlockW;
         const bool inside = px < W && py < H;
         const float fpx = (float)(px + work.ox) + 0.5f, fpy = (float)(py + work.oy) + 0.5f;
-        const uint2 rg = ranges[tile];
+        uint2 rg = ranges[tile];
+        if (!in_bounds(rg.x <= rg.y && rg.y <= work.n_pairs, kChkPair)) rg.y = rg.x;
         const uint32_t end1 = rg.y - rg.x > kBudget ? rg.x + kBudget : rg.y;
         // the block's chained state (warp 0)
         float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
@@ -589,9 +596,9 @@ __global__ void __launch_bounds__(kPpThreads, 8) k_blend_pp(int tiles_x, int W, 
         }
         if (warp == 0) {
             bool final_out = true;
-            if (end1 < rg.y) {
+            const int slot = end1 < rg.y ? work.cand_slot[tile] : -1;
+            if (end1 < rg.y && in_bounds(slot >= 0, kChkSlot)) {
                 // pairs remain: the state for pass 2 and the merge, as pass 1 records it
-                const int slot = work.cand_slot[tile];
                 const bool all = __all_sync(0xffffffffu, done);
                 if (lane == 0 && !all) atomicAnd(work.cand_done + slot, 0u);
                 work.state[(size_t)slot * kBlendThreads + blk * 32 + lane] = make_float4(cr, cg, cb, done ? -T : T);
@@ -619,6 +626,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_chunks(int tiles_x, int
     const int tile = work.cand_tile[slot];
     const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
     const uint2 rg = ranges[tile];
+    if (!in_bounds(rg.y <= work.n_pairs, kChkPair)) return;
     const uint32_t c = w - work.cand_chunk0[slot];
     const uint32_t start = rg.x + kBudget + c * kChunk;
     const uint32_t end = min(rg.y, start + kChunk);
@@ -693,6 +701,7 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W,
     const int tile = work.cand_tile[slot];
     const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
     const uint2 rg = ranges[tile];
+    if (!in_bounds(rg.y <= work.n_pairs, kChkPair)) return;
     const float4 sb = mine ? work.state[pix] : make_float4(0.f, 0.f, 0.f, 1.f);
     Pixel px{sb.w, sb.x, sb.y, sb.z, 0u, !mine, false};
     const uint32_t start = rg.x + kBudget + (w - work.cand_chunk0[slot]) * kChunk;
@@ -718,10 +727,14 @@ __global__ void __launch_bounds__(256) k_blend_count(int n_tiles, const uint2 *_
         const uint32_t nk = (n - kBudget + kChunk - 1) / kChunk;
         slot = atomicAdd(work.meta + 0, 1);
         const uint32_t c0 = atomicAdd(reinterpret_cast<unsigned *>(work.meta + 1), nk);
-        work.cand_tile[slot] = t;
-        work.cand_chunk0[slot] = c0;
-        work.cand_done[slot] = 1u;  // cleared by pass 1 unless every pixel is done
-        for (uint32_t c = 0; c < nk; ++c) work.chunk_slot[c0 + c] = slot;
+        if (in_bounds((uint32_t)slot < work.max_slots && c0 + nk <= work.max_chunks, kChkSlot)) {
+            work.cand_tile[slot] = t;
+            work.cand_chunk0[slot] = c0;
+            work.cand_done[slot] = 1u;  // cleared by pass 1 unless every pixel is done
+            for (uint32_t c = 0; c < nk; ++c) work.chunk_slot[c0 + c] = slot;
+        } else {
+            slot = -1;
+        }
     }
     work.cand_slot[t] = slot;
 }
@@ -795,5 +808,7 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
     k_blend_fix<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
     return launched + 3;
 }
+
+CS_DEFINE_CHECK_READER(check_word_blend)
 
 }  // namespace cs

@@ -734,7 +734,7 @@ __device__ __forceinline__ void project_chunk(
                     srec[1 * kSrecLd + t] = r1;
                     srec[2 * kSrecLd + t] = r2;
                     slive[t] = 1;
-                } else {
+                } else if (in_bounds((uint32_t)s < cam.n_splats, kChkRecord)) {
                     float4 *ro = rec + (size_t)s * kRecVec;
                     ro[0] = r0;
                     ro[1] = r1;
@@ -743,6 +743,7 @@ __device__ __forceinline__ void project_chunk(
             }
         }
     }
+    if (!in_bounds((uint32_t)s < cam.n_splats, kChkRecord)) return;
     key[s] = live ? min(max(__float_as_uint(tz), cam.key_lo), cam.key_hi) - cam.key_lo : 0xFFFFFFFFu;
     bin[s] = live ? bword : 0u;
 }
@@ -829,7 +830,8 @@ __global__ void __launch_bounds__(kProjThreads, 5) k_project(
             for (int i = 0; i < kRecVec; ++i) {
                 const int o = (int)threadIdx.x + i * kProjThreads;
                 const int sl = o / kRecVec, k = o - sl * kRecVec;
-                if (s_live[sl]) rec[s0 * kRecVec + o] = s_rec[k * kSrecLd + sl];
+                if (s_live[sl] && in_bounds(s0 + sl < cam.n_splats, kChkRecord))
+                    rec[s0 * kRecVec + o] = s_rec[k * kSrecLd + sl];
             }
             __syncthreads();  // the staging buffers are reused by the next chunk
         } else {
@@ -967,5 +969,7 @@ int launch_contrib_to_template(int n_splats, const Group *groups, int n_groups, 
                                                                   contrib_splat, contrib_tmpl);
     return 1;
 }
+
+CS_DEFINE_CHECK_READER(check_word_geometry)
 
 }  // namespace cs

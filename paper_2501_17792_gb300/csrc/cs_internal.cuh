@@ -36,6 +36,44 @@
 
 namespace cs {
 
+// Debug build with bounds checks (nvcc -DCS_CHECKS=1; build.build(checks=
+// True) makes libcrowdsplat_checks.so): an index that a checked access would
+// take outside its buffer sets one bit of the translation unit's check word
+// and the access is skipped, so the fault is reported (cs_debug_checks)
+// instead of reading or writing out of bounds.  The release build compiles
+// every check away.
+#ifndef CS_CHECKS
+#define CS_CHECKS 0
+#endif
+constexpr uint32_t kChkRecord = 1u;  // splat record, depth key or bin word index >= splats of the frame
+constexpr uint32_t kChkPair = 2u;    // pair index >= pairs of the frame
+constexpr uint32_t kChkTile = 4u;    // tile index >= tiles of the frame
+constexpr uint32_t kChkSplat = 8u;   // splat id written into the pair list >= splats
+constexpr uint32_t kChkSort = 16u;   // radix scatter position or gathered index >= elements
+constexpr uint32_t kChkSlot = 32u;   // compositing slot or chunk beyond the planned capacity
+#if CS_CHECKS
+static __device__ uint32_t g_check_word;
+__device__ __forceinline__ bool in_bounds(bool ok, uint32_t bit) {
+    if (!ok) atomicOr(&g_check_word, bit);
+    return ok;
+}
+// reads and clears this translation unit's check word (synchronous)
+#define CS_DEFINE_CHECK_READER(fn)                                  \
+    uint32_t fn() {                                                 \
+        uint32_t v = 0u, z = 0u;                                    \
+        if (cudaMemcpyFromSymbol(&v, g_check_word, sizeof(v)) != cudaSuccess) return 0xFFFFFFFFu; \
+        cudaMemcpyToSymbol(g_check_word, &z, sizeof(z));            \
+        return v;                                                   \
+    }
+#else
+__device__ __forceinline__ bool in_bounds(bool, uint32_t) { return true; }
+#define CS_DEFINE_CHECK_READER(fn) \
+    uint32_t fn() { return 0u; }
+#endif
+uint32_t check_word_geometry();
+uint32_t check_word_sort();
+uint32_t check_word_blend();
+
 constexpr int kJoints = 24;
 constexpr int kMaxTemplates = 63;
 constexpr int kMaxLevels = 4;
@@ -105,6 +143,7 @@ struct CamParams {
     // depth keys: float bits of the view depth clamped to [key_lo, key_hi]
     // (bits of bounds of every live depth), minus key_lo; culled = all ones
     uint32_t key_lo, key_hi;
+    uint32_t n_splats;     // splats of the frame (bounds of the checked debug build)
 };
 
 // Bits of the depth keys of a frame whose live depths lie in float-bit range
@@ -295,12 +334,12 @@ int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint3
 size_t bin_scan_blocks(size_t n);
 int bin_scan_sums(const uint32_t *bins, uint32_t n, uint32_t *sums, cudaStream_t st);
 int launch_emit_pairs_scan(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
-                           const uint32_t *sums, const float4 *rec, int tiles_x, uint16_t *ptile, uint32_t *pval,
-                           cudaStream_t st);
+                           const uint32_t *sums, const float4 *rec, int tiles_x, uint32_t n_tiles, uint16_t *ptile,
+                           uint32_t *pval, cudaStream_t st);
 int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
-                      const uint32_t *pair_off, const float4 *rec, int tiles_x, uint16_t *ptile,
+                      const uint32_t *pair_off, const float4 *rec, int tiles_x, uint32_t n_tiles, uint16_t *ptile,
                       uint32_t *pval, cudaStream_t st);
-int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, cudaStream_t st);
+int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, uint32_t n_tiles, cudaStream_t st);
 int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cudaStream_t st);
 
 // ---- compositing (cs_blend.cu) ----
@@ -336,6 +375,7 @@ struct BlendWork {
     int32_t *chunk_slot;  // [chunks]: the slot of each pass-2 chunk
     int32_t ox, oy;       // window origin: pixel (i, j) has its centre at (ox + i + 0.5, oy + j + 0.5)
     int32_t items;        // pass-1 schedule: CS_BLEND_ITEMS_AUTO, _TILES or _BLOCKS
+    uint32_t n_pairs, max_slots, max_chunks;  // bounds of the checked debug build
 };
 constexpr int kBlendKeys = 64;     // schedule keys of pass 1 (see cs_blend.cu)
 constexpr int kBlendClasses = 24;  // list length classes: 0 empty, c: 2^(c-1) <= n < 2^c (last: n >= 2^22)

@@ -305,9 +305,10 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(
         const uint32_t d = (uint32_t)((key >> shift) & (kDigits - 1));
         const uint32_t g = gbase[d] + (p - dstart[d]);
         const uint32_t val = sval[p];
+        if (!in_bounds(g < n, kChkSort)) continue;
         kout[g] = key;
         vout[g] = val;
-        if (gdst) gdst[g] = gsrc[val];
+        if (gdst && in_bounds(val < n, kChkSort)) gdst[g] = gsrc[val];
     }
 }
 
@@ -399,16 +400,20 @@ int radix_sort_u16(uint16_t *k0, uint32_t *v0, uint16_t *k1, uint32_t *v1, uint3
 // the depth sort); larger ones take the reach box from the record.
 __device__ __forceinline__ void emit_splat_pairs(uint32_t b, uint32_t s, uint32_t o, uint32_t e,
                                                  const float4 *__restrict__ rec, int tiles_x,
-                                                 uint16_t *__restrict__ ptile, uint32_t *__restrict__ pval) {
-    if (o >= e) return;
+                                                 uint16_t *__restrict__ ptile, uint32_t *__restrict__ pval,
+                                                 uint32_t n_tiles, uint32_t n_pairs) {
+    if (o >= e || !in_bounds(e <= n_pairs, kChkPair)) return;
     if (!(b & kBinLarge)) {
         const uint32_t x0 = b & 0xFFu, y0 = (b >> 8) & 0xFFu;
         uint32_t m = (b >> 16) & 0x1FFu;
         while (m && o < e) {
             const uint32_t k = __ffs(m) - 1;
             m &= m - 1;
-            ptile[o] = (uint16_t)((y0 + k / 3) * (uint32_t)tiles_x + x0 + k % 3);
-            pval[o] = s;
+            const uint32_t tile = (y0 + k / 3) * (uint32_t)tiles_x + x0 + k % 3;
+            if (in_bounds(tile < n_tiles, kChkTile)) {
+                ptile[o] = (uint16_t)tile;
+                pval[o] = s;
+            }
             ++o;
         }
         return;
@@ -420,8 +425,10 @@ __device__ __forceinline__ void emit_splat_pairs(uint32_t b, uint32_t s, uint32_
     for (int yy = ay0 >> 4; yy <= (ay1 >> 4); ++yy) {
         for (int xx = ax0 >> 4; xx <= (ax1 >> 4); ++xx) {
             if (o >= e) return;
-            ptile[o] = (uint16_t)(yy * tiles_x + xx);
-            pval[o] = s;
+            if (in_bounds((uint32_t)(yy * tiles_x + xx) < n_tiles, kChkTile)) {
+                ptile[o] = (uint16_t)(yy * tiles_x + xx);
+                pval[o] = s;
+            }
             ++o;
         }
     }
@@ -431,12 +438,14 @@ __device__ __forceinline__ void emit_splat_pairs(uint32_t b, uint32_t s, uint32_
 __global__ void __launch_bounds__(256) k_emit_pairs(uint32_t n, const uint32_t *__restrict__ order,
                                                     const uint32_t *__restrict__ bins,
                                                     const uint32_t *__restrict__ pair_off,
-                                                    const float4 *__restrict__ rec, int tiles_x,
+                                                    const float4 *__restrict__ rec, int tiles_x, uint32_t n_tiles,
                                                     uint16_t *__restrict__ ptile,
                                                     uint32_t *__restrict__ pval) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    emit_splat_pairs(bins[i], order[i], pair_off[i], pair_off[i + 1], rec, tiles_x, ptile, pval);
+    const uint32_t s = order[i];
+    if (!in_bounds(s < n, kChkSplat)) return;
+    emit_splat_pairs(bins[i], s, pair_off[i], pair_off[i + 1], rec, tiles_x, ptile, pval, n_tiles, pair_off[n]);
 }
 
 // Pair emission fused with the down-sweep of the pair-count scan: block b
@@ -453,9 +462,10 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_pairs_scan(uint32_t n, co
                                                                  const uint32_t *__restrict__ bins,
                                                                  const uint32_t *__restrict__ sums,
                                                                  const float4 *__restrict__ rec, int tiles_x,
-                                                                 uint16_t *__restrict__ ptile,
+                                                                 uint32_t n_tiles, uint16_t *__restrict__ ptile,
                                                                  uint32_t *__restrict__ pval) {
     __shared__ uint32_t total, n_large;
+    const uint32_t n_pairs = CS_CHECKS ? sums[gridDim.x] : 0xFFFFFFFFu;  // the scan's total
     __shared__ uint4 s_large[kScanThreads];  // splat id, first pair, tile x0 | y0 << 16, tiles per row
     __shared__ uint32_t s_cnt[kScanThreads];  // its pairs
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -467,10 +477,10 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_pairs_scan(uint32_t n, co
         const uint32_t b = i < n ? bins[i] : 0u;
         const uint32_t c = bin_count(b);
         const uint32_t o = carry + block_excl_scan(c, &total);
-        if (c) {
+        if (c && in_bounds(order[i] < n, kChkSplat)) {
             const uint32_t s = order[i];
             if (!(b & kBinLarge)) {
-                emit_splat_pairs(b, s, o, o + c, rec, tiles_x, ptile, pval);
+                emit_splat_pairs(b, s, o, o + c, rec, tiles_x, ptile, pval, n_tiles, n_pairs);
             } else {
                 const float4 r3 = rec[(size_t)s * kRecVec];  // reach x, reach y, log2 o, C
                 const uint32_t rx = __float_as_uint(r3.x), ry = __float_as_uint(r3.y);
@@ -486,9 +496,12 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_pairs_scan(uint32_t n, co
         for (uint32_t q = warp; q < nl; q += kScanThreads / 32) {
             const uint4 L = s_large[q];  // splat id, first pair, tile x0 | y0 << 16, tiles per row
             const uint32_t cnt = s_cnt[q];
+            if (!in_bounds(L.y + cnt <= n_pairs, kChkPair)) continue;
             for (uint32_t k = lane; k < cnt; k += 32) {
                 const uint32_t row = k / L.w, col = k - row * L.w;
-                ptile[L.y + k] = (uint16_t)(((L.z >> 16) + row) * (uint32_t)tiles_x + (L.z & 0xFFFFu) + col);
+                const uint32_t tile = ((L.z >> 16) + row) * (uint32_t)tiles_x + (L.z & 0xFFFFu) + col;
+                if (!in_bounds(tile < n_tiles, kChkTile)) continue;
+                ptile[L.y + k] = (uint16_t)tile;
                 pval[L.y + k] = L.x;
             }
         }
@@ -508,20 +521,20 @@ int bin_scan_sums(const uint32_t *bins, uint32_t n, uint32_t *sums, cudaStream_t
 }
 
 int launch_emit_pairs_scan(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
-                           const uint32_t *sums, const float4 *rec, int tiles_x, uint16_t *ptile, uint32_t *pval,
-                           cudaStream_t st) {
+                           const uint32_t *sums, const float4 *rec, int tiles_x, uint32_t n_tiles, uint16_t *ptile,
+                           uint32_t *pval, cudaStream_t st) {
     if (n_splats == 0) return 0;
-    k_emit_pairs_scan<<<(uint32_t)bin_scan_blocks(n_splats), kScanThreads, 0, st>>>(n_splats, order, bins_sorted,
-                                                                                    sums, rec, tiles_x, ptile, pval);
+    k_emit_pairs_scan<<<(uint32_t)bin_scan_blocks(n_splats), kScanThreads, 0, st>>>(
+        n_splats, order, bins_sorted, sums, rec, tiles_x, n_tiles, ptile, pval);
     return 1;
 }
 
 int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *bins_sorted,
-                      const uint32_t *pair_off, const float4 *rec, int tiles_x, uint16_t *ptile,
+                      const uint32_t *pair_off, const float4 *rec, int tiles_x, uint32_t n_tiles, uint16_t *ptile,
                       uint32_t *pval, cudaStream_t st) {
     if (n_splats == 0) return 0;
     k_emit_pairs<<<(n_splats + 255) / 256, 256, 0, st>>>(n_splats, order, bins_sorted, pair_off, rec,
-                                                          tiles_x, ptile, pval);
+                                                          tiles_x, n_tiles, ptile, pval);
     return 1;
 }
 
@@ -530,7 +543,7 @@ int launch_emit_pairs(uint32_t n_splats, const uint32_t *order, const uint32_t *
 // neighbours, and writes the start / end of every tile that begins / ends
 // among its keys.
 __global__ void __launch_bounds__(256) k_tile_ranges(uint32_t n, const uint16_t *__restrict__ ptile,
-                                                     uint2 *__restrict__ ranges) {
+                                                     uint2 *__restrict__ ranges, uint32_t n_tiles) {
     const uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) * 8u;
     if (base >= n) return;
     uint32_t v[8];
@@ -553,16 +566,18 @@ __global__ void __launch_bounds__(256) k_tile_ranges(uint32_t n, const uint16_t 
         const uint32_t t = v[k];
         if (t > 0xFFFFu) break;  // past the end
         const uint32_t after = k < 7 ? v[k + 1] : next;
-        if (t != prev) ranges[t].x = base + k;
-        if (t != after) ranges[t].y = base + k + 1;
+        if (in_bounds(t < n_tiles, kChkTile)) {
+            if (t != prev) ranges[t].x = base + k;
+            if (t != after) ranges[t].y = base + k + 1;
+        }
         prev = t;
     }
 }
 
-int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, cudaStream_t st) {
+int launch_tile_ranges(uint32_t n_pairs, const uint16_t *ptile, uint2 *ranges, uint32_t n_tiles, cudaStream_t st) {
     if (n_pairs == 0) return 0;
     const uint32_t threads = (n_pairs + 7) / 8;
-    k_tile_ranges<<<(threads + 255) / 256, 256, 0, st>>>(n_pairs, ptile, ranges);
+    k_tile_ranges<<<(threads + 255) / 256, 256, 0, st>>>(n_pairs, ptile, ranges, n_tiles);
     return 1;
 }
 
@@ -582,5 +597,7 @@ int launch_count_live(uint32_t n, const uint32_t *sorted_keys, int32_t *out, cud
     k_count_live<<<(n + 255) / 256, 256, 0, st>>>(n, sorted_keys, out);
     return 1;
 }
+
+CS_DEFINE_CHECK_READER(check_word_sort)
 
 }  // namespace cs

@@ -43,6 +43,21 @@ def test_library_exports_every_declared_symbol(lib):
         assert name in binding.SIGNATURES, name
 
 
+def test_checked_debug_build_compiles_and_exports_every_declared_symbol():
+    """The debug build with bounds checks in the kernels (CS_CHECKS=1) builds
+    for sm_103a and exports the same ABI; the release build reports its
+    checks as absent without touching a GPU (NULL arguments)."""
+    from paper_2501_17792_gb300 import build
+    path = build.build(checks=True)
+    assert os.path.basename(path) == "libcrowdsplat_checks.so" and path != build.LIB
+    L = C.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    from paper_2501_17792_gb300 import binding
+    L.cs_debug_checks.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    assert L.cs_debug_checks(None, None, None) == binding.CS_ERR_ARG
+
+
 def test_library_is_built_for_sm103a():
     from paper_2501_17792_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
