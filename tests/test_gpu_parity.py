@@ -424,6 +424,15 @@ def test_row_windows_stitch_to_the_full_frame_bit_for_bit():
     # a column window too, and the windows the library refuses
     cam = dataclasses.replace(sc.camera, width=128, win_x0=96, full_width=320, full_height=180)
     assert np.array_equal(r.render(cam).cpu().numpy(), full[:, 96:224])
+    # the same with every short list composited as a whole-tile item
+    r.debug_blend_items(binding.CS_BLEND_ITEMS_TILES)
+    full_t = render(r, sc)
+    parts = [r.render(shard.sub_camera(sc.camera, r0, r1)).cpu().numpy()
+             for r0, r1 in shard.row_ranges(sc.camera.height, 3)]
+    assert np.array_equal(np.concatenate(parts, 0), full_t)
+    assert np.array_equal(r.render(cam).cpu().numpy(), full_t[:, 96:224])
+    assert np.abs(full_t - full).max() <= PU.TOL_MAX_ABS  # the schedules differ in rounding order only
+    r.debug_blend_items(binding.CS_BLEND_ITEMS_AUTO)
     for bad in (dict(win_y0=8, height=16), dict(win_y0=16, height=20), dict(win_y0=176, height=16)):
         with pytest.raises(binding.CrowdSplatError) as e:
             r.render(dataclasses.replace(sc.camera, full_width=320, full_height=180, **bad))
