@@ -69,7 +69,7 @@ struct cs_ctx {
 
     // instances
     int n_inst = 0;
-    DevBuf<int32_t> tid, vis;
+    DevBuf<int32_t> tid, vis, cull;  // cull: the cull's frame totals and group bytes
     DevBuf<float> root, pose, B, V, Cloc;
     std::vector<int32_t> tid_host_check;
     DevBuf<Group> groups;
@@ -443,7 +443,7 @@ void cs_destroy(cs_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     free_templates(ctx);
-    release(ctx->tid); release(ctx->vis); release(ctx->root); release(ctx->pose);
+    release(ctx->tid); release(ctx->vis); release(ctx->cull); release(ctx->root); release(ctx->pose);
     release(ctx->B); release(ctx->V); release(ctx->Cloc); release(ctx->groups);
     release(ctx->rec); release(ctx->key); release(ctx->ids); release(ctx->key2); release(ctx->ids2);
     release(ctx->bins); release(ctx->bins_sorted); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
@@ -800,6 +800,7 @@ int cs_set_instances(cs_ctx *ctx, int32_t n, const int32_t *template_id, const f
     size_t want = (size_t)std::max(n, 1);
     CS_TRY(ensure(ctx, ctx->tid, want, "template ids"));
     CS_TRY(ensure(ctx, ctx->vis, want, "visible list"));
+    CS_TRY(ensure(ctx, ctx->cull, cull_scratch_words(want), "cull scratch"));
     CS_TRY(ensure(ctx, ctx->root, want * 12, "roots"));
     CS_TRY(ensure(ctx, ctx->pose, want * kJoints * 3, "poses"));
     CS_TRY(ensure(ctx, ctx->B, want * kJoints * 12, "skinning transforms"));
@@ -867,6 +868,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     CS_TRY(ensure(ctx, ctx->ranges, (size_t)T, "tile ranges"));
     CS_TRY(ensure(ctx, ctx->groups, (size_t)kMaxTemplates * kMaxLevels, "groups"));
     CS_TRY(ensure(ctx, ctx->vis, (size_t)std::max(I, 1), "visible list"));
+    CS_TRY(ensure(ctx, ctx->cull, cull_scratch_words((size_t)std::max(I, 1)), "cull scratch"));
     if (timing) CS_CUDA(cudaEventRecord(ev[0], st));
 
     // 1. forward kinematics
@@ -879,7 +881,7 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     if (I > 0) {
         launched += launch_cull_group(I, ctx->n_tpl, ctx->tid.p, ctx->root.p, ctx->d_tpl, cp, ctx->lod,
                           ctx->instance_cull, ctx->V.p, ctx->Cloc.p, ctx->vis.p, ctx->groups.p,
-                          ctx->d_meta, st);
+                          ctx->d_meta, ctx->cull.p, st);
         CS_CUDA(cudaGetLastError());
         CS_CUDA(cudaMemcpyAsync(ctx->h_meta, ctx->d_meta, kMetaWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CS_CUDA(cudaMemcpyAsync(ctx->h_groups, ctx->groups.p, kMaxGroups * sizeof(Group), cudaMemcpyDeviceToHost, st));
@@ -1244,7 +1246,7 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
     int64_t tb = (int64_t)ctx->n_gauss_total * per_g + (int64_t)ctx->sh_planes_total * 16 +
                  (int64_t)ctx->n_tpl * sizeof(TemplateInfo) +
                  (int64_t)ctx->lod_idx_cap * sizeof(uint32_t);
-    int64_t ib = bytes_of(ctx->tid) + bytes_of(ctx->vis) + bytes_of(ctx->root) + bytes_of(ctx->pose) +
+    int64_t ib = bytes_of(ctx->tid) + bytes_of(ctx->vis) + bytes_of(ctx->cull) + bytes_of(ctx->root) + bytes_of(ctx->pose) +
                  bytes_of(ctx->B) + bytes_of(ctx->V) + bytes_of(ctx->Cloc) + bytes_of(ctx->groups);
     int64_t fb = bytes_of(ctx->rec) + bytes_of(ctx->key) + bytes_of(ctx->ids) + bytes_of(ctx->key2) +
                  bytes_of(ctx->ids2) + bytes_of(ctx->bins) + bytes_of(ctx->bins_sorted) + bytes_of(ctx->pair_off) + bytes_of(ctx->pval) +
@@ -1476,7 +1478,7 @@ int cs_render_static(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_fram
     if (I > 0) {
         launched += launch_cull_group(I, ctx->n_tpl, ctx->tid.p, ctx->root.p, ctx->d_tpl, cp, ctx->lod,
                                       ctx->instance_cull, ctx->V.p, ctx->Cloc.p, ctx->vis.p, ctx->groups.p,
-                                      ctx->d_meta, st);
+                                      ctx->d_meta, ctx->cull.p, st);
         CS_CUDA(cudaGetLastError());
         CS_CUDA(cudaMemcpyAsync(ctx->h_meta, ctx->d_meta, kMetaWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CS_CUDA(cudaMemcpyAsync(ctx->h_groups, ctx->groups.p, kMaxGroups * sizeof(Group), cudaMemcpyDeviceToHost, st));

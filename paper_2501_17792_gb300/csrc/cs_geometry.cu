@@ -105,23 +105,30 @@ int launch_fk(int n_inst, int n_tpl, const int32_t *tid, const float *pose, cons
 }
 
 // ---------------------------------------------------------------------------
-// LoD + instance cull + grouping: one block of 1024 threads
+// LoD + instance cull + grouping.  Every CTA takes kCullThreads instances
+// (LoD band, view transform, cull, depth bound, group byte) and adds its
+// group counts and depth bound to the frame's totals; the CTA that finishes
+// last (a ticket taken after a memory fence: no CTA waits for another)
+// turns the totals into the groups and places every visible instance.
 // ---------------------------------------------------------------------------
 
 constexpr int kCullThreads = 1024;
-constexpr int CS_MAX_INSTANCES_BYTES = 131072;  // one group byte per instance
 constexpr uint8_t kHidden = 255;
+// frame totals in the cull scratch (zeroed before the launch): group counts,
+// then the inverted bits of the lowest depth bound, the highest, the ticket
+constexpr int kCullZloInv = kMaxGroups, kCullZhi = kMaxGroups + 1, kCullTicket = kMaxGroups + 2;
 
 __global__ void __launch_bounds__(kCullThreads) k_cull_group(
     int n_inst, int n_tpl, const int32_t *__restrict__ tid, const float *__restrict__ root,
     const TemplateInfo *__restrict__ tpls, CamParams cam, LodParams lod, int do_cull,
     float *__restrict__ V, float *__restrict__ Cloc, int32_t *__restrict__ vis,
-    Group *__restrict__ groups, int32_t *__restrict__ meta) {
-    extern __shared__ uint8_t grp[];  // [n_inst] group of each instance
-    __shared__ int32_t gcount[kMaxTemplates * kMaxLevels];
-    __shared__ int32_t gslot[kMaxTemplates * kMaxLevels];
-    __shared__ int32_t wcount[kCullThreads / 32][kMaxTemplates * kMaxLevels];  // per warp and group
+    Group *__restrict__ groups, int32_t *__restrict__ meta, int32_t *__restrict__ tot,
+    uint8_t *__restrict__ grp) {
+    __shared__ int32_t gcount[kMaxGroups];
+    __shared__ int32_t gslot[kMaxGroups];
+    __shared__ int32_t wcount[kCullThreads / 32][kMaxGroups];  // per warp and group
     __shared__ uint32_t zlo_bits, zhi_bits;
+    __shared__ bool last;
     const int L = lod.n_levels;
     const int n_grp = n_tpl * L;
     for (int g = threadIdx.x; g < n_grp; g += blockDim.x) gcount[g] = 0;
@@ -131,9 +138,9 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
     }
     __syncthreads();
 
-    for (int i0 = 0; i0 < n_inst; i0 += blockDim.x) {
-        // every lane runs every round (the depth range is reduced per warp)
-        const int i = i0 + threadIdx.x;
+    {
+        // every lane of the CTA runs (the depth bound is reduced per warp)
+        const int i = (int)blockIdx.x * kCullThreads + threadIdx.x;
         uint32_t zl_bits = 0x7F7FFFFFu, zh_bits = 0u;
         if (i < n_inst) {
             const float *rt = root + (size_t)i * 12;
@@ -211,6 +218,28 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
         }
     }
     __syncthreads();
+    // this CTA's counts and depth bound into the frame totals
+    for (int g = threadIdx.x; g < n_grp; g += blockDim.x)
+        if (gcount[g]) atomicAdd(tot + g, gcount[g]);
+    if (threadIdx.x == 0) {
+        unsigned *tu = reinterpret_cast<unsigned *>(tot);
+        if (zlo_bits != 0x7F7FFFFFu) atomicMax(tu + kCullZloInv, ~zlo_bits);
+        atomicMax(tu + kCullZhi, zhi_bits);
+    }
+    __threadfence();  // the group bytes and totals before the ticket
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(tot + kCullTicket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the last CTA: the frame's totals (read past L1: other CTAs wrote them)
+    for (int g = threadIdx.x; g < n_grp; g += blockDim.x) gcount[g] = __ldcg(tot + g);
+    if (threadIdx.x == 0) {
+        const uint32_t zinv = (uint32_t)__ldcg(tot + kCullZloInv);
+        zlo_bits = zinv ? ~zinv : 0x7F7FFFFFu;
+        zhi_bits = max((uint32_t)__ldcg(tot + kCullZhi), __float_as_uint(cam.near_z));
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         int slot = 0, ng = 0;
         long long splat = 0, blocks = 0;
@@ -251,7 +280,7 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i0 = 0; i0 < n_inst; i0 += kCullThreads) {
         const int i = i0 + threadIdx.x;
-        const int g = i < n_inst ? grp[i] : kHidden;
+        const int g = i < n_inst ? __ldcg(grp + i) : kHidden;
         const unsigned peers = __match_any_sync(0xffffffffu, g);
         for (int k = lane; k < n_grp; k += 32) wcount[warp][k] = 0;
         __syncwarp();
@@ -273,22 +302,17 @@ __global__ void __launch_bounds__(kCullThreads) k_cull_group(
     }
 }
 
+size_t cull_scratch_words(size_t n_inst) { return kMaxGroups + 3 + (n_inst + 3) / 4; }
+
 int launch_cull_group(int n_inst, int n_tpl, const int32_t *tid, const float *root,
                        const TemplateInfo *tpls, const CamParams &cam, const LodParams &lod,
                        int do_cull, float *V, float *Cloc, int32_t *vis, Group *groups,
-                       int32_t *meta, cudaStream_t st) {
-    size_t smem = (size_t)(n_inst > 0 ? n_inst : 1);
-    // the group bytes (dynamic) and the per-warp group counts (static,
-    // 32 KB) exceed the default 48 KB from about 14,000 instances on
-    static int configured_device = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (configured_device != dev) {
-        cudaFuncSetAttribute(k_cull_group, cudaFuncAttributeMaxDynamicSharedMemorySize, CS_MAX_INSTANCES_BYTES);
-        configured_device = dev;
-    }
-    k_cull_group<<<1, kCullThreads, smem, st>>>(n_inst, n_tpl, tid, root, tpls, cam, lod, do_cull,
-                                                V, Cloc, vis, groups, meta);
+                       int32_t *meta, int32_t *scratch, cudaStream_t st) {
+    if (cudaMemsetAsync(scratch, 0, (kMaxGroups + 3) * sizeof(int32_t), st) != cudaSuccess) return -1;
+    const unsigned blocks = (unsigned)((n_inst + kCullThreads - 1) / kCullThreads);
+    k_cull_group<<<blocks > 0 ? blocks : 1u, kCullThreads, 0, st>>>(
+        n_inst, n_tpl, tid, root, tpls, cam, lod, do_cull, V, Cloc, vis, groups, meta, scratch,
+        reinterpret_cast<uint8_t *>(scratch + kMaxGroups + 3));
     return 1;
 }
 

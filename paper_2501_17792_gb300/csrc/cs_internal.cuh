@@ -287,10 +287,15 @@ int launch_contrib_to_template(int n_splats, const Group *groups, int n_groups, 
 // ---- geometry (cs_geometry.cu) ----
 int launch_fk(int n_inst, int n_tpl, const int32_t *tid, const float *pose, const TemplateInfo *tpls,
               int max_depth, float *B, cudaStream_t st);
+// Cull scratch of n instances (frame totals, then a group byte per
+// instance), in 4-byte words.
+size_t cull_scratch_words(size_t n_inst);
+// Returns the kernels launched, or -1 when the scratch could not be cleared
+// (the CUDA error is then cudaGetLastError's).
 int launch_cull_group(int n_inst, int n_tpl, const int32_t *tid, const float *root,
                        const TemplateInfo *tpls, const CamParams &cam, const LodParams &lod,
                        int do_cull, float *V, float *Cloc, int32_t *vis, Group *groups,
-                       int32_t *meta, cudaStream_t st);
+                       int32_t *meta, int32_t *scratch, cudaStream_t st);
 int launch_project(int n_blocks, const Group *groups, const Group *groups_host, int n_groups,
                    const TemplateInfo *tpl_host, const int32_t *vis, const float *B, const float *V,
                    const float *root, const TemplateArrays &ta, const TemplateInfo *tpls,
