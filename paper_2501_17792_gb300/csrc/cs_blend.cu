@@ -49,6 +49,7 @@ constexpr int kBlockW = kBlendBlockW, kBlockH = kBlendBlockH;  // pixels per war
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr uint32_t kBudget = kBlendBudget;  // pairs of pass 1 per tile
 constexpr uint32_t kChunk = kBlendChunk;    // pairs per pass-2 chunk
+constexpr size_t kChunkGrid = 8192;         // CTAs of the chunk and fix-up grids at most
 
 // e^q evaluated as 2^(q log2 e) on the hardware ex2 unit
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -619,21 +620,24 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_chunks(int tiles_x, int
                                                                 const float4 *__restrict__ rec,
                                                                 BlendWork work) {
     __shared__ BlendShared<> sh;
-    const uint32_t w = blockIdx.x;
-    if (w >= (uint32_t)work.meta[1]) return;
-    const int slot = work.chunk_slot[w];
-    if (work.cand_done[slot]) return;
-    const int tile = work.cand_tile[slot];
-    const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
-    const uint2 rg = ranges[tile];
-    if (!in_bounds(rg.y <= work.n_pairs, kChkPair)) return;
-    const uint32_t c = w - work.cand_chunk0[slot];
-    const uint32_t start = rg.x + kBudget + c * kChunk;
-    const uint32_t end = min(rg.y, start + kChunk);
-    const float4 s1 = work.state[(size_t)slot * kBlendThreads + threadIdx.x];
-    Pixel px{1.0f, 0.0f, 0.0f, 0.0f, 0u, !g.inside || s1.w < 0.0f, false};
-    composite_range(sh, start, end, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
-    work.part[(size_t)w * kBlendThreads + threadIdx.x] = make_float4(px.r, px.g, px.b, px.stopped ? -px.T : px.T);
+    // chunk w of the frame, grid-stride (the grid is capped, not sized for
+    // the worst case)
+    for (uint32_t w = blockIdx.x; w < (uint32_t)work.meta[1]; w += gridDim.x) {
+        const int slot = work.chunk_slot[w];
+        if (work.cand_done[slot]) continue;
+        const int tile = work.cand_tile[slot];
+        const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
+        const uint2 rg = ranges[tile];
+        if (!in_bounds(rg.y <= work.n_pairs, kChkPair)) continue;
+        const uint32_t c = w - work.cand_chunk0[slot];
+        const uint32_t start = rg.x + kBudget + c * kChunk;
+        const uint32_t end = min(rg.y, start + kChunk);
+        const float4 s1 = work.state[(size_t)slot * kBlendThreads + threadIdx.x];
+        Pixel px{1.0f, 0.0f, 0.0f, 0.0f, 0u, !g.inside || s1.w < 0.0f, false};
+        composite_range(sh, start, end, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
+        work.part[(size_t)w * kBlendThreads + threadIdx.x] = make_float4(px.r, px.g, px.b, px.stopped ? -px.T : px.T);
+        __syncthreads();  // the staging buffers are reused by the next chunk
+    }
 }
 
 // Merge: pass-1 state then the chunks in depth order, per pixel, up to the
@@ -691,22 +695,23 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W,
                                                              const float4 *__restrict__ rec,
                                                              float4 *__restrict__ out, BlendWork work) {
     __shared__ BlendShared<> sh;
-    const uint32_t w = blockIdx.x;
-    if (w >= (uint32_t)work.meta[1]) return;
-    const int slot = work.chunk_slot[w];
-    if (work.cand_done[slot]) return;
-    const size_t pix = (size_t)slot * kBlendThreads + threadIdx.x;
-    const bool mine = work.stop[pix] == (int32_t)w;
-    if (__syncthreads_count(mine) == 0) return;
-    const int tile = work.cand_tile[slot];
-    const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
-    const uint2 rg = ranges[tile];
-    if (!in_bounds(rg.y <= work.n_pairs, kChkPair)) return;
-    const float4 sb = mine ? work.state[pix] : make_float4(0.f, 0.f, 0.f, 1.f);
-    Pixel px{sb.w, sb.x, sb.y, sb.z, 0u, !mine, false};
-    const uint32_t start = rg.x + kBudget + (w - work.cand_chunk0[slot]) * kChunk;
-    composite_range(sh, start, min(rg.y, start + kChunk), pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
-    if (mine && g.inside) out[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, 1.0f - px.T);
+    for (uint32_t w = blockIdx.x; w < (uint32_t)work.meta[1]; w += gridDim.x) {
+        const int slot = work.chunk_slot[w];
+        if (work.cand_done[slot]) continue;
+        const size_t pix = (size_t)slot * kBlendThreads + threadIdx.x;
+        const bool mine = work.stop[pix] == (int32_t)w;
+        if (__syncthreads_count(mine) == 0) continue;
+        const int tile = work.cand_tile[slot];
+        const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
+        const uint2 rg = ranges[tile];
+        if (!in_bounds(rg.y <= work.n_pairs, kChkPair)) continue;
+        const float4 sb = mine ? work.state[pix] : make_float4(0.f, 0.f, 0.f, 1.f);
+        Pixel px{sb.w, sb.x, sb.y, sb.z, 0u, !mine, false};
+        const uint32_t start = rg.x + kBudget + (w - work.cand_chunk0[slot]) * kChunk;
+        composite_range(sh, start, min(rg.y, start + kChunk), pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
+        if (mine && g.inside) out[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, 1.0f - px.T);
+        __syncthreads();  // the staging buffers are reused by the next chunk
+    }
 }
 
 // Plan, part 1 (one thread per tile; meta zeroed before): tiles per list
@@ -803,9 +808,13 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
     const int launched = 3;
     // no tile has pairs left after pass 1
     if (n_pairs <= kBudget) return launched;
-    k_blend_chunks<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);
+    // chunk grids capped at kChunkGrid CTAs (grid-stride over the frame's
+    // chunks): a frame whose lists all end within the pass-1 budget does not
+    // pay for a worst-case grid of CTAs that return at once
+    const unsigned chunk_grid = (unsigned)std::min<size_t>(max_chunks, kChunkGrid);
+    k_blend_chunks<<<chunk_grid, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);
     k_blend_merge<<<(unsigned)max_cand, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, out, work);
-    k_blend_fix<<<(unsigned)max_chunks, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+    k_blend_fix<<<chunk_grid, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
     return launched + 3;
 }
 
