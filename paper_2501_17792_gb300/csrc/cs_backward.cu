@@ -54,14 +54,9 @@ struct BwdShared {
     float4 s3[kBwdThreads];  // conic A, B, C, -
     uint32_t sid[kBwdThreads];
     uint8_t mask[kBwdThreads];
+    float gsum[kBwdThreads][9];  // the batch's gradients summed over the CTA's warps
     uint32_t max_end;
 };
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 __global__ void __launch_bounds__(kBwdThreads) k_blend_backward(
     int tiles_x, int W, int H, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
@@ -102,8 +97,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_backward(
             const float4 *r = rec + (size_t)s * kRecVec;
             const float4 q = __ldg(r), a = __ldg(r + 1), c = __ldg(r + 2);  // {rx, ry, log2 o, C}, {u, v, A, B}, {rgb, radius}
             sh.s0[tid] = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
-            // opacity from its logarithm (within an ulp): only gradients use it
-            sh.s1[tid] = make_float4(-0.5f * kLog2e * q.w, q.z, c.w, exp2f(q.z));
+            // 1 / opacity from its logarithm: only the opacity gradient uses it
+            sh.s1[tid] = make_float4(-0.5f * kLog2e * q.w, q.z, c.w, exp2f(-q.z));
             sh.s2[tid] = c;
             sh.s3[tid] = make_float4(a.z, a.w, q.w, 0.f);
             sh.sid[tid] = s;
@@ -118,6 +113,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_backward(
             }
             sh.mask[tid] = (uint8_t)m;
         }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) sh.gsum[tid][c] = 0.0f;
         __syncthreads();
         for (int j = (int)nb - 1; j >= 0; --j) {
             if (!(sh.mask[j] & wbit)) continue;  // uniform per warp
@@ -138,15 +135,18 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_backward(
                             contributes = true;
                             const float4 c = sh.s2[j];
                             const float4 k = sh.s3[j];
-                            const float om = 1.0f - alpha;
-                            const float Tb = T / om;  // transmittance in front of this splat
+                            // one reciprocal of 1 - alpha for the five quotients (off by
+                            // an ulp from dividing each): the walk back divides T by it
+                            // at every splat, so the chain waits on a multiply only
+                            const float iom = 1.0f / (1.0f - alpha);
+                            const float Tb = T * iom;  // transmittance in front of this splat
                             const float wgt = alpha * Tb;
                             gr = wgt * g.x;
                             gg = wgt * g.y;
                             gb = wgt * g.z;
                             // d pixel / d alpha: own colour minus what it hides, and the alpha channel
-                            const float galpha = g.x * (c.x * Tb - Sr / om) + g.y * (c.y * Tb - Sg / om) +
-                                                 g.z * (c.z * Tb - Sb / om) + g.w * (Tf / om);
+                            const float galpha = g.x * (c.x * Tb - Sr * iom) + g.y * (c.y * Tb - Sg * iom) +
+                                                 g.z * (c.z * Tb - Sb * iom) + g.w * (Tf * iom);
                             Sr += c.x * wgt;
                             Sg += c.y * wgt;
                             Sb += c.z * wgt;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_backward(
                             if (araw < 0.99f) {
                                 // alpha = o e^q: d alpha / d q = alpha, d alpha / d o = e^q
                                 const float gq = galpha * araw;
-                                go = galpha * (b.w > 0.0f ? araw / b.w : 0.0f);
+                                go = galpha * araw * b.w;
                                 gA = -0.5f * dx * dx * gq;
                                 gB = -dx * dy * gq;
                                 gC = -0.5f * dy * dy * gq;
@@ -166,27 +166,36 @@ __global__ void __launch_bounds__(kBwdThreads) k_blend_backward(
                 }
             }
             if (__any_sync(0xffffffffu, contributes)) {
-                gu = warp_sum(gu);
-                gv = warp_sum(gv);
-                gA = warp_sum(gA);
-                gB = warp_sum(gB);
-                gC = warp_sum(gC);
-                go = warp_sum(go);
-                gr = warp_sum(gr);
-                gg = warp_sum(gg);
-                gb = warp_sum(gb);
-                if (lane == 0) {
-                    float *d = reinterpret_cast<float *>(dsplat + (size_t)sh.sid[j] * 3);
-                    atomicAdd(d + 0, gu);
-                    atomicAdd(d + 1, gv);
-                    atomicAdd(d + 2, gA);
-                    atomicAdd(d + 3, gB);
-                    atomicAdd(d + 4, gC);
-                    atomicAdd(d + 5, go);
-                    atomicAdd(d + 6, gr);
-                    atomicAdd(d + 7, gg);
-                    atomicAdd(d + 8, gb);
+                // the warp's sums of the nine gradients by a reduce-scatter
+                // butterfly (16 shuffles instead of 9 x 5): at the step of
+                // distance 16, 8, 4, 2 each lane keeps half of its values
+                // and adds its partner's copy of that half; the step of
+                // distance 1 completes the sum.  Lane l then holds gradient
+                // (l >> 1) & 15, and nine lanes add theirs at once into the
+                // batch's shared sums.
+                float v[16] = {gu, gv, gA, gB, gC, go, gr, gg, gb, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int half = 8; half >= 1; half >>= 1) {
+                    const bool upper = (lane & (2 * half)) != 0;
+#pragma unroll
+                    for (int i = 0; i < half; ++i) {
+                        const float recv = __shfl_xor_sync(0xffffffffu, upper ? v[i] : v[i + half], 2 * half);
+                        v[i] = (upper ? v[i + half] : v[i]) + recv;
+                    }
                 }
+                v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+                const int comp = (lane >> 1) & 15;
+                if ((lane & 1) == 0 && comp < 9) atomicAdd(&sh.gsum[j][comp], v[0]);
+            }
+        }
+        // one set of global adds per (tile, splat) instead of per warp
+        __syncthreads();
+        if ((uint32_t)tid < nb) {
+            float *d = reinterpret_cast<float *>(dsplat + (size_t)sh.sid[tid] * 3);
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                const float x = sh.gsum[tid][c];
+                if (x != 0.0f) atomicAdd(d + c, x);
             }
         }
         hi = lo;
