@@ -87,8 +87,9 @@ struct cs_ctx {
     uint32_t key_lo = 0;     // the last frame's depth-key offset
     DevBuf<float> contrib_s;  // per-splat compositing weight sums (cs_render_contrib)
     // training frame (cs_render_train / cs_backward)
-    DevBuf<uint32_t> px_end;
-    DevBuf<float> px_T, g_cov, g_B, g_dummy;
+    DevBuf<uint32_t> px_end, bwd_cnt, bwd_chunk0, bwd_scratch;
+    DevBuf<float4> px_fin, px_bnd;  // training: final state per pixel, states at the backward chunk boundaries
+    DevBuf<float> g_cov, g_B, g_dummy;
     DevBuf<float4> dsplat;
     bool train_valid = false;
     CamParams train_cp{};
@@ -449,7 +450,8 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->bins); release(ctx->bins_sorted); release(ctx->pair_off); release(ctx->pval); release(ctx->pval2);
     release(ctx->scratch); release(ctx->rect); release(ctx->ranges); release(ctx->ptile);
     release(ctx->ptile2); release(ctx->img); release(ctx->contrib_s); release(ctx->dbg_rec);
-    release(ctx->px_end); release(ctx->px_T); release(ctx->dsplat); release(ctx->g_cov); release(ctx->g_B);
+    release(ctx->px_end); release(ctx->px_fin); release(ctx->px_bnd); release(ctx->bwd_cnt); release(ctx->bwd_chunk0);
+    release(ctx->bwd_scratch); release(ctx->dsplat); release(ctx->g_cov); release(ctx->g_B);
     release(ctx->g_dummy);
     release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_pp); release(ctx->bw_cslot); release(ctx->bw_chunk0);
     release(ctx->bw_done); release(ctx->bw_state); release(ctx->bw_part);
@@ -992,9 +994,11 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
     if (train) {
         const size_t npix = (size_t)cam->width * cam->height;
         CS_TRY(ensure(ctx, ctx->px_end, npix, "per-pixel list ends"));
-        CS_TRY(ensure(ctx, ctx->px_T, npix, "per-pixel transmittance"));
+        CS_TRY(ensure(ctx, ctx->px_fin, npix, "per-pixel final state"));
+        CS_TRY(ensure(ctx, ctx->px_bnd, bwd_boundary_slots((size_t)P) * 256, "chunk-boundary states"));
         bw.px_end = ctx->px_end.p;
-        bw.px_T = ctx->px_T.p;
+        bw.px_fin = ctx->px_fin.p;
+        bw.px_bnd = ctx->px_bnd.p;
     }
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ctx->ranges.p, pval, ctx->rec.p, out,
                              bw, (uint32_t)P, st);
@@ -1113,6 +1117,10 @@ int cs_backward(cs_ctx *ctx, const float *dl_drgba, const cs_grads *grads) {
     const size_t S = (size_t)std::max<int64_t>(ctx->S, 1), G = std::max<size_t>(ctx->n_gauss_total, 1);
     const size_t I = (size_t)std::max(ctx->n_inst, 1);
     CS_TRY(ensure(ctx, ctx->dsplat, S * 3, "splat gradients"));
+    const size_t nt = (size_t)std::max(cp.tiles_x * cp.tiles_y, 1);
+    CS_TRY(ensure(ctx, ctx->bwd_cnt, nt, "backward chunk counts"));
+    CS_TRY(ensure(ctx, ctx->bwd_chunk0, nt + 1, "backward chunk offsets"));
+    CS_TRY(ensure(ctx, ctx->bwd_scratch, scan_scratch_words(nt), "backward scan scratch"));
     CS_TRY(ensure(ctx, ctx->g_cov, G * 6, "covariance gradients"));
     CS_TRY(ensure(ctx, ctx->g_B, I * kJoints * 12, "skinning-transform gradients"));
     // destinations the caller does not want go to one scratch buffer
@@ -1130,7 +1138,11 @@ int cs_backward(cs_ctx *ctx, const float *dl_drgba, const cs_grads *grads) {
     a.pval = ctx->pair_buf ? ctx->pval2.p : ctx->pval.p;
     a.rec = ctx->rec.p;
     a.px_end = ctx->px_end.p;
-    a.px_T = ctx->px_T.p;
+    a.px_fin = ctx->px_fin.p;
+    a.px_bnd = ctx->px_bnd.p;
+    a.chunk_cnt = ctx->bwd_cnt.p;
+    a.chunk0 = ctx->bwd_chunk0.p;
+    a.scan_scratch = ctx->bwd_scratch.p;
     a.dl_drgba = reinterpret_cast<const float4 *>(dl_drgba);
     a.dsplat = ctx->dsplat.p;
     a.proj_blocks = ctx->S > 0 ? ctx->train_proj_blocks : 0;
@@ -1254,7 +1266,8 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
                  bytes_of(ctx->ptile) + bytes_of(ctx->ptile2) + bytes_of(ctx->img) + bytes_of(ctx->bw_slot) +
                  bytes_of(ctx->bw_tile) + bytes_of(ctx->bw_meta) + bytes_of(ctx->bw_chunk0) + bytes_of(ctx->bw_done) +
                  bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop) + bytes_of(ctx->bw_pp) + bytes_of(ctx->bw_cslot) + bytes_of(ctx->contrib_s) +
-                 bytes_of(ctx->px_end) + bytes_of(ctx->px_T) + bytes_of(ctx->dsplat) + bytes_of(ctx->g_cov) +
+                 bytes_of(ctx->px_end) + bytes_of(ctx->px_fin) + bytes_of(ctx->px_bnd) + bytes_of(ctx->bwd_cnt) +
+                 bytes_of(ctx->bwd_chunk0) + bytes_of(ctx->bwd_scratch) + bytes_of(ctx->dsplat) + bytes_of(ctx->g_cov) +
                  bytes_of(ctx->g_B) + bytes_of(ctx->g_dummy);
     out->template_bytes = tb;
     out->instance_bytes = ib;

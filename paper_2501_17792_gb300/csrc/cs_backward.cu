@@ -2,11 +2,14 @@
 // projection, SH colour, linear blend skinning and forward kinematics.
 //
 // The loss enters as dL/d(pixel RGBA).  Kernels, in order:
-//   k_blend_backward     one CTA per 16x16 tile: each pixel walks its
-//                        contributors back to front (recomputing alpha and the
-//                        transmittance from the stored final value) and
-//                        produces dL/d(u, v, conic, opacity, rgb) per splat,
-//                        summed over a warp's pixels before one atomic add
+//   k_blend_backward     one CTA per chunk of kBwdChunk pairs of a 16x16
+//                        tile's list: each pixel walks its contributors in
+//                        the chunk back to front (recomputing alpha, and the
+//                        transmittance from the state the forward kept at the
+//                        chunk's end, or from its final state), producing
+//                        dL/d(u, v, conic, opacity, rgb) per splat, summed
+//                        over the tile's pixels before the atomic adds; the
+//                        chunks of one list run in parallel
 //   k_project_backward   one CTA per (instance, 256 Gaussians), like the
 //                        forward projection: recompute, then the chain rule to
 //                        the template mean, canonical covariance, opacity and
@@ -58,35 +61,76 @@ struct BwdShared {
     uint32_t max_end;
 };
 
+// Backward chunks of each tile's list: ceil(n / kBwdChunk).
+__global__ void __launch_bounds__(256) k_bwd_chunk_counts(int n_tiles, const uint2 *__restrict__ ranges,
+                                                          uint32_t *__restrict__ cnt) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tiles) cnt[t] = (ranges[t].y - ranges[t].x + kBwdChunk - 1) / kBwdChunk;
+}
+
 __global__ void __launch_bounds__(kBwdThreads) k_blend_backward(
     int tiles_x, int W, int H, const uint2 *__restrict__ ranges, const uint32_t *__restrict__ pval,
-    const float4 *__restrict__ rec, const uint32_t *__restrict__ px_end, const float *__restrict__ px_T,
+    const float4 *__restrict__ rec, const uint32_t *__restrict__ px_end, const float4 *__restrict__ px_fin,
+    const float4 *__restrict__ px_bnd, const uint32_t *__restrict__ chunk0, int n_tiles,
     const float4 *__restrict__ dl_drgba, float4 *__restrict__ dsplat) {
     __shared__ BwdShared sh;
-    const int tile = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    __shared__ int s_tile;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // chunk w of the frame: the tile whose chunks [chunk0[t], chunk0[t + 1]) hold it
+    const uint32_t w = blockIdx.x;
+    if (w >= chunk0[n_tiles]) return;
+    if (tid == 0) {
+        int lo = 0, hi = n_tiles - 1;  // the last t with chunk0[t] <= w
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (chunk0[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        s_tile = lo;
+    }
+    __syncthreads();
+    const int tile = s_tile;
     const int tx0 = (tile % tiles_x) * kTile, ty0 = (tile / tiles_x) * kTile;
     // pixel layout of the forward: warp w covers an 8x4 block
     const int bx = (warp & 1) * kBlockW, by = (warp >> 1) * kBlockH;
     const int px = tx0 + bx + (lane % kBlockW), py = ty0 + by + (lane / kBlockW);
     const bool inside = px < W && py < H;
     const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-    const uint2 rg = ranges[tile];
+    const uint2 rg0 = ranges[tile];
+    // this chunk: pairs [a, b) of the tile's list
+    const uint32_t a_lo = rg0.x + (w - chunk0[tile]) * kBwdChunk;
+    const uint32_t b_hi = min(rg0.y, a_lo + kBwdChunk);
+    const uint2 rg = make_uint2(a_lo, b_hi);
     uint32_t end = rg.x;
     float Tf = 1.0f;
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    float T = 1.0f;                      // transmittance behind the current splat
+    float Sr = 0.f, Sg = 0.f, Sb = 0.f;  // colour composited behind it
     if (inside) {
         const size_t p = (size_t)py * W + px;
-        end = px_end[p];
-        Tf = px_T[p];
+        const uint32_t e = px_end[p];
+        const float4 fin = px_fin[p];
+        Tf = fin.w;
         g = dl_drgba[p];
+        end = min(e, b_hi);
+        if (e <= b_hi) {
+            // the pixel's list ends in this chunk: the walk starts from its final state
+            T = Tf;
+        } else if (end > rg.x) {
+            // it goes on past the chunk: the state the forward kept at b, and
+            // the colour composited behind b (final minus in front of b)
+            const float4 st = px_bnd[(size_t)(b_hi / kBwdChunk) * kBwdThreads + tid];
+            T = st.w;
+            Sr = fin.x - st.x;
+            Sg = fin.y - st.y;
+            Sb = fin.z - st.z;
+        }
     }
     if (tid == 0) sh.max_end = rg.x;
     __syncthreads();
     atomicMax(&sh.max_end, end);
     __syncthreads();
     const uint32_t hi_all = sh.max_end;
-    float T = Tf;                        // transmittance behind the current splat
-    float Sr = 0.f, Sg = 0.f, Sb = 0.f;  // colour composited behind it
     const uint32_t wbit = 1u << warp;
     for (uint32_t hi = hi_all; hi > rg.x;) {
         const uint32_t lo = hi - rg.x > (uint32_t)kBwdThreads ? hi - kBwdThreads : rg.x;
@@ -694,8 +738,13 @@ int launch_backward(const BackwardArgs &a, cudaStream_t st) {
     int launched = 0;
     const int T = a.tiles_x * a.tiles_y;
     if (T > 0 && a.n_pairs > 0) {
-        k_blend_backward<<<T, kBwdThreads, 0, st>>>(a.tiles_x, a.W, a.H, a.ranges, a.pval, a.rec, a.px_end, a.px_T,
-                                                     a.dl_drgba, a.dsplat);
+        // chunks of kBwdChunk pairs per tile, numbered tile by tile; one CTA
+        // per chunk walks it back to front from the state the forward kept
+        k_bwd_chunk_counts<<<(T + 255) / 256, 256, 0, st>>>(T, a.ranges, a.chunk_cnt);
+        launched += 1 + exclusive_scan(a.chunk_cnt, nullptr, a.chunk0, (uint32_t)T, a.scan_scratch, st);
+        const unsigned grid = a.n_pairs / kBwdChunk + (unsigned)T;  // at least the chunks of the frame
+        k_blend_backward<<<grid, kBwdThreads, 0, st>>>(a.tiles_x, a.W, a.H, a.ranges, a.pval, a.rec, a.px_end,
+                                                        a.px_fin, a.px_bnd, a.chunk0, T, a.dl_drgba, a.dsplat);
         ++launched;
     }
     if (a.proj_blocks > 0) {

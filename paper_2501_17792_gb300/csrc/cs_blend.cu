@@ -50,6 +50,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr uint32_t kBudget = kBlendBudget;  // pairs of pass 1 per tile
 constexpr uint32_t kChunk = kBlendChunk;    // pairs per pass-2 chunk
 constexpr size_t kChunkGrid = 8192;         // CTAs of the chunk and fix-up grids at most
+static_assert(kBwdChunk % kBlendThreads == 0, "backward chunk boundaries fall on batch starts");
 
 // e^q evaluated as 2^(q log2 e) on the hardware ex2 unit
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -106,7 +107,8 @@ __device__ __forceinline__ void composite_range(BlendShared<kT> &sh, uint32_t st
                                                 const uint32_t *__restrict__ pval,
                                                 const float4 *__restrict__ rec, int tx0, int ty0,
                                                 float fpx, float fpy, Pixel &px,
-                                                float *__restrict__ contrib = nullptr, int brow0 = 0) {
+                                                float *__restrict__ contrib = nullptr, int brow0 = 0,
+                                                float4 *__restrict__ bnd = nullptr) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t wbit = 1u << warp;
     auto stage = [&](const StagedRecord &r, int h) {
@@ -137,6 +139,10 @@ __device__ __forceinline__ void composite_range(BlendShared<kT> &sh, uint32_t st
     int h = 0;
     for (uint32_t base = start; base < end; base += kT, h ^= 1) {
         const int nb = (int)min((uint32_t)kT, end - base);
+        // training: the pixel's state before pair base at every backward
+        // chunk boundary (kBwdChunk is a multiple of the batch)
+        if (kMode == 2 && base != start && (base - start) % kBwdChunk == 0)
+            bnd[(size_t)(base / kBwdChunk) * kT + threadIdx.x] = make_float4(px.r, px.g, px.b, px.T);
         for (int c = 0; c < nb; c += 32) {
             if (__all_sync(0xffffffffu, px.done)) break;
             const bool mine = (sh.mask[h][c + lane] & wbit) != 0 && c + lane < nb;
@@ -219,10 +225,11 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
     if (!in_bounds(rg.x <= rg.y && rg.y <= work.n_pairs, kChkPair)) rg.y = rg.x;
     Pixel px{1.0f, 0.0f, 0.0f, 0.0f, rg.x, !g.inside, false};
     const uint32_t end1 = rg.y - rg.x > kBudget && kMode == 0 ? rg.x + kBudget : rg.y;
-    composite_range<kMode, kT>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib, w0 / 2);
+    composite_range<kMode, kT>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib, w0 / 2,
+                               work.px_bnd);
     if (kMode == 2 && g.inside) {
         work.px_end[(size_t)g.py * W + g.px] = px.last;
-        work.px_T[(size_t)g.py * W + g.px] = px.T;
+        work.px_fin[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, px.T);
     }
     if (end1 < rg.y && in_bounds(work.cand_slot[tile] >= 0, kChkSlot)) {
         // pairs remain: record the pixel state for pass 2 and the merge (the

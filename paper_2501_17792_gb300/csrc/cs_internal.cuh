@@ -373,9 +373,14 @@ struct BlendWork {
     // alpha * T (added to); lists are then composited in one pass
     float *contrib;
     // when set (training forward): per pixel, one past the index of its last
-    // composited pair and its final transmittance; one pass as well
+    // composited pair and its final state (r, g, b, T); one pass as well.
+    // px_bnd: every pixel's state (r, g, b, T) before pair b of its tile's
+    // list, for every b = start + k kBwdChunk (k >= 1) the pass reaches, at
+    // px_bnd[(b / kBwdChunk) * 256 + pixel of the tile] (b / kBwdChunk is
+    // distinct for all such b of a frame: lists are disjoint)
     uint32_t *px_end;
-    float *px_T;
+    float4 *px_fin;
+    float4 *px_bnd;
     int32_t *pp_tile;     // [tiles]
     int32_t *chunk_slot;  // [chunks]: the slot of each pass-2 chunk
     int32_t ox, oy;       // window origin: pixel (i, j) has its centre at (ox + i + 0.5, oy + j + 0.5)
@@ -389,6 +394,9 @@ constexpr int kBlendMetaWords = kBlendCursorAt + kBlendClasses;
 constexpr int kBlendBlockW = 8, kBlendBlockH = 4;  // pixels of one warp in a 16x16 tile
 constexpr uint32_t kBlendBudget = 32768;  // pairs composited by pass 1 per tile
 constexpr uint32_t kBlendChunk = 1024;   // pairs per pass-2 chunk
+constexpr uint32_t kBwdChunk = 1024;     // pairs per chunk of the compositing backward
+// boundary-state slots of a training frame of n_pairs pairs
+constexpr size_t bwd_boundary_slots(size_t n_pairs) { return n_pairs / kBwdChunk + 2; }
 constexpr size_t blend_max_slots(size_t n_tiles, size_t n_pairs) {
     return n_tiles < n_pairs / kBlendBudget + 1 ? n_tiles : n_pairs / kBlendBudget + 1;
 }
@@ -413,7 +421,11 @@ struct BackwardArgs {
     const uint32_t *pval;
     const float4 *rec;
     const uint32_t *px_end;
-    const float *px_T;
+    const float4 *px_fin;   // final (r, g, b, T) per pixel
+    const float4 *px_bnd;   // states at the chunk boundaries (BlendWork::px_bnd)
+    uint32_t *chunk_cnt;    // [tiles + 1] scratch: backward chunks per tile, then their exclusive scan
+    uint32_t *chunk0;
+    uint32_t *scan_scratch;
     const float4 *dl_drgba;
     float4 *dsplat;  // [S][3]: du, dv, dA, dB | dC, do, dr, dg | db, -, -, -
     int proj_blocks;
