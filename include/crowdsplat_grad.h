@@ -49,9 +49,9 @@ typedef struct {
 /* cs_render that also keeps, per pixel, where its list of composited splats
  * ends, its final colour and transmittance, and its state at every 1,024th
  * pair of its tile's list, so that cs_backward can walk each 1,024-pair
- * chunk of a list in parallel (lists are composited in one pass, so the
- * frame is slower than cs_render's; the image is the same up to float
- * rounding order).  The state stays valid until the next render or any
+ * chunk of a list in parallel (every list is composited in such chunks,
+ * merged per pixel in order, so the frame is slower than cs_render's; the
+ * image is the same up to float rounding order).  The state stays valid until the next render or any
  * change of templates, LoD, subsets or instances.  Same arguments and
  * errors as cs_render; CS_ERR_STATE with BF16 template storage. */
 int cs_render_train(cs_ctx *ctx, const cs_camera *cam, float *rgba_out, cs_frame_stats *stats);

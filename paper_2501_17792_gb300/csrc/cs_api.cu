@@ -89,6 +89,9 @@ struct cs_ctx {
     // training frame (cs_render_train / cs_backward)
     DevBuf<uint32_t> px_end, bwd_cnt, bwd_chunk0, bwd_scratch;
     DevBuf<float4> px_fin, px_bnd;  // training: final state per pixel, states at the backward chunk boundaries
+    DevBuf<float4> t_part, t_state;  // training forward: chunk partials, state before each pixel's stopping chunk
+    DevBuf<uint32_t> t_last, t_slast;
+    DevBuf<int32_t> t_stop;
     DevBuf<float> g_cov, g_B, g_dummy;
     DevBuf<float4> dsplat;
     bool train_valid = false;
@@ -451,7 +454,8 @@ void cs_destroy(cs_ctx *ctx) {
     release(ctx->scratch); release(ctx->rect); release(ctx->ranges); release(ctx->ptile);
     release(ctx->ptile2); release(ctx->img); release(ctx->contrib_s); release(ctx->dbg_rec);
     release(ctx->px_end); release(ctx->px_fin); release(ctx->px_bnd); release(ctx->bwd_cnt); release(ctx->bwd_chunk0);
-    release(ctx->bwd_scratch); release(ctx->dsplat); release(ctx->g_cov); release(ctx->g_B);
+    release(ctx->bwd_scratch); release(ctx->t_part); release(ctx->t_state); release(ctx->t_last);
+    release(ctx->t_slast); release(ctx->t_stop); release(ctx->dsplat); release(ctx->g_cov); release(ctx->g_B);
     release(ctx->g_dummy);
     release(ctx->bw_slot); release(ctx->bw_tile); release(ctx->bw_meta); release(ctx->bw_stop); release(ctx->bw_pp); release(ctx->bw_cslot); release(ctx->bw_chunk0);
     release(ctx->bw_done); release(ctx->bw_state); release(ctx->bw_part);
@@ -996,9 +1000,26 @@ static int render_impl(cs_ctx *ctx, const cs_camera *cam, float4 *out, cs_frame_
         CS_TRY(ensure(ctx, ctx->px_end, npix, "per-pixel list ends"));
         CS_TRY(ensure(ctx, ctx->px_fin, npix, "per-pixel final state"));
         CS_TRY(ensure(ctx, ctx->px_bnd, bwd_boundary_slots((size_t)P) * 256, "chunk-boundary states"));
+        const size_t nt = (size_t)std::max(T, 1), tc = train_max_chunks(nt, (size_t)P);
+        CS_TRY(ensure(ctx, ctx->bwd_cnt, nt, "training chunk counts"));
+        CS_TRY(ensure(ctx, ctx->bwd_chunk0, nt + 1, "training chunk offsets"));
+        CS_TRY(ensure(ctx, ctx->bwd_scratch, scan_scratch_words(nt), "training scan scratch"));
+        CS_TRY(ensure(ctx, ctx->t_part, tc * 256, "training chunk partials"));
+        CS_TRY(ensure(ctx, ctx->t_last, tc * 256, "training chunk ends"));
+        CS_TRY(ensure(ctx, ctx->t_state, npix, "training stop states"));
+        CS_TRY(ensure(ctx, ctx->t_slast, npix, "training stop ends"));
+        CS_TRY(ensure(ctx, ctx->t_stop, npix, "training stop chunks"));
         bw.px_end = ctx->px_end.p;
         bw.px_fin = ctx->px_fin.p;
         bw.px_bnd = ctx->px_bnd.p;
+        bw.t_cnt = ctx->bwd_cnt.p;
+        bw.t_chunk0 = ctx->bwd_chunk0.p;
+        bw.t_scan = ctx->bwd_scratch.p;
+        bw.t_part = ctx->t_part.p;
+        bw.t_last = ctx->t_last.p;
+        bw.t_state = ctx->t_state.p;
+        bw.t_slast = ctx->t_slast.p;
+        bw.t_stop = ctx->t_stop.p;
     }
     launched += launch_blend(cp.tiles_x, cp.tiles_y, cam->width, cam->height, ctx->ranges.p, pval, ctx->rec.p, out,
                              bw, (uint32_t)P, st);
@@ -1267,7 +1288,9 @@ int cs_memory_stats(cs_ctx *ctx, cs_memory_stats_t *out) {
                  bytes_of(ctx->bw_tile) + bytes_of(ctx->bw_meta) + bytes_of(ctx->bw_chunk0) + bytes_of(ctx->bw_done) +
                  bytes_of(ctx->bw_state) + bytes_of(ctx->bw_part) + bytes_of(ctx->bw_stop) + bytes_of(ctx->bw_pp) + bytes_of(ctx->bw_cslot) + bytes_of(ctx->contrib_s) +
                  bytes_of(ctx->px_end) + bytes_of(ctx->px_fin) + bytes_of(ctx->px_bnd) + bytes_of(ctx->bwd_cnt) +
-                 bytes_of(ctx->bwd_chunk0) + bytes_of(ctx->bwd_scratch) + bytes_of(ctx->dsplat) + bytes_of(ctx->g_cov) +
+                 bytes_of(ctx->bwd_chunk0) + bytes_of(ctx->bwd_scratch) + bytes_of(ctx->t_part) + bytes_of(ctx->t_last) +
+                 bytes_of(ctx->t_state) + bytes_of(ctx->t_slast) + bytes_of(ctx->t_stop) + bytes_of(ctx->dsplat) +
+                 bytes_of(ctx->g_cov) +
                  bytes_of(ctx->g_B) + bytes_of(ctx->g_dummy);
     out->template_bytes = tb;
     out->instance_bytes = ib;

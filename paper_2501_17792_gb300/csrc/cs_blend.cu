@@ -141,7 +141,7 @@ __device__ __forceinline__ void composite_range(BlendShared<kT> &sh, uint32_t st
         const int nb = (int)min((uint32_t)kT, end - base);
         // training: the pixel's state before pair base at every backward
         // chunk boundary (kBwdChunk is a multiple of the batch)
-        if (kMode == 2 && base != start && (base - start) % kBwdChunk == 0)
+        if (kMode == 2 && bnd && base != start && (base - start) % kBwdChunk == 0)
             bnd[(size_t)(base / kBwdChunk) * kT + threadIdx.x] = make_float4(px.r, px.g, px.b, px.T);
         for (int c = 0; c < nb; c += 32) {
             if (__all_sync(0xffffffffu, px.done)) break;
@@ -721,6 +721,132 @@ __global__ void __launch_bounds__(kBlendThreads) k_blend_fix(int tiles_x, int W,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Training frames: every tile's list in chunks of kBwdChunk pairs composited
+// in parallel, as the split passes of plain frames do (the operator is
+// associative), and per pixel the state at each chunk boundary, the end of
+// its composited list and its final state for the backward.
+//   k_train_counts   chunks per tile (then an exclusive scan numbers them)
+//   k_train_chunks   CTA per chunk: its composite from T = 1 for every pixel
+//                    of the tile, and one past its last composited pair
+//   k_train_merge    CTA per tile: per pixel, the chunks in order, C += T C_k,
+//                    T *= T_k, keeping the state before every chunk; up to the
+//                    chunk in which T T_k would fall below the stop threshold
+//                    (or whose partial met it from T = 1)
+//   k_train_fix      CTA per chunk: that chunk again from the pixel's true
+//                    state with the stop rule, for the pixels stopping in it
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_train_counts(int n_tiles, const uint2 *__restrict__ ranges,
+                                                      uint32_t *__restrict__ cnt) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tiles) cnt[t] = (ranges[t].y - ranges[t].x + kBwdChunk - 1) / kBwdChunk;
+}
+
+// tile of chunk w: the last t with chunk0[t] <= w (thread 0, broadcast)
+__device__ __forceinline__ int chunk_tile(const uint32_t *__restrict__ chunk0, int n_tiles, uint32_t w, int *s_tile) {
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_tiles - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (chunk0[mid] <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        *s_tile = lo;
+    }
+    __syncthreads();
+    return *s_tile;
+}
+
+__global__ void __launch_bounds__(kBlendThreads) k_train_chunks(int tiles_x, int W, int H,
+                                                                const uint2 *__restrict__ ranges,
+                                                                const uint32_t *__restrict__ pval,
+                                                                const float4 *__restrict__ rec, BlendWork work) {
+    __shared__ BlendShared<> sh;
+    __shared__ int s_tile;
+    const int n_tiles = tiles_x * ((H + kTile - 1) / kTile);
+    const uint32_t w = blockIdx.x;
+    if (w >= work.t_chunk0[n_tiles]) return;
+    const int tile = chunk_tile(work.t_chunk0, n_tiles, w, &s_tile);
+    const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
+    const uint2 rg = ranges[tile];
+    const uint32_t a = rg.x + (w - work.t_chunk0[tile]) * kBwdChunk, b = min(rg.y, a + kBwdChunk);
+    Pixel px{1.0f, 0.0f, 0.0f, 0.0f, 0u, !g.inside, false};
+    composite_range<2>(sh, a, b, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
+    work.t_part[(size_t)w * kBlendThreads + threadIdx.x] = make_float4(px.r, px.g, px.b, px.stopped ? -px.T : px.T);
+    work.t_last[(size_t)w * kBlendThreads + threadIdx.x] = px.last;
+}
+
+__global__ void __launch_bounds__(kBlendThreads) k_train_merge(int tiles_x, int W, int H,
+                                                               const uint2 *__restrict__ ranges,
+                                                               float4 *__restrict__ out, BlendWork work) {
+    const int tile = blockIdx.x;
+    const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
+    if (!g.inside) return;
+    const size_t pix = (size_t)g.py * W + g.px;
+    const uint2 rg = ranges[tile];
+    float T = 1.0f, r = 0.0f, gg = 0.0f, b = 0.0f;
+    uint32_t last = rg.x;
+    int32_t stop = -1;
+    const uint32_t c0 = work.t_chunk0[tile], c1 = work.t_chunk0[tile + 1];
+    for (uint32_t w = c0; w < c1; ++w) {
+        if (w > c0) {
+            // the state before pair a of chunk w, for the backward
+            const uint32_t a = rg.x + (w - c0) * kBwdChunk;
+            work.px_bnd[(size_t)(a / kBwdChunk) * kBlendThreads + threadIdx.x] = make_float4(r, gg, b, T);
+        }
+        const float4 p = work.t_part[(size_t)w * kBlendThreads + threadIdx.x];
+        const float Tk = fabsf(p.w);
+        if (p.w >= 0.0f && T * Tk >= 1e-4f) {
+            // no splat of the chunk meets the stop rule from this T: it applies as a whole
+            r += T * p.x;
+            gg += T * p.y;
+            b += T * p.z;
+            T *= Tk;
+            const uint32_t lk = work.t_last[(size_t)w * kBlendThreads + threadIdx.x];
+            if (lk) last = lk;
+        } else {
+            stop = (int32_t)w;
+            break;
+        }
+    }
+    work.t_stop[pix] = stop;
+    if (stop >= 0) {
+        work.t_state[pix] = make_float4(r, gg, b, T);
+        work.t_slast[pix] = last;
+    } else {
+        out[pix] = make_float4(r, gg, b, 1.0f - T);
+        work.px_end[pix] = last;
+        work.px_fin[pix] = make_float4(r, gg, b, T);
+    }
+}
+
+__global__ void __launch_bounds__(kBlendThreads) k_train_fix(int tiles_x, int W, int H,
+                                                             const uint2 *__restrict__ ranges,
+                                                             const uint32_t *__restrict__ pval,
+                                                             const float4 *__restrict__ rec,
+                                                             float4 *__restrict__ out, BlendWork work) {
+    __shared__ BlendShared<> sh;
+    __shared__ int s_tile;
+    const int n_tiles = tiles_x * ((H + kTile - 1) / kTile);
+    const uint32_t w = blockIdx.x;
+    if (w >= work.t_chunk0[n_tiles]) return;
+    const int tile = chunk_tile(work.t_chunk0, n_tiles, w, &s_tile);
+    const TileGeom g = tile_geom(tile, tiles_x, W, H, work.ox, work.oy);
+    const size_t pix = (size_t)g.py * W + g.px;
+    const bool mine = g.inside && work.t_stop[pix] == (int32_t)w;
+    if (__syncthreads_count(mine) == 0) return;
+    const uint2 rg = ranges[tile];
+    const uint32_t a = rg.x + (w - work.t_chunk0[tile]) * kBwdChunk, b = min(rg.y, a + kBwdChunk);
+    const float4 sb = mine ? work.t_state[pix] : make_float4(0.f, 0.f, 0.f, 1.f);
+    Pixel px{sb.w, sb.x, sb.y, sb.z, mine ? work.t_slast[pix] : 0u, !mine, false};
+    composite_range<2>(sh, a, b, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px);
+    if (mine) {
+        out[pix] = make_float4(px.r, px.g, px.b, 1.0f - px.T);
+        work.px_end[pix] = px.last;
+        work.px_fin[pix] = make_float4(px.r, px.g, px.b, px.T);
+    }
+}
+
 // Plan, part 1 (one thread per tile; meta zeroed before): tiles per list
 // length class (warp-aggregated atomics), and a slot plus
 // ceil((n - kBudget) / kChunk) consecutive chunks for every tile with more
@@ -801,9 +927,15 @@ int launch_blend(int tiles_x, int tiles_y, int W, int H, const uint2 *ranges, co
         return 1;
     }
     if (work.px_end) {
-        // training forward: one pass, per-pixel state for the backward
-        k_blend<2, kBlendThreads><<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
-        return 1;
+        // training forward: every list in parallel chunks, per-pixel state
+        // for the backward
+        k_train_counts<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ranges, work.t_cnt);
+        const int sc = exclusive_scan(work.t_cnt, nullptr, work.t_chunk0, (uint32_t)n, work.t_scan, st);
+        const unsigned grid = (unsigned)train_max_chunks((size_t)n, n_pairs);
+        k_train_chunks<<<grid, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, work);
+        k_train_merge<<<n, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, out, work);
+        k_train_fix<<<grid, kBlendThreads, 0, st>>>(tiles_x, W, H, ranges, pval, rec, out, work);
+        return 4 + sc;
     }
     const unsigned tb = (unsigned)((n + 255) / 256);
     if (cudaMemsetAsync(work.meta, 0, kBlendMetaWords * sizeof(int32_t), st) != cudaSuccess) return -1;

@@ -381,6 +381,18 @@ struct BlendWork {
     uint32_t *px_end;
     float4 *px_fin;
     float4 *px_bnd;
+    // training forward in chunks of kBwdChunk pairs (numbered tile by tile):
+    // chunk counts per tile and their exclusive scan ([tiles + 1]), scan
+    // scratch; per chunk and pixel its composite from T = 1 (T negated when
+    // it met the stop rule) and one past its last composited pair (0: none);
+    // per image pixel the state before its stopping chunk, its last pair so
+    // far and that chunk (-1: none)
+    uint32_t *t_cnt, *t_chunk0, *t_scan;
+    float4 *t_part;
+    uint32_t *t_last;
+    float4 *t_state;
+    uint32_t *t_slast;
+    int32_t *t_stop;
     int32_t *pp_tile;     // [tiles]
     int32_t *chunk_slot;  // [chunks]: the slot of each pass-2 chunk
     int32_t ox, oy;       // window origin: pixel (i, j) has its centre at (ox + i + 0.5, oy + j + 0.5)
@@ -397,6 +409,8 @@ constexpr uint32_t kBlendChunk = 1024;   // pairs per pass-2 chunk
 constexpr uint32_t kBwdChunk = 1024;     // pairs per chunk of the compositing backward
 // boundary-state slots of a training frame of n_pairs pairs
 constexpr size_t bwd_boundary_slots(size_t n_pairs) { return n_pairs / kBwdChunk + 2; }
+// kBwdChunk-pair chunks of a frame of n_tiles tiles and n_pairs pairs, at most
+constexpr size_t train_max_chunks(size_t n_tiles, size_t n_pairs) { return n_pairs / kBwdChunk + n_tiles; }
 constexpr size_t blend_max_slots(size_t n_tiles, size_t n_pairs) {
     return n_tiles < n_pairs / kBlendBudget + 1 ? n_tiles : n_pairs / kBlendBudget + 1;
 }
