@@ -16,9 +16,9 @@
 // and every tile with a short list with one CTA, one warp per block
 // (described at the kernel).
 //
-// The one-pass kernels (statistics and training frames) and the split passes
-// below take one CTA per tile, one thread per pixel, each warp an 8x4 block
-// of the tile.  A CTA walks depth-ordered pairs in batches of 256, software
+// The one-pass kernel of statistics frames, the split passes and the
+// chunked passes of training frames below take one CTA per tile (or chunk of
+// its list), one thread per pixel, each warp an 8x4 block of the tile.  A CTA walks depth-ordered pairs in batches of 256, software
 // pipelined:
 // while the warps composite batch k from one half of a shared double buffer,
 // each thread holds in registers the record it loaded for batch k+1; after
@@ -107,8 +107,7 @@ __device__ __forceinline__ void composite_range(BlendShared<kT> &sh, uint32_t st
                                                 const uint32_t *__restrict__ pval,
                                                 const float4 *__restrict__ rec, int tx0, int ty0,
                                                 float fpx, float fpy, Pixel &px,
-                                                float *__restrict__ contrib = nullptr, int brow0 = 0,
-                                                float4 *__restrict__ bnd = nullptr) {
+                                                float *__restrict__ contrib = nullptr, int brow0 = 0) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t wbit = 1u << warp;
     auto stage = [&](const StagedRecord &r, int h) {
@@ -139,10 +138,6 @@ __device__ __forceinline__ void composite_range(BlendShared<kT> &sh, uint32_t st
     int h = 0;
     for (uint32_t base = start; base < end; base += kT, h ^= 1) {
         const int nb = (int)min((uint32_t)kT, end - base);
-        // training: the pixel's state before pair base at every backward
-        // chunk boundary (kBwdChunk is a multiple of the batch)
-        if (kMode == 2 && bnd && base != start && (base - start) % kBwdChunk == 0)
-            bnd[(size_t)(base / kBwdChunk) * kT + threadIdx.x] = make_float4(px.r, px.g, px.b, px.T);
         for (int c = 0; c < nb; c += 32) {
             if (__all_sync(0xffffffffu, px.done)) break;
             const bool mine = (sh.mask[h][c + lane] & wbit) != 0 && c + lane < nb;
@@ -208,8 +203,8 @@ __device__ __forceinline__ TileGeom tile_geom(int tile, int tiles_x, int W, int 
     return g;
 }
 
-// Pass 1: the first kBudget pairs of every tile (kMode 1 statistics, 2
-// training: every pair in one pass).  kT threads per CTA: 256 cover a tile,
+// One CTA per tile: the first kBudget pairs of the tile (kMode 1,
+// statistics: every pair in one pass).  kT threads per CTA: 256 cover a tile,
 // 128 half a tile (two CTAs per tile, rows 0-7 and 8-15, each compositing
 // the tile's list on its own, so the halves do not wait for each other).
 template <int kMode, int kT>
@@ -225,12 +220,7 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
     if (!in_bounds(rg.x <= rg.y && rg.y <= work.n_pairs, kChkPair)) rg.y = rg.x;
     Pixel px{1.0f, 0.0f, 0.0f, 0.0f, rg.x, !g.inside, false};
     const uint32_t end1 = rg.y - rg.x > kBudget && kMode == 0 ? rg.x + kBudget : rg.y;
-    composite_range<kMode, kT>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib, w0 / 2,
-                               work.px_bnd);
-    if (kMode == 2 && g.inside) {
-        work.px_end[(size_t)g.py * W + g.px] = px.last;
-        work.px_fin[(size_t)g.py * W + g.px] = make_float4(px.r, px.g, px.b, px.T);
-    }
+    composite_range<kMode, kT>(sh, rg.x, end1, pval, rec, g.tx0, g.ty0, g.fpx, g.fpy, px, work.contrib, w0 / 2);
     if (end1 < rg.y && in_bounds(work.cand_slot[tile] >= 0, kChkSlot)) {
         // pairs remain: record the pixel state for pass 2 and the merge (the
         // plan set cand_done to 1; every part clears it unless all its

@@ -372,12 +372,13 @@ struct BlendWork {
     // when set: per splat, sum over pixels of its compositing weight
     // alpha * T (added to); lists are then composited in one pass
     float *contrib;
-    // when set (training forward): per pixel, one past the index of its last
-    // composited pair and its final state (r, g, b, T); one pass as well.
+    // when set (training forward, in chunks): per pixel, one past the index
+    // of its last composited pair and its final state (r, g, b, T).
     // px_bnd: every pixel's state (r, g, b, T) before pair b of its tile's
-    // list, for every b = start + k kBwdChunk (k >= 1) the pass reaches, at
-    // px_bnd[(b / kBwdChunk) * 256 + pixel of the tile] (b / kBwdChunk is
-    // distinct for all such b of a frame: lists are disjoint)
+    // list, for every b = start + k kBwdChunk (k >= 1) up to the chunk in
+    // which the pixel stops, at px_bnd[(b / kBwdChunk) * 256 + pixel of the
+    // tile] (b / kBwdChunk is distinct for all such b of a frame: lists are
+    // disjoint)
     uint32_t *px_end;
     float4 *px_fin;
     float4 *px_bnd;
