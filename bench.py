@@ -163,7 +163,7 @@ def bench_config(sc, args, world=1):
             "template_storage": args.storage}
 
 
-def project_survey_bytes(st, tpl_bytes):
+def project_scope_bytes(st, tpl_bytes):
     """Algorithmic bytes of the fused skinning + projection kernel as the
     hot-path scope table counts them: the shared templates read once, the
     24 skinning transforms (48 B each) of every visible instance, and one
@@ -365,7 +365,7 @@ def run_ours(args, sc, rank, world, local_rank):
     # 40 B per splat record); its measured DRAM traffic is the committed
     # one-pass capture's, null once the kernel has changed since
     top_ms = stage_ms["skin_project"]
-    algo = project_survey_bytes(st0, tpl_b)
+    algo = project_scope_bytes(st0, tpl_b)
     achieved = algo / (top_ms * 1e-3) / 1e9
     kp = prof.get("k_project", {})
     traffic = kp.get("dram_bytes_per_launch")
