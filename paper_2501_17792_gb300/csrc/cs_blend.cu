@@ -249,14 +249,14 @@ __global__ void __launch_bounds__(kT) k_blend(int tiles_x, int W, int H, const u
 // eight warps, instead of every pair in turn: a long list of large splats
 // no longer leaves the GPU waiting on a single CTA.
 //
-// A tile whose list is shorter (below 2^(kPpTileClass - 1) pairs) is one
-// item of its own instead: the CTA stages each batch of kPpRound pairs once
+// In frames with many busy tiles (blend_key), a tile whose list is shorter
+// (below 2^(kPpTileClass - 1) pairs) is one item of its own instead: the CTA stages each batch of kPpRound pairs once
 // for the whole tile, with the blocks each reach box meets as one bit mask
 // per block, and warp w composites block w's pairs in depth order, as the
 // definition reads.  Eight block items would stage every pair eight times
 // and pay eight rounds of barriers and chaining; where lists are mid-length
 // and many (a 4K frame of a large crowd) the pass is bound by instruction
-// issue, and the tile items issue 17% fewer instructions there.
+// issue, and the tile items issue about a fifth fewer instructions there.
 //
 // Persistent CTAs take items in decreasing schedule key (blend_key: the
 // list length class, raised for tile items), so the longest dependency
